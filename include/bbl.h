@@ -1,0 +1,207 @@
+/*
+ * bbl.h - C ABI of the GB300 bootstrapped block Lanczos eigensolver.
+ *
+ * Method: Zbikowski & Johnson, "Bootstrapped Block Lanczos for
+ * large-dimension eigenvalue problems" (arXiv 2210.15763), Sec. II.
+ * The solver finds the nev algebraically smallest eigenpairs of a large,
+ * sparse, real symmetric matrix H by block Lanczos with full
+ * reorthogonalisation, started from a pivot block that is random or
+ * "bootstrapped" from a truncated space.
+ *
+ * Conventions for every entry point
+ *  - Every function returns a bbl_status; nothing throws across the ABI.
+ *    On failure bbl_last_error() returns a thread-local message.
+ *  - Argument errors are detected on the host before any kernel launch.
+ *  - "device pointer" = memory allocated by the caller with cudaMalloc (or by
+ *    torch) on the current device; "host pointer" = ordinary host memory.
+ *    Pointers documented "host or device" are classified with
+ *    cudaPointerGetAttributes.
+ *  - Blocks of vectors are n x b ROW-MAJOR (the b values of one row are
+ *    contiguous), the layout of the paper's W^T (Sec. II.B, Eqs. 3-5).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    ordered on that stream; functions that return results in host memory
+ *    synchronise it before returning.
+ *  - The caller owns every pointer it passes; the library owns (and frees in
+ *    the matching destroy call) everything it allocates.
+ *  - Matrix values are given in FP64 or FP32; the storage precision of the
+ *    device copy is chosen at creation (FP64, or FP32 for the mixed-precision
+ *    form).  Column indices are int32 (n < 2^31), row pointers int64.
+ */
+#ifndef BBL_H
+#define BBL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BBL_OK = 0,
+    BBL_ERR_INVALID_ARG = 1,    /* bad size, pointer, option or CSR structure      */
+    BBL_ERR_NOT_SYMMETRIC = 2,  /* symmetry check requested and failed             */
+    BBL_ERR_OOM = 3,            /* a device allocation failed                      */
+    BBL_ERR_CUDA = 4,           /* a CUDA runtime error (message has the details)  */
+    BBL_ERR_NOT_CONVERGED = 5,  /* basis full before the tolerance was met; the
+                                   best Ritz pairs so far are still returned       */
+    BBL_ERR_NUMERICAL = 6,      /* NaN / Inf or an unrecoverable breakdown         */
+    BBL_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up              */
+    BBL_ERR_UNSUPPORTED = 8     /* valid request this build does not implement     */
+} bbl_status;
+
+typedef enum { BBL_FP64 = 0, BBL_FP32 = 1 } bbl_dtype;
+typedef enum { BBL_CSR = 0, BBL_SELL = 1 } bbl_format;
+
+typedef struct bbl_matrix bbl_matrix;   /* opaque, library-owned device copy of H */
+
+/* Solver options (Sec. II.B; defaults from bbl_options_default). */
+typedef struct {
+    double tol;                 /* converged when every one of the nev lowest Ritz
+                                   pairs has ||H x - theta x||_2 <= tol*||H||_inf
+                                   (default 1e-8)                                  */
+    int max_vectors;            /* basis capacity; J_max = max_vectors / b blocks
+                                   (default 2000)                                  */
+    int criterion;              /* 0: residual estimate ||B_j s_i[last b]||_2;
+                                   1: rms change of the nev lowest Ritz values
+                                   below rms_tol (the paper's Sec. III.A test)     */
+    double rms_tol;             /* for criterion 1 (default 1e-6)                  */
+    uint64_t seed;              /* random pivot and deflation vectors (splitmix64) */
+    double defl_tol;            /* a new column whose orthogonal part is below
+                                   defl_tol*||H||_inf is deflated (default 1e-10;
+                                   1e-6 is used for FP32 storage if left at 0)     */
+    int storage;                /* bbl_dtype of the Lanczos blocks: BBL_FP64, or
+                                   BBL_FP32 (mixed precision: FP32 blocks and SpMM,
+                                   FP64 coefficients, Gram, T, residual).  Must
+                                   match the matrix storage.                       */
+    int polish;                 /* FP32 storage only: 1 (default) restarts FP64
+                                   block Lanczos from the FP32 Ritz vectors to
+                                   reach `tol`; needs an FP64 copy of the values
+                                   (bbl_matrix_create keeps one when asked)       */
+    double stage1_tol;          /* FP32 stage tolerance when polishing (default 2e-6) */
+    int check_every;            /* Ritz solve every k-th block (default 1)         */
+    void* stream;               /* cudaStream_t                                    */
+} bbl_options;
+
+typedef struct {
+    int iters;                  /* block iterations (SpMM calls) in the main stage */
+    int vec_equiv_iters;        /* iters * b (Sec. III.A's vector-equivalent count) */
+    int polish_iters;           /* FP64 block iterations of the polish stage       */
+    int deflations;
+    int converged;
+    double t_spmm_ms, t_reorth_ms, t_cholqr_ms, t_ritz_ms, t_other_ms, t_total_ms;
+    double spmm_bytes;          /* algorithmic bytes of one SpMM of the main stage */
+    double spmm_gbs;            /* spmm_bytes * iters / t_spmm                     */
+    double ns_per_op;           /* t_spmm / (nnz * b * iters)  (Tables I-II)       */
+    double ortho_err;           /* max |V^T V - I| over the final basis (if measured) */
+} bbl_stats;
+
+void bbl_options_default(bbl_options* opt);
+const char* bbl_last_error(void);
+const char* bbl_status_string(bbl_status s);
+int bbl_version(void);
+
+/* ---------------------------------------------------------------- matrix
+ * Copies a CSR matrix (host or device arrays) to the device.
+ *   n, nnz      dimension and number of stored entries (nnz >= 0, n >= 1)
+ *   row_ptr     int64[n+1], row_ptr[0]=0, non-decreasing, row_ptr[n]=nnz
+ *   col         int32[nnz], each row's columns strictly increasing in [0,n)
+ *   val         FP64 or FP32 (val_dtype) [nnz]
+ *   storage     precision of the device values (BBL_FP32 = mixed form)
+ *   fmt         BBL_CSR, or BBL_SELL (SELL-C-sigma with C = 32 rows per
+ *               slice, rows sorted by length inside windows of sell_sigma
+ *               rows; sell_sigma a multiple of 32, 0 = 32 = no sorting)
+ *   keep_fp64   FP32 storage only: also keep an FP64 CSR copy of the values
+ *               for the FP64 polish stage and the FP64 residual
+ *   check_symmetry  1: verify H_ij == H_ji exactly (BBL_ERR_NOT_SYMMETRIC)
+ * The structure (sortedness, range) is always validated on the device
+ * before the call returns.  ||H||_inf and diag(H) are computed at creation. */
+bbl_status bbl_matrix_create(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                             const void* val, bbl_dtype val_dtype, bbl_dtype storage, bbl_format fmt,
+                             int sell_sigma, int keep_fp64, int check_symmetry, void* stream,
+                             bbl_matrix** out);
+void bbl_matrix_destroy(bbl_matrix* A);
+/* n, nnz, ||H||_inf, device bytes held, stored format and precision.  Any output may be NULL. */
+bbl_status bbl_matrix_info(const bbl_matrix* A, int64_t* n, int64_t* nnz, double* norm_inf,
+                           int64_t* device_bytes, int* fmt, int* storage, int64_t* padded_nnz);
+
+/* ---------------------------------------------------------------- S1: SpMM
+ * W = H V (Sec. II.B, Eq. 3; w_{a,i} = sum_j H_ij v_{a,j}).  V, W: device,
+ * n x b row-major, element type = the matrix storage type.  b in 1..16.   */
+bbl_status bbl_spmm(const bbl_matrix* A, int b, const void* V, void* W, void* stream);
+/* Same product in FP64 arithmetic on FP64 blocks whatever the storage (the
+ * final residual of the mixed form).  b in 1..16. */
+bbl_status bbl_spmm_f64(const bbl_matrix* A, int b, const double* V, double* W, void* stream);
+
+/* ---------------------------------------------------------------- S2: reorthogonalisation
+ * Full reorthogonalisation of W against the stored basis (Sec. II.A; block
+ * classical Gram-Schmidt, `passes` passes):  C_p = Q^T W, W <- W - Q C_p.
+ *   basis   device, nblocks consecutive n x b row-major blocks (block-major)
+ *   W       device n x b, overwritten
+ *   coeff   device FP64 [passes][nblocks*b][b] (row-major), or NULL
+ * dtype: element type of basis and W (FP64 / FP32; FP32 accumulates the
+ * coefficients in FP64 across row chunks).  passes in 1..2.            */
+bbl_status bbl_block_reorth(int64_t n, int b, int nblocks, bbl_dtype dtype, const void* basis, void* W,
+                            double* coeff, int passes, void* stream);
+
+/* ---------------------------------------------------------------- S3: CholQR2
+ * W = Q B with Q orthonormal (overwrites W), B upper triangular b x b:
+ * G1 = W^T W, R1 = chol(G1), W <- W R1^{-1}, G2, R2, W <- W R2^{-1}, B = R2 R1.
+ * (Replaces the paper's spectral factorisation of the overlap, Eqs. 9-11.)
+ *   B          device FP64 b x b row-major
+ *   defl_abs   a column whose Cholesky pivot is <= defl_abs^2 is deflated
+ *   n_deflated host int, may be NULL: number of deflated columns.  Deflated
+ *              columns of Q are zero and their rows of B are zero (the solver
+ *              replaces them); the call then returns BBL_OK.               */
+bbl_status bbl_cholqr2(int64_t n, int b, bbl_dtype dtype, void* W, double* B, double defl_abs,
+                       int* n_deflated, void* stream);
+
+/* ---------------------------------------------------------------- S4: Ritz solve
+ * Lowest nev eigenpairs of the symmetric band matrix T (Eq. 12), m x m with
+ * bandwidth p (T_ij = 0 for |i-j| > p), given in lower band storage
+ * Tband[i*(p+1) + d] = T[i][i-d] (d = 0..p; entries with i-d < 0 ignored).
+ *   theta  device FP64 [nev] ascending;  S device FP64 m x nev row-major,
+ *   unit columns (sign: first largest-magnitude entry positive).
+ * Method: Sylvester-inertia bisection (LDL^T of T - sigma I) then inverse
+ * iteration (banded LU with partial pivoting) and Rayleigh quotients; the
+ * vectors of clustered eigenvalues are orthonormalised together.
+ * 1 <= nev <= min(m, 32), p <= 16, m <= 16384.                                   */
+bbl_status bbl_ritz_banded(int m, int p, int nev, const double* Tband, double* theta, double* S,
+                           void* stream);
+
+/* ---------------------------------------------------------------- S5: Ritz vectors
+ * X = Q S: basis as in bbl_block_reorth (m = nblocks*b columns), S device
+ * FP64 m x k row-major, X device FP64 n x k row-major.  k in 1..16.     */
+bbl_status bbl_ritz_vectors(int64_t n, int b, int nblocks, bbl_dtype dtype, const void* basis, int k,
+                            const double* S, double* X, void* stream);
+
+/* ---------------------------------------------------------------- S6: pivots
+ * Random pivot: n x b i.i.d. N(0,1) from splitmix64 (counter 2k, 2k+1 of
+ * element k = i*b + c, Box-Muller), P device FP64.                       */
+bbl_status bbl_pivot_random(int64_t n, int b, uint64_t seed, double* P, void* stream);
+/* Bootstrapped pivot (Sec. II.B "bootstrap", Sec. III): S = the trunc_dim
+ * rows with the smallest H_ii (ties: lower index), eigenvectors of the
+ * lowest b eigenvalues of H[S,S] (block Lanczos on the GPU to sub_tol, or a
+ * dense solve when trunc_dim <= b), zero-padded into P (device FP64 n x b
+ * row-major).  If b > trunc_dim the remaining columns are random.       */
+bbl_status bbl_pivot_bootstrap(const bbl_matrix* A, int64_t trunc_dim, int b, double sub_tol, uint64_t seed,
+                               double* P, void* stream);
+
+/* ---------------------------------------------------------------- solve
+ * Block Lanczos for the nev lowest eigenpairs (Sec. II.B, Eqs. 4-12).
+ *   pivot   host or device FP64 n x b, or NULL (random, opt->seed)
+ *   evals   host FP64 [nev] ascending
+ *   evecs   host or device FP64 n x nev row-major, or NULL
+ *   resid   host FP64 [nev]: true ||H x_i - theta_i x_i||_2 in FP64, or NULL
+ *   stats   host, or NULL
+ * b in 1..16, nev in 1..min(64, max_vectors).  Returns BBL_OK when
+ * converged, BBL_ERR_NOT_CONVERGED (outputs filled) when the basis is full.
+ * Device work is ordered on opt->stream; the call synchronises it.      */
+bbl_status bbl_solve(const bbl_matrix* A, int nev, int b, const double* pivot, const bbl_options* opt,
+                     double* evals, double* evecs, double* resid, bbl_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BBL_H */

@@ -1,0 +1,247 @@
+"""GB300-native bootstrapped block Lanczos (Zbikowski & Johnson, arXiv 2210.15763).
+
+Thin Python binding of the C ABI declared in include/bbl.h.  Every step of
+the eigensolver runs in the CUDA library libbbl.so; this module only
+marshals arguments.  PyTorch provides device memory and streams.  There is
+no CPU fallback: the functions raise if the library cannot be loaded or no
+GPU is present.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+
+import numpy as np
+
+from . import _lib
+from ._lib import BBLError, CSR, FP32, FP64, SELL, Options, Stats
+
+__all__ = ["Matrix", "spmm", "spmm_f64", "block_reorth", "cholqr2", "ritz_banded", "ritz_vectors", "pivot_random",
+           "pivot_bootstrap", "solve", "SolveResult", "BBLError", "options", "FP32", "FP64", "CSR", "SELL"]
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("paper_2210_15763_gb300 needs a CUDA GPU (no CPU fallback)")
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(int(x))
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t == torch.float64:
+        return FP64
+    if t == torch.float32:
+        return FP32
+    raise TypeError(f"unsupported dtype {t}")
+
+
+def options(**kw) -> Options:
+    """bbl_options with defaults from bbl_options_default, overridden by keywords."""
+    lib = _lib.load()
+    o = Options()
+    lib.bbl_options_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "stream":
+            o.stream = _stream(v)
+        elif k == "storage" and isinstance(v, str):
+            o.storage = FP32 if v == "fp32" else FP64
+        else:
+            setattr(o, k, v)
+    return o
+
+
+class Matrix:
+    """Device copy of a sparse symmetric matrix (bbl_matrix).
+
+    `csr` is anything with n, row_ptr (int64), col (int32) and val (float64 or
+    float32) as numpy arrays or torch tensors (host or device)."""
+
+    def __init__(self, csr, storage: str = "fp64", fmt: str = "csr", sell_sigma: int = 0, keep_fp64: bool = False,
+                 check_symmetry: bool = False, stream=None):
+        lib = _lib.load()
+        self._lib = lib
+        rp, col, val = csr.row_ptr, csr.col, csr.val
+        if isinstance(rp, np.ndarray):
+            rp = np.ascontiguousarray(rp, dtype=np.int64)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            if val.dtype not in (np.float64, np.float32):
+                val = val.astype(np.float64)
+            val = np.ascontiguousarray(val)
+            vdt = FP64 if val.dtype == np.float64 else FP32
+        else:
+            vdt = _dtype_code(val.dtype)
+        self._keep = (rp, col, val)  # keep the arrays alive during the call
+        h = C.c_void_p()
+        st = lib.bbl_matrix_create(int(csr.n), int(rp[-1]) if isinstance(rp, np.ndarray) else int(rp[-1].item()),
+                                   _ptr(rp), _ptr(col), _ptr(val), vdt, FP32 if storage == "fp32" else FP64,
+                                   SELL if fmt == "sell" else CSR, int(sell_sigma), int(keep_fp64),
+                                   int(check_symmetry), _stream(stream), C.byref(h))
+        self._keep = None
+        _lib.check(st)
+        self.handle = h
+        self.storage = storage
+        self.fmt = fmt
+        n, nnz, nb, fm, sto, pnz = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int(), C.c_int(), C.c_int64()
+        norm = C.c_double()
+        _lib.check(lib.bbl_matrix_info(h, C.byref(n), C.byref(nnz), C.byref(norm), C.byref(nb), C.byref(fm),
+                                       C.byref(sto), C.byref(pnz)))
+        self.n, self.nnz, self.norm_inf, self.device_bytes, self.padded_nnz = n.value, nnz.value, norm.value, nb.value, pnz.value
+
+    @property
+    def dtype(self):
+        torch = _torch()
+        return torch.float32 if self.storage == "fp32" else torch.float64
+
+    def diagonal(self, stream=None):
+        torch = _torch()
+        d = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        _lib.check(self._lib.bbl_matrix_diagonal(self.handle, _ptr(d), _stream(stream)))
+        return d
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.bbl_matrix_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spmm(A: Matrix, V, W=None, stream=None, lanes_per_row: int | None = None):
+    """W = H V (S1); V, W: CUDA tensors n x b in the matrix storage dtype."""
+    torch = _torch()
+    b = V.shape[1]
+    if W is None:
+        W = torch.empty_like(V)
+    if lanes_per_row is None:
+        _lib.check(A._lib.bbl_spmm(A.handle, b, _ptr(V), _ptr(W), _stream(stream)))
+    else:
+        _lib.check(A._lib.bbl_spmm_group(A.handle, b, _ptr(V), _ptr(W), int(lanes_per_row), _stream(stream)))
+    return W
+
+
+def spmm_f64(A: Matrix, V, W=None, stream=None):
+    """W = H V in FP64 arithmetic (FP64 blocks) whatever the storage."""
+    torch = _torch()
+    if W is None:
+        W = torch.empty_like(V)
+    _lib.check(A._lib.bbl_spmm_f64(A.handle, V.shape[1], _ptr(V), _ptr(W), _stream(stream)))
+    return W
+
+
+def block_reorth(basis, W, passes: int = 2, stream=None):
+    """Full reorthogonalisation of W (n x b) against basis (nblocks x n x b), in place.
+    Returns the FP64 coefficients (passes x nblocks*b x b)."""
+    torch = _torch()
+    nb, n, b = basis.shape
+    coeff = torch.empty((passes, nb * b, b), dtype=torch.float64, device=W.device)
+    _lib.check(_lib.load().bbl_block_reorth(n, b, nb, _dtype_code(W.dtype), _ptr(basis), _ptr(W), _ptr(coeff),
+                                            passes, _stream(stream)))
+    return coeff
+
+
+def cholqr2(W, defl_abs: float = 0.0, stream=None):
+    """CholQR2 in place: W <- Q; returns (B (b x b FP64), number of deflated columns)."""
+    torch = _torch()
+    n, b = W.shape
+    B = torch.empty((b, b), dtype=torch.float64, device=W.device)
+    nd = C.c_int()
+    _lib.check(_lib.load().bbl_cholqr2(n, b, _dtype_code(W.dtype), _ptr(W), _ptr(B), float(defl_abs), C.byref(nd),
+                                       _stream(stream)))
+    return B, nd.value
+
+
+def ritz_banded(Tband, nev: int, stream=None):
+    """Lowest nev eigenpairs of the band matrix in lower band storage (m x (p+1))."""
+    torch = _torch()
+    m, p1 = Tband.shape
+    theta = torch.empty(nev, dtype=torch.float64, device=Tband.device)
+    S = torch.empty((m, nev), dtype=torch.float64, device=Tband.device)
+    _lib.check(_lib.load().bbl_ritz_banded(m, p1 - 1, nev, _ptr(Tband), _ptr(theta), _ptr(S), _stream(stream)))
+    return theta, S
+
+
+def ritz_vectors(basis, S, stream=None):
+    """X = Q S (FP64 n x k)."""
+    torch = _torch()
+    nb, n, b = basis.shape
+    k = S.shape[1]
+    X = torch.empty((n, k), dtype=torch.float64, device=basis.device)
+    _lib.check(_lib.load().bbl_ritz_vectors(n, b, nb, _dtype_code(basis.dtype), _ptr(basis), k, _ptr(S), _ptr(X),
+                                            _stream(stream)))
+    return X
+
+
+def pivot_random(n: int, b: int, seed: int, stream=None):
+    torch = _torch()
+    P = torch.empty((n, b), dtype=torch.float64, device="cuda")
+    _lib.check(_lib.load().bbl_pivot_random(n, b, seed, _ptr(P), _stream(stream)))
+    return P
+
+
+def pivot_bootstrap(A: Matrix, trunc_dim: int, b: int, sub_tol: float = 1e-10, seed: int = 0, stream=None):
+    torch = _torch()
+    P = torch.empty((A.n, b), dtype=torch.float64, device="cuda")
+    _lib.check(A._lib.bbl_pivot_bootstrap(A.handle, int(trunc_dim), b, float(sub_tol), seed, _ptr(P), _stream(stream)))
+    return P
+
+
+@dataclasses.dataclass
+class SolveResult:
+    evals: np.ndarray
+    evecs: object
+    resid: np.ndarray
+    stats: dict
+    status: str
+
+    @property
+    def converged(self) -> bool:
+        return self.status == "BBL_OK"
+
+
+def solve(A: Matrix, nev: int, b: int, pivot=None, evecs: str = "device", **opts) -> SolveResult:
+    """Block Lanczos for the nev lowest eigenpairs (bbl_solve).
+
+    pivot: None (random), a CUDA tensor or a numpy array, n x b FP64.
+    evecs: "device" (CUDA tensor), "host" (numpy array) or None."""
+    torch = _torch()
+    o = options(**opts)
+    if "storage" not in opts:
+        o.storage = FP32 if A.storage == "fp32" else FP64
+    if "stream" not in opts:
+        o.stream = _stream(None)
+    ev = np.zeros(nev)
+    rs = np.zeros(nev)
+    if evecs == "device":
+        X = torch.empty((A.n, nev), dtype=torch.float64, device="cuda")
+    elif evecs == "host":
+        X = np.zeros((A.n, nev))
+    else:
+        X = None
+    if isinstance(pivot, np.ndarray):
+        pivot = np.ascontiguousarray(pivot, dtype=np.float64)
+    st = Stats()
+    s = A._lib.bbl_solve(A.handle, nev, b, _ptr(pivot), C.byref(o), _ptr(ev), _ptr(X), _ptr(rs), C.byref(st))
+    _lib.check(s, allow=(0, 5))
+    return SolveResult(ev, X, rs, st.as_dict(), _lib.STATUS[s])

@@ -1,0 +1,158 @@
+// Internal helpers shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/bbl.h"
+
+namespace bbl {
+
+constexpr int kWarp = 32;
+constexpr int kSellC = 32;     // rows per SELL slice
+constexpr int kMaxB = 16;      // largest block size
+
+// ------------------------------------------------------------------ errors
+bbl_status set_error(bbl_status s, const char* fmt, ...);
+void clear_error();
+
+#define BBL_CUDA(call)                                                                 \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            if (e_ == cudaErrorMemoryAllocation)                                       \
+                return ::bbl::set_error(BBL_ERR_OOM, "%s: %s (%s:%d)", #call,          \
+                                        cudaGetErrorString(e_), __FILE__, __LINE__);   \
+            return ::bbl::set_error(BBL_ERR_CUDA, "%s: %s (%s:%d)", #call,             \
+                                    cudaGetErrorString(e_), __FILE__, __LINE__);       \
+        }                                                                              \
+    } while (0)
+
+#define BBL_TRY(expr)                                                                  \
+    do {                                                                               \
+        bbl_status s_ = (expr);                                                        \
+        if (s_ != BBL_OK) return s_;                                                   \
+    } while (0)
+
+#define BBL_LAUNCH_CHECK() BBL_CUDA(cudaGetLastError())
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline size_t dtype_size(int dt) { return dt == BBL_FP64 ? 8 : 4; }
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Is p device-accessible memory the kernels may read directly?
+bool is_device_pointer(const void* p);
+
+// ------------------------------------------------------------------ device buffers
+// Owning device allocation; frees on destruction.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    bbl_status alloc(size_t nbytes) {
+        release();
+        if (nbytes == 0) nbytes = 16;
+        cudaError_t e = cudaMalloc(&p, nbytes);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            (void)cudaGetLastError();
+            return set_error(BBL_ERR_OOM, "cudaMalloc(%zu bytes): %s", nbytes, cudaGetErrorString(e));
+        }
+        bytes = nbytes;
+        return BBL_OK;
+    }
+    template <typename T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+// Pinned host staging buffer.
+struct HostBuf {
+    void* p = nullptr;
+    HostBuf() = default;
+    HostBuf(const HostBuf&) = delete;
+    HostBuf& operator=(const HostBuf&) = delete;
+    ~HostBuf() { if (p) cudaFreeHost(p); }
+    bbl_status alloc(size_t nbytes) {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cudaError_t e = cudaMallocHost(&p, nbytes ? nbytes : 16);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            (void)cudaGetLastError();
+            return set_error(BBL_ERR_OOM, "cudaMallocHost(%zu): %s", nbytes, cudaGetErrorString(e));
+        }
+        return BBL_OK;
+    }
+    template <typename T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+}  // namespace bbl
+
+// ------------------------------------------------------------------ the matrix object
+struct bbl_matrix {
+    int64_t n = 0, nnz = 0;
+    int fmt = BBL_CSR;
+    int storage = BBL_FP64;
+    double norm_inf = 0.0;
+    // CSR (always kept unless SELL-only FP32 without keep flag; see matrix.cu)
+    bbl::DevBuf row_ptr;   // int64 [n+1]
+    bbl::DevBuf col;       // int32 [nnz]
+    bbl::DevBuf val;       // storage type [nnz]
+    bbl::DevBuf val64;     // FP64 copy of the values (FP32 storage with keep_fp64)
+    bool has_csr = false;
+    // SELL-C-sigma
+    int sell_sigma = 0;
+    int64_t nslices = 0, padded_nnz = 0;
+    bbl::DevBuf slice_ptr; // int64 [nslices+1], element offsets
+    bbl::DevBuf sell_col;  // int32 [padded_nnz]
+    bbl::DevBuf sell_val;  // storage type [padded_nnz]
+    bbl::DevBuf sell_len;  // int32 [nslices*32] row lengths (0 past n)
+    bbl::DevBuf perm;      // int32 [nslices*32] original row of each slot (-1 past n)
+    // diagonal, FP64 [n]
+    bbl::DevBuf diag;
+    int64_t device_bytes() const {
+        return (int64_t)(row_ptr.bytes + col.bytes + val.bytes + val64.bytes + slice_ptr.bytes + sell_col.bytes +
+                         sell_val.bytes + sell_len.bytes + perm.bytes + diag.bytes);
+    }
+};
+
+namespace bbl {
+// spmm.cu
+bbl_status spmm_dispatch(const bbl_matrix* A, int b, const void* V, void* W, bool f64_arith, cudaStream_t st,
+                         int rows_per_warp_hint = 0);
+// block.cu
+struct BlockWork;  // scratch for Gram/reorth/CholQR2
+bbl_status gram(int64_t n, int b, int nblocks, int dtype, const void* Q, const void* W, double* C,
+                DevBuf& partials, cudaStream_t st);
+bbl_status update(int64_t n, int b, int nblocks, int dtype, const void* Q, const double* C, void* W,
+                  cudaStream_t st);
+bbl_status ritz_vectors(int64_t n, int b, int nblocks, int dtype, const void* Q, int k, const double* S,
+                        double* X, cudaStream_t st);
+bbl_status cholqr2_dev(int64_t n, int b, int dtype, void* W, double* B, double defl_abs2, int* d_ndefl,
+                       int* d_deflmask, DevBuf& partials, DevBuf& small, cudaStream_t st);
+// ritz.cu
+bbl_status ritz_dev(int m, int p, int nev, const double* Tband, double* theta, double* S, DevBuf& work,
+                    cudaStream_t st);
+// rng.cu
+bbl_status fill_normal(int64_t n, int b, uint64_t seed, uint64_t offset, double* P, cudaStream_t st);
+bbl_status fill_uniform_cols(int64_t n, int b, int dtype, uint64_t seed, uint64_t offset, const int* mask,
+                             void* Z, cudaStream_t st);
+}  // namespace bbl

@@ -1,0 +1,608 @@
+// S4: Ritz solve of the block-tridiagonal T (Sec. II.B, Eq. 12), which the
+// paper hands to LAPACK.  T is symmetric with bandwidth p = b (its
+// off-diagonal blocks B_j from CholQR2 are upper triangular), stored as a
+// lower band: Tb[i*(p+1) + d] = T[i][i-d].
+//
+// Three kernels, all on the device:
+//  1. bisect  - one CTA per wanted eigenvalue index i.  Sylvester's law of
+//               inertia: the number of negative pivots of the LDL^T
+//               factorisation of T - sigma I is the number of eigenvalues below
+//               sigma.  Each warp evaluates one shift (multisection), the
+//               (p+1)x(p+1) active window of the elimination lives in shared
+//               memory with circular row/column indices, one lane per window
+//               column.  Rounds run first in FP32 (64x the FP64 rate on this
+//               GPU) down to a bracket of 1e-4 * scale, the bracket is then
+//               checked with two FP64 counts and refined in FP64.
+//  2. invit   - one warp per eigenvalue: banded LU with partial pivoting of
+//               T - theta I (U has bandwidth 2p), two steps of inverse
+//               iteration from a per-index pseudo-random start, Rayleigh
+//               quotient.
+//  3. cluster - one CTA: eigenvalues closer than 1e-3 * scale are grouped;
+//               their vectors are orthonormalised twice (modified
+//               Gram-Schmidt) and rotated by a small Jacobi Rayleigh-Ritz;
+//               columns get the sign convention (first largest-magnitude
+//               entry positive).
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace bbl {
+namespace {
+
+constexpr int kMaxP = kMaxB;            // bandwidth limit
+constexpr int kWin = kMaxP + 1;         // LDL^T window edge
+constexpr int kBisectWarps = 4;
+constexpr int kMaxNev = 32;
+
+__device__ __forceinline__ double band_get(const double* __restrict__ Tb, int p, int m, int r, int c) {
+    // T[r][c] for any r, c (0 outside the band or the matrix)
+    if (r < 0 || c < 0 || r >= m || c >= m) return 0.0;
+    if (r >= c) return (r - c <= p) ? Tb[(int64_t)r * (p + 1) + (r - c)] : 0.0;
+    return (c - r <= p) ? Tb[(int64_t)c * (p + 1) + (c - r)] : 0.0;
+}
+
+// Number of eigenvalues of T strictly below sigma (LDL^T of T - sigma I),
+// evaluated by one warp.  win: this warp's (p+1)^2 shared-memory window.
+template <typename F>
+__device__ int inertia_count(const double* __restrict__ Tb, int p, int m, double sigma, double pivmin, F* win) {
+    const int lane = threadIdx.x & 31;
+    const int P1 = p + 1;
+    // initial window: rows/cols 0..p
+    for (int e = lane; e < P1 * P1; e += 32) {
+        const int r = e / P1, c = e % P1;
+        double v = band_get(Tb, p, m, r, c);
+        if (r == c) v = (r < m) ? v - sigma : 1e300;
+        win[e] = (F)((r == c && r >= m) ? (F)1e30 : (F)v);
+    }
+    __syncwarp();
+    int neg = 0;
+    const F fpivmin = (F)pivmin;
+    for (int k = 0; k < m; ++k) {
+        const int ks = k % P1;
+        F d = win[ks * P1 + ks];
+        if (fabs((double)d) < (double)fpivmin) d = -fpivmin;
+        neg += (d < F(0));
+        const F rd = F(1) / d;
+        // lane c (1..p) updates window column k+c, rows k+c..k+p (lower triangle
+        // plus the mirrored upper part it owns)
+        if (lane >= 1 && lane <= p) {
+            const int cs = (k + lane) % P1;
+            const F u = win[ks * P1 + cs] * rd;
+            for (int r = 1; r <= p; ++r) {
+                const int rs = (k + r) % P1;
+                win[rs * P1 + cs] -= win[rs * P1 + ks] * u;
+            }
+        }
+        __syncwarp();
+        // bring in row/column k+p+1 in the freed slot ks
+        const int R = k + p + 1;
+        if (lane <= p) {
+            const int C = k + 1 + lane;  // C in [k+1, k+p+1]
+            const int cs = C % P1;
+            double v;
+            if (R >= m) v = (C == R) ? 1e300 : 0.0;
+            else v = band_get(Tb, p, m, R, C) - (C == R ? sigma : 0.0);
+            const F fv = (R >= m && C == R) ? (F)1e30 : (F)v;
+            win[ks * P1 + cs] = fv;
+            win[cs * P1 + ks] = fv;
+        }
+        __syncwarp();
+    }
+    return neg;
+}
+
+struct Bracket {
+    double lo, hi;
+};
+
+__global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p, int nev, const double* __restrict__ Tb,
+                                                                   double* __restrict__ theta_out,
+                                                                   double* __restrict__ width_out) {
+    __shared__ double win64[kBisectWarps][kWin * kWin];
+    __shared__ float win32[kBisectWarps][kWin * kWin];
+    __shared__ int counts[kBisectWarps];
+    __shared__ double red[2][32 * kBisectWarps];
+    __shared__ double s_lo, s_hi;
+    const int i = blockIdx.x;
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
+    // Gershgorin interval
+    double gmin = 1e308, gmax = -1e308;
+    for (int r = tid; r < m; r += blockDim.x) {
+        double off = 0.0;
+        for (int c = max(0, r - p); c <= min(m - 1, r + p); ++c)
+            if (c != r) off += fabs(band_get(Tb, p, m, r, c));
+        const double d = band_get(Tb, p, m, r, r);
+        gmin = fmin(gmin, d - off);
+        gmax = fmax(gmax, d + off);
+    }
+    red[0][tid] = gmin;
+    red[1][tid] = gmax;
+    __syncthreads();
+    if (tid == 0) {
+        for (int t = 1; t < blockDim.x; ++t) {
+            gmin = fmin(gmin, red[0][t]);
+            gmax = fmax(gmax, red[1][t]);
+        }
+        const double scale = fmax(fabs(gmin), fabs(gmax));
+        const double pad = 1e-10 * scale + 1e-300;
+        s_lo = gmin - pad;
+        s_hi = gmax + pad;
+    }
+    __syncthreads();
+    const double scale = fmax(fmax(fabs(s_lo), fabs(s_hi)), 1e-300);
+    // pivots smaller than these are replaced by -pivmin (a perturbation of T
+    // far below the bracket widths used): keeps the elimination finite
+    const double pivmin64 = 1e-14 * scale;
+    const double pivmin32 = 1e-6 * scale;
+    const double glo = s_lo, ghi = s_hi;
+    double lo = glo, hi = ghi;
+    // phase 1: FP32 multisection to a 1e-4 * scale bracket
+    for (int round = 0; round < 40 && (hi - lo) > 1e-4 * scale; ++round) {
+        const double sigma = lo + (hi - lo) * (double)(warp + 1) / (double)(kBisectWarps + 1);
+        const int cnt = inertia_count<float>(Tb, p, m, sigma, pivmin32, win32[warp]);
+        if (lane == 0) counts[warp] = cnt;
+        __syncthreads();
+        double nlo = lo, nhi = hi;
+        for (int w = 0; w < kBisectWarps; ++w) {
+            const double s = lo + (hi - lo) * (double)(w + 1) / (double)(kBisectWarps + 1);
+            if (counts[w] <= i) nlo = fmax(nlo, s);
+            else nhi = fmin(nhi, s);
+        }
+        __syncthreads();
+        if (nlo >= nhi) break;  // inconsistent FP32 counts: stop, the FP64 check below decides
+        lo = nlo;
+        hi = nhi;
+    }
+    // phase 2: check the bracket in FP64 (warp 0 at lo, warp 1 at hi)
+    if (warp < 2) {
+        const int cnt = inertia_count<double>(Tb, p, m, warp == 0 ? lo : hi, pivmin64, win64[warp]);
+        if (lane == 0) counts[warp] = cnt;
+    }
+    __syncthreads();
+    if (!(counts[0] <= i && counts[1] > i)) {
+        lo = glo;
+        hi = ghi;
+    }
+    __syncthreads();
+    // phase 3: FP64 multisection
+    for (int round = 0; round < 200; ++round) {
+        const double tolw = 1e-12 * scale + 1e-300;
+        if (hi - lo <= tolw) break;
+        const double sigma = lo + (hi - lo) * (double)(warp + 1) / (double)(kBisectWarps + 1);
+        const int cnt = inertia_count<double>(Tb, p, m, sigma, pivmin64, win64[warp]);
+        if (lane == 0) counts[warp] = cnt;
+        __syncthreads();
+        double nlo = lo, nhi = hi;
+        for (int w = 0; w < kBisectWarps; ++w) {
+            const double s = lo + (hi - lo) * (double)(w + 1) / (double)(kBisectWarps + 1);
+            if (counts[w] <= i) nlo = fmax(nlo, s);
+            else nhi = fmin(nhi, s);
+        }
+        __syncthreads();
+        if (nlo >= nhi || (nlo == lo && nhi == hi)) break;
+        lo = nlo;
+        hi = nhi;
+    }
+    if (tid == 0) {
+        theta_out[i] = 0.5 * (lo + hi);
+        width_out[i] = hi - lo;
+    }
+}
+
+__device__ __forceinline__ double hash_uniform(uint64_t a, uint64_t b) {
+    uint64_t z = a * 0x9E3779B97F4A7C15ull + b + 0x632BE59BD9B4E019ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return ((double)(z >> 11) + 0.5) * 0x1.0p-53 * 2.0 - 1.0;
+}
+
+// Inverse iteration for eigenvalue i.  ws: per-eigenvalue workspace of
+// m*(3p+1) doubles + m ints (U rows of width 2p+1, L multipliers, pivots).
+__global__ void __launch_bounds__(32) invit_kernel(int m, int p, const double* __restrict__ Tb,
+                                                    double* __restrict__ theta, double* __restrict__ S, int nev,
+                                                    double* __restrict__ ws, double scale_hint) {
+    extern __shared__ double sm[];
+    const int i = blockIdx.x;
+    const int lane = threadIdx.x;
+    const int P1 = p + 1, UW = 2 * p + 1;
+    double* win = sm;              // P1 x UW circular window
+    double* x = win + P1 * UW;     // m
+    double* lsh = x + m;           // p multipliers
+    double* U = ws + (int64_t)i * m * (3 * p + 1);
+    double* L = U + (int64_t)m * UW;
+    int* piv = reinterpret_cast<int*>(ws + (int64_t)nev * m * (3 * p + 1)) + (int64_t)i * m;
+    const double sigma = theta[i];
+    double scale = 0.0;
+    for (int r = lane; r < m; r += 32) {
+        double s = 0.0;
+        for (int c = max(0, r - p); c <= min(m - 1, r + p); ++c) s += fabs(band_get(Tb, p, m, r, c));
+        scale = fmax(scale, s);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) scale = fmax(scale, __shfl_xor_sync(0xffffffffu, scale, off));
+    scale = fmax(scale, scale_hint);
+    const double tiny = 1e-14 * fmax(scale, 1e-300);
+    // window init: rows 0..p, columns 0..2p
+    for (int e = lane; e < P1 * UW; e += 32) {
+        const int r = e / UW, c = e % UW;
+        double v = (r < m && c < m) ? band_get(Tb, p, m, r, c) : 0.0;
+        if (r == c && r < m) v -= sigma;
+        win[(r % P1) * UW + (c % UW)] = v;
+    }
+    __syncwarp();
+    for (int k = 0; k < m; ++k) {
+        const int ks = k % P1;
+        const int kc = k % UW;
+        // pivot search over rows k..min(k+p, m-1)
+        double best = -1.0;
+        int bi = 0;
+        if (lane <= p && k + lane < m) {
+            best = fabs(win[((k + lane) % P1) * UW + kc]);
+            bi = lane;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        const int ps = (k + bi) % P1;
+        if (bi != 0) {
+            for (int c = lane; c < UW; c += 32) {
+                const int cs = (k + c) % UW;
+                const double a = win[ks * UW + cs], b2 = win[ps * UW + cs];
+                win[ks * UW + cs] = b2;
+                win[ps * UW + cs] = a;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            piv[k] = k + bi;
+            double u = win[ks * UW + kc];
+            if (fabs(u) < tiny) u = (u < 0.0) ? -tiny : tiny;
+            win[ks * UW + kc] = u;
+        }
+        __syncwarp();
+        for (int c = lane; c < UW; c += 32) U[(int64_t)k * UW + c] = win[ks * UW + (k + c) % UW];
+        const double u0 = win[ks * UW + kc];
+        if (lane >= 1 && lane <= p) {
+            const double l = (k + lane < m) ? win[((k + lane) % P1) * UW + kc] / u0 : 0.0;
+            lsh[lane - 1] = l;
+            L[(int64_t)k * p + lane - 1] = l;
+        }
+        __syncwarp();
+        for (int c = lane; c < UW; c += 32) {
+            if (c == 0) continue;
+            const int cs = (k + c) % UW;
+            const double top = win[ks * UW + cs];
+            for (int r = 1; r <= p; ++r) {
+                const int rs = (k + r) % P1;
+                win[rs * UW + cs] -= lsh[r - 1] * top;
+            }
+        }
+        __syncwarp();
+        // slot ks now holds row k+p+1; column slot kc now holds column k+2p+1
+        const int R = k + p + 1;
+        for (int c = lane; c < UW; c += 32) {
+            const int C = k + 1 + c;
+            double v = 0.0;
+            if (R < m && C < m) v = band_get(Tb, p, m, R, C) - (R == C ? sigma : 0.0);
+            win[ks * UW + (C % UW)] = v;
+        }
+        if (lane >= 1 && lane <= p) {
+            win[((k + lane) % P1) * UW + kc] = 0.0;  // (k+lane, k+2p+1) is outside the band
+        }
+        __syncwarp();
+    }
+    // inverse iteration
+    for (int r = lane; r < m; r += 32) x[r] = hash_uniform((uint64_t)i + 1, (uint64_t)r);
+    __syncwarp();
+    for (int it = 0; it < 3; ++it) {
+        // forward: P and L
+        for (int k = 0; k < m; ++k) {
+            if (lane == 0) {
+                const int pk = piv[k];
+                if (pk != k) {
+                    const double t = x[k];
+                    x[k] = x[pk];
+                    x[pk] = t;
+                }
+            }
+            __syncwarp();
+            if (lane >= 1 && lane <= p && k + lane < m) x[k + lane] -= L[(int64_t)k * p + lane - 1] * x[k];
+            __syncwarp();
+        }
+        // backward: U (bandwidth 2p)
+        for (int k = m - 1; k >= 0; --k) {
+            double s = 0.0;
+            for (int c = lane; c < UW; c += 32)
+                if (c >= 1 && k + c < m) s += U[(int64_t)k * UW + c] * x[k + c];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0) x[k] = (x[k] - s) / U[(int64_t)k * UW];
+            __syncwarp();
+        }
+        // normalise
+        double nn = 0.0;
+        for (int r = lane; r < m; r += 32) nn += x[r] * x[r];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, off);
+        const double inv = 1.0 / sqrt(nn);
+        for (int r = lane; r < m; r += 32) x[r] *= inv;
+        __syncwarp();
+    }
+    // Rayleigh quotient
+    double rq = 0.0;
+    for (int r = lane; r < m; r += 32) {
+        double tx = 0.0;
+        for (int c = max(0, r - p); c <= min(m - 1, r + p); ++c) tx += band_get(Tb, p, m, r, c) * x[c];
+        rq += x[r] * tx;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) rq += __shfl_xor_sync(0xffffffffu, rq, off);
+    if (lane == 0) theta[i] = rq;
+    for (int r = lane; r < m; r += 32) S[(int64_t)r * nev + i] = x[r];
+}
+
+// Groups close eigenvalues, orthonormalises their vectors, Rayleigh-Ritz in
+// each group (cyclic Jacobi), sorts, applies the sign convention.
+__global__ void __launch_bounds__(256) cluster_kernel(int m, int p, int nev, const double* __restrict__ Tb,
+                                                      double* __restrict__ theta, double* __restrict__ S,
+                                                      double* __restrict__ tmp /* m x nev */) {
+    __shared__ double K[kMaxNev * kMaxNev];
+    __shared__ double Z[kMaxNev * kMaxNev];
+    __shared__ double red[256];
+    __shared__ double th[kMaxNev];
+    __shared__ int start[kMaxNev + 1];
+    __shared__ int ngroups;
+    __shared__ double s_scale;
+    const int tid = threadIdx.x;
+    // scale = max |theta|, at least the largest diagonal magnitude
+    double sc = 0.0;
+    for (int r = tid; r < m; r += 256) sc = fmax(sc, fabs(band_get(Tb, p, m, r, r)));
+    for (int k = tid; k < nev; k += 256) sc = fmax(sc, fabs(theta[k]));
+    red[tid] = sc;
+    __syncthreads();
+    if (tid == 0) {
+        for (int t = 1; t < 256; ++t) sc = fmax(sc, red[t]);
+        s_scale = fmax(sc, 1e-300);
+        // sort theta (and remember the permutation in start[] temporarily): insertion sort
+        for (int k = 0; k < nev; ++k) th[k] = theta[k];
+    }
+    __syncthreads();
+    // sort columns by theta (selection on thread 0, column swaps in parallel)
+    for (int a = 0; a < nev; ++a) {
+        __shared__ int sel;
+        if (tid == 0) {
+            int best = a;
+            for (int k = a + 1; k < nev; ++k)
+                if (th[k] < th[best]) best = k;
+            sel = best;
+            const double t = th[a];
+            th[a] = th[best];
+            th[best] = t;
+        }
+        __syncthreads();
+        if (sel != a) {
+            for (int r = tid; r < m; r += 256) {
+                const double t = S[(int64_t)r * nev + a];
+                S[(int64_t)r * nev + a] = S[(int64_t)r * nev + sel];
+                S[(int64_t)r * nev + sel] = t;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        int g = 0;
+        start[0] = 0;
+        for (int k = 1; k < nev; ++k)
+            if (th[k] - th[k - 1] > 1e-3 * s_scale) start[++g] = k;
+        start[++g] = nev;
+        ngroups = g;
+    }
+    __syncthreads();
+    for (int g = 0; g < ngroups; ++g) {
+        const int a0 = start[g], a1 = start[g + 1], k = a1 - a0;
+        if (k < 2) continue;
+        // MGS twice over the group's columns
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int a = a0; a < a1; ++a) {
+                for (int q = a0; q < a; ++q) {
+                    double s = 0.0;
+                    for (int r = tid; r < m; r += 256) s += S[(int64_t)r * nev + q] * S[(int64_t)r * nev + a];
+                    red[tid] = s;
+                    __syncthreads();
+                    for (int w = 128; w > 0; w >>= 1) {
+                        if (tid < w) red[tid] += red[tid + w];
+                        __syncthreads();
+                    }
+                    const double dot = red[0];
+                    __syncthreads();
+                    for (int r = tid; r < m; r += 256) S[(int64_t)r * nev + a] -= dot * S[(int64_t)r * nev + q];
+                    __syncthreads();
+                }
+                double s = 0.0;
+                for (int r = tid; r < m; r += 256) s += S[(int64_t)r * nev + a] * S[(int64_t)r * nev + a];
+                red[tid] = s;
+                __syncthreads();
+                for (int w = 128; w > 0; w >>= 1) {
+                    if (tid < w) red[tid] += red[tid + w];
+                    __syncthreads();
+                }
+                const double inv = 1.0 / sqrt(red[0]);
+                __syncthreads();
+                for (int r = tid; r < m; r += 256) S[(int64_t)r * nev + a] *= inv;
+                __syncthreads();
+            }
+        }
+        // tmp = T * S_group
+        for (int r = tid; r < m; r += 256) {
+            for (int a = a0; a < a1; ++a) {
+                double t = 0.0;
+                for (int c = max(0, r - p); c <= min(m - 1, r + p); ++c) t += band_get(Tb, p, m, r, c) * S[(int64_t)c * nev + a];
+                tmp[(int64_t)r * nev + a] = t;
+            }
+        }
+        __syncthreads();
+        // K = S_g^T T S_g
+        for (int e = 0; e < k * k; ++e) {
+            const int a = a0 + e / k, q = a0 + e % k;
+            double s = 0.0;
+            for (int r = tid; r < m; r += 256) s += S[(int64_t)r * nev + a] * tmp[(int64_t)r * nev + q];
+            red[tid] = s;
+            __syncthreads();
+            for (int w = 128; w > 0; w >>= 1) {
+                if (tid < w) red[tid] += red[tid + w];
+                __syncthreads();
+            }
+            if (tid == 0) K[e] = red[0];
+            __syncthreads();
+        }
+        // cyclic Jacobi on K (thread 0; k <= 64)
+        if (tid == 0) {
+            for (int e = 0; e < k * k; ++e) Z[e] = (e / k == e % k) ? 1.0 : 0.0;
+            for (int a = 0; a < k; ++a)
+                for (int q = a + 1; q < k; ++q) {
+                    const double s = 0.5 * (K[a * k + q] + K[q * k + a]);
+                    K[a * k + q] = K[q * k + a] = s;
+                }
+            for (int sweep = 0; sweep < 50; ++sweep) {
+                double off = 0.0;
+                for (int a = 0; a < k; ++a)
+                    for (int q = a + 1; q < k; ++q) off += K[a * k + q] * K[a * k + q];
+                if (off < 1e-32 * s_scale * s_scale) break;
+                for (int a = 0; a < k; ++a)
+                    for (int q = a + 1; q < k; ++q) {
+                        const double apq = K[a * k + q];
+                        if (fabs(apq) < 1e-300) continue;
+                        const double tau = (K[q * k + q] - K[a * k + a]) / (2.0 * apq);
+                        const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                        for (int r = 0; r < k; ++r) {
+                            const double kra = K[r * k + a], krq = K[r * k + q];
+                            K[r * k + a] = c * kra - s * krq;
+                            K[r * k + q] = s * kra + c * krq;
+                        }
+                        for (int r = 0; r < k; ++r) {
+                            const double kar = K[a * k + r], kqr = K[q * k + r];
+                            K[a * k + r] = c * kar - s * kqr;
+                            K[q * k + r] = s * kar + c * kqr;
+                        }
+                        for (int r = 0; r < k; ++r) {
+                            const double zra = Z[r * k + a], zrq = Z[r * k + q];
+                            Z[r * k + a] = c * zra - s * zrq;
+                            Z[r * k + q] = s * zra + c * zrq;
+                        }
+                    }
+            }
+            // sort eigenpairs of K ascending
+            for (int a = 0; a < k; ++a) {
+                int best = a;
+                for (int q = a + 1; q < k; ++q)
+                    if (K[q * k + q] < K[best * k + best]) best = q;
+                if (best != a) {
+                    const double t = K[a * k + a];
+                    K[a * k + a] = K[best * k + best];
+                    K[best * k + best] = t;
+                    for (int r = 0; r < k; ++r) {
+                        const double z = Z[r * k + a];
+                        Z[r * k + a] = Z[r * k + best];
+                        Z[r * k + best] = z;
+                    }
+                }
+            }
+            for (int a = 0; a < k; ++a) th[a0 + a] = K[a * k + a];
+        }
+        __syncthreads();
+        // S_g <- S_g Z
+        for (int r = tid; r < m; r += 256) {
+            double row[kMaxNev];
+            for (int a = 0; a < k; ++a) row[a] = S[(int64_t)r * nev + a0 + a];
+            for (int a = 0; a < k; ++a) {
+                double s = 0.0;
+                for (int q = 0; q < k; ++q) s += row[q] * Z[q * k + a];
+                S[(int64_t)r * nev + a0 + a] = s;
+            }
+        }
+        __syncthreads();
+    }
+    // sign convention: the first entry of largest magnitude is positive
+    for (int a = 0; a < nev; ++a) {
+        double best = -1.0;
+        int bi = 0;
+        for (int r = tid; r < m; r += 256) {
+            const double v = fabs(S[(int64_t)r * nev + a]);
+            if (v > best) {
+                best = v;
+                bi = r;
+            }
+        }
+        __shared__ double bv[256];
+        __shared__ int bix[256];
+        bv[tid] = best;
+        bix[tid] = bi;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (tid < w) {
+                if (bv[tid + w] > bv[tid] || (bv[tid + w] == bv[tid] && bix[tid + w] < bix[tid])) {
+                    bv[tid] = bv[tid + w];
+                    bix[tid] = bix[tid + w];
+                }
+            }
+            __syncthreads();
+        }
+        const bool flip = S[(int64_t)bix[0] * nev + a] < 0.0;
+        __syncthreads();
+        if (flip)
+            for (int r = tid; r < m; r += 256) S[(int64_t)r * nev + a] = -S[(int64_t)r * nev + a];
+        __syncthreads();
+    }
+    for (int k = tid; k < nev; k += 256) theta[k] = th[k];
+}
+
+}  // namespace
+
+size_t ritz_workspace_bytes(int m, int p, int nev) {
+    return sizeof(double) * ((size_t)nev * m * (3 * p + 1) + (size_t)m * nev + 2 * (size_t)nev) +
+           sizeof(int) * (size_t)nev * m + 256;
+}
+
+bbl_status ritz_dev(int m, int p, int nev, const double* Tb, double* theta, double* S, DevBuf& work, cudaStream_t st) {
+    const size_t need = ritz_workspace_bytes(m, p, nev);
+    if (work.bytes < need) BBL_TRY(work.alloc(need + need / 2));
+    double* ws = work.as<double>();
+    double* width = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + sizeof(double) * (size_t)nev * m * (3 * p + 1) +
+                                      sizeof(int) * (size_t)nev * m + 64);
+    width = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(width) + 15) & ~uintptr_t(15));
+    double* tmp = width + nev + 2;
+    bisect_kernel<<<nev, 32 * kBisectWarps, 0, st>>>(m, p, nev, Tb, theta, width);
+    BBL_LAUNCH_CHECK();
+    const size_t smem = sizeof(double) * ((size_t)(p + 1) * (2 * p + 1) + m + p + 8);
+    if (smem > 48 * 1024) {
+        BBL_CUDA(cudaFuncSetAttribute(invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    invit_kernel<<<nev, 32, smem, st>>>(m, p, Tb, theta, S, nev, ws, 0.0);
+    BBL_LAUNCH_CHECK();
+    cluster_kernel<<<1, 256, 0, st>>>(m, p, nev, Tb, theta, S, tmp);
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
+}
+
+}  // namespace bbl
+
+extern "C" bbl_status bbl_ritz_banded(int m, int p, int nev, const double* Tband, double* theta, double* S,
+                                      void* stream) {
+    using namespace bbl;
+    if (m < 1 || p < 0 || p > kMaxP || nev < 1 || nev > m || nev > kMaxNev || !Tband || !theta || !S)
+        return set_error(BBL_ERR_INVALID_ARG, "ritz_banded: bad arguments (m=%d p=%d nev=%d)", m, p, nev);
+    if (m > 16384) return set_error(BBL_ERR_UNSUPPORTED, "ritz_banded: m=%d above 16384", m);
+    cudaStream_t st = as_stream(stream);
+    DevBuf work;
+    BBL_TRY(ritz_dev(m, p, nev, Tband, theta, S, work, st));
+    BBL_CUDA(cudaStreamSynchronize(st));
+    return BBL_OK;
+}

@@ -1,0 +1,515 @@
+// bbl_solve: host orchestration of the block Lanczos iteration (Sec. II.B).
+//
+// Per block iteration j (all device work on the caller's stream, one small
+// device->host read of the Ritz report per checked iteration):
+//   S1  W = H V_j                                   (spmm.cu)
+//   S2  C1 = Q^T W, W -= Q C1;  A_j = sym(C1[j]);    (block.cu; Q = [V_0..V_j])
+//       C2 = Q^T W, W -= Q C2                       (second Gram-Schmidt pass)
+//   S3  V_{j+1} R2 R1 = W (CholQR2), B_j = R2 R1     (block.cu)
+//   S4  T_j (Eq. 12) -> theta, S; estimates ||B_j S[last b, i]||   (ritz.cu)
+// then X = Q S and the FP64 residuals ||H x_i - theta_i x_i||.
+//
+// The first Gram-Schmidt pass subsumes the paper's subtraction of V_n A_n
+// and V_{n-1} B_{n-1}^T (Eq. 8 with the Eq. 6 term): its coefficients for
+// blocks j and j-1 are exactly those in exact arithmetic.
+//
+// Mixed precision (FP32 storage): stage 1 runs the same loop on FP32
+// blocks with FP32 SpMM and FP64 coefficients / Gram / T / residual, to
+// stage1_tol; stage 2 ("polish") restarts FP64 block Lanczos from the stage-1
+// Ritz vectors -- the bootstrapping idea of Sec. II.B applied across
+// precisions -- until the FP64 residuals meet tol.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace bbl {
+
+size_t ritz_workspace_bytes(int m, int p, int nev);
+
+namespace {
+
+template <typename TI, typename TO>
+__global__ void convert_kernel(int64_t count, const TI* __restrict__ in, TO* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = (TO)in[e];
+}
+
+// A_j = sym(C1[j-block]) into the lower band of T
+__global__ void fill_A_kernel(int j, int b, const double* __restrict__ C1, double* __restrict__ Tb) {
+    const int e = threadIdx.x;
+    if (e >= b * b) return;
+    const int r = e / b, c = e % b;
+    if (c > r) return;
+    const int jb = j * b;
+    const double v = 0.5 * (C1[(int64_t)(jb + r) * b + c] + C1[(int64_t)(jb + c) * b + r]);
+    Tb[(int64_t)(jb + r) * (b + 1) + (r - c)] = v;
+}
+
+// B_j (upper triangular) into block (j+1, j) of T
+__global__ void fill_B_kernel(int j, int b, int rows_alloc, const double* __restrict__ Bj, double* __restrict__ Tb) {
+    const int e = threadIdx.x;
+    if (e >= b * b) return;
+    const int r = e / b, c = e % b;
+    if (c < r) return;
+    const int row = (j + 1) * b + r;
+    if (row >= rows_alloc) return;
+    Tb[(int64_t)row * (b + 1) + (b + r - c)] = Bj[r * b + c];
+}
+
+// est_i = || B_j S[m-b .. m-1, i] ||_2, written into the report
+__global__ void estimate_kernel(int m, int b, int k, const double* __restrict__ Bj, const double* __restrict__ S,
+                                double* __restrict__ est) {
+    const int i = threadIdx.x;
+    if (i >= k) return;
+    double s2 = 0.0;
+    for (int r = 0; r < b; ++r) {
+        double t = 0.0;
+        for (int c = 0; c < b; ++c) t += Bj[r * b + c] * S[(int64_t)(m - b + c) * k + i];
+        s2 += t * t;
+    }
+    est[i] = sqrt(s2);
+}
+
+// Z[:, c] -> W[:, c] for masked columns
+template <typename T>
+__global__ void merge_cols_kernel(int64_t n, int b, const int* __restrict__ mask, const T* __restrict__ Z,
+                                  T* __restrict__ W) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * b; e += (int64_t)gridDim.x * blockDim.x)
+        if (mask[e % b]) W[e] = Z[e];
+}
+
+// per-CTA partial sums of (Y - X diag(theta))^2 per column, k <= 16
+__global__ void resid_partial_kernel(int64_t n, int k, const double* __restrict__ Y, const double* __restrict__ X,
+                                     const double* __restrict__ theta, double* __restrict__ partial) {
+    __shared__ double red[256];
+    for (int i = 0; i < k; ++i) {
+        double s = 0.0;
+        const double th = theta[i];
+        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+            const double d = Y[r * k + i] - th * X[r * k + i];
+            s += d * d;
+        }
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[blockIdx.x * k + i] = red[0];
+        __syncthreads();
+    }
+}
+
+// per-CTA (max |x|, first index) per column
+__global__ void colmax_partial_kernel(int64_t n, int k, const double* __restrict__ X, double* __restrict__ pv,
+                                      int64_t* __restrict__ pi) {
+    __shared__ double bv[256];
+    __shared__ int64_t bi[256];
+    for (int i = 0; i < k; ++i) {
+        double best = -1.0;
+        int64_t idx = 0;
+        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+            const double v = fabs(X[r * k + i]);
+            if (v > best) {
+                best = v;
+                idx = r;
+            }
+        }
+        bv[threadIdx.x] = best;
+        bi[threadIdx.x] = idx;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (threadIdx.x < w) {
+                if (bv[threadIdx.x + w] > bv[threadIdx.x] ||
+                    (bv[threadIdx.x + w] == bv[threadIdx.x] && bi[threadIdx.x + w] < bi[threadIdx.x])) {
+                    bv[threadIdx.x] = bv[threadIdx.x + w];
+                    bi[threadIdx.x] = bi[threadIdx.x + w];
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            pv[blockIdx.x * k + i] = bv[0];
+            pi[blockIdx.x * k + i] = bi[0];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void scale_cols_kernel(int64_t n, int k, const double* __restrict__ sgn, double* __restrict__ X) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k; e += (int64_t)gridDim.x * blockDim.x)
+        X[e] *= sgn[e % k];
+}
+
+constexpr int kRedBlocks = 304;
+
+struct Timer {
+    cudaEvent_t ev[6] = {};
+    bool ok = false;
+    bbl_status init() {
+        for (auto& e : ev) BBL_CUDA(cudaEventCreate(&e));
+        ok = true;
+        return BBL_OK;
+    }
+    ~Timer() {
+        if (ok)
+            for (auto& e : ev) cudaEventDestroy(e);
+    }
+    float ms(int a, int b) const {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev[a], ev[b]);
+        return t;
+    }
+};
+
+struct StageOut {
+    std::vector<double> theta, est;
+    int iters = 0, deflations = 0, nev_eff = 0;
+    bool converged = false;
+    double t_spmm = 0, t_reorth = 0, t_chol = 0, t_ritz = 0, t_other = 0;
+};
+
+// Normalise columns of X (FP64, n x k) to the sign convention and compute the
+// true residuals ||H x_i - theta_i x_i||_2 (FP64 SpMM).
+bbl_status finish_vectors(const bbl_matrix* A, int k, double* X, const double* theta_dev, double* resid_host,
+                          DevBuf& scratch, cudaStream_t st) {
+    const int64_t n = A->n;
+    const size_t need = sizeof(double) * (size_t)n * k + (sizeof(double) * 2 + sizeof(int64_t)) * kRedBlocks * k + 256;
+    if (scratch.bytes < need) BBL_TRY(scratch.alloc(need));
+    double* Y = scratch.as<double>();
+    double* pv = Y + (size_t)n * k;
+    int64_t* pi = reinterpret_cast<int64_t*>(pv + (size_t)kRedBlocks * k);
+    double* pr = reinterpret_cast<double*>(pi + (size_t)kRedBlocks * k);
+    colmax_partial_kernel<<<kRedBlocks, 256, 0, st>>>(n, k, X, pv, pi);
+    BBL_LAUNCH_CHECK();
+    std::vector<double> hv((size_t)kRedBlocks * k);
+    std::vector<int64_t> hi((size_t)kRedBlocks * k);
+    BBL_CUDA(cudaMemcpyAsync(hv.data(), pv, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, st));
+    BBL_CUDA(cudaMemcpyAsync(hi.data(), pi, sizeof(int64_t) * hi.size(), cudaMemcpyDeviceToHost, st));
+    BBL_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> sgn(k, 1.0);
+    for (int i = 0; i < k; ++i) {
+        double best = -1.0;
+        int64_t idx = 0;
+        for (int blk = 0; blk < kRedBlocks; ++blk) {
+            const double v = hv[(size_t)blk * k + i];
+            const int64_t j = hi[(size_t)blk * k + i];
+            if (v > best || (v == best && j < idx)) {
+                best = v;
+                idx = j;
+            }
+        }
+        double xv = 0.0;
+        BBL_CUDA(cudaMemcpy(&xv, X + idx * k + i, sizeof(double), cudaMemcpyDeviceToHost));
+        if (xv < 0.0) sgn[i] = -1.0;
+    }
+    BBL_CUDA(cudaMemcpyAsync(pv, sgn.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+    scale_cols_kernel<<<kRedBlocks, 256, 0, st>>>(n, k, pv, X);
+    BBL_LAUNCH_CHECK();
+    if (resid_host) {
+        BBL_TRY(spmm_dispatch(A, k, X, Y, true, st));
+        resid_partial_kernel<<<kRedBlocks, 256, 0, st>>>(n, k, Y, X, theta_dev, pr);
+        BBL_LAUNCH_CHECK();
+        std::vector<double> hp((size_t)kRedBlocks * k);
+        BBL_CUDA(cudaMemcpyAsync(hp.data(), pr, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st));
+        BBL_CUDA(cudaStreamSynchronize(st));
+        for (int i = 0; i < k; ++i) {
+            double s = 0.0;
+            for (int blk = 0; blk < kRedBlocks; ++blk) s += hp[(size_t)blk * k + i];
+            resid_host[i] = std::sqrt(s);
+        }
+    }
+    return BBL_OK;
+}
+
+// One block Lanczos run from an FP64 device pivot (n x b).  dtype: storage of
+// the blocks; f64_spmm: FP64 arithmetic in the SpMM.  On return X (device
+// FP64 n x nev_eff) holds the Ritz vectors, theta_dev the Ritz values.
+bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivot_dev, int dtype, bool f64_spmm,
+                         double tol, const bbl_options& o, cudaStream_t st, double* X, double* theta_dev,
+                         StageOut& out) {
+    const int64_t n = A->n;
+    const size_t s = dtype_size(dtype);
+    const double nrm = A->norm_inf > 0 ? A->norm_inf : 1.0;
+    int J_max = std::max(1, o.max_vectors / b);
+    {
+        size_t freeb = 0, totalb = 0;
+        BBL_CUDA(cudaMemGetInfo(&freeb, &totalb));
+        const size_t per_block = (size_t)n * b * s;
+        const size_t reserve = (size_t)(2ull << 30) + 8 * (size_t)n * b * 8;
+        if (freeb > reserve) {
+            const int fit = (int)std::min<size_t>((freeb - reserve) / per_block, (size_t)1 << 30);
+            J_max = std::max(1, std::min(J_max, fit));
+        }
+    }
+    const int m_max = J_max * b;
+    if (nev > m_max) return set_error(BBL_ERR_INVALID_ARG, "solve: nev=%d exceeds the basis capacity %d", nev, m_max);
+    DevBuf basis, Z, coeff, partials, small, Tb, S, rwork, flags, bj;
+    BBL_TRY(basis.alloc((size_t)J_max * n * b * s));
+    BBL_TRY(Z.alloc((size_t)n * b * s));
+    BBL_TRY(coeff.alloc(sizeof(double) * 2 * (size_t)m_max * b));
+    const int t_rows = m_max + b;
+    BBL_TRY(Tb.alloc(sizeof(double) * (size_t)t_rows * (b + 1)));
+    BBL_TRY(S.alloc(sizeof(double) * (size_t)m_max * nev));
+    BBL_TRY(rwork.alloc(ritz_workspace_bytes(m_max, b, nev) + 1024));
+    BBL_TRY(bj.alloc(sizeof(double) * kMaxB * kMaxB));
+    BBL_TRY(flags.alloc(sizeof(int) * (4 + 2 * kMaxB) + sizeof(double) * 2 * 64));
+    BBL_TRY(small.alloc(sizeof(double) * 8 * kMaxB * kMaxB + sizeof(int) * 4 * kMaxB));
+    BBL_CUDA(cudaMemsetAsync(Tb.p, 0, Tb.bytes, st));
+    BBL_CUDA(cudaMemsetAsync(flags.p, 0, flags.bytes, st));
+    BBL_CUDA(cudaMemsetAsync(small.p, 0, small.bytes, st));
+    int* d_ndefl = flags.as<int>();          // [0] cumulative deflations
+    int* d_mask = d_ndefl + 4;               // [b] deflation mask of the last CholQR2
+    int* d_mask2 = d_mask + kMaxB;
+    double* d_est = reinterpret_cast<double*>(flags.as<char>() + sizeof(int) * (4 + 2 * kMaxB));
+    HostBuf report;
+    BBL_TRY(report.alloc(sizeof(double) * 128 + sizeof(int) * 8));
+    double* h_theta = report.as<double>();
+    double* h_est = h_theta + 64;
+    int* h_ndefl = reinterpret_cast<int*>(h_est + 64);
+
+    auto blockp = [&](int j) -> char* { return basis.as<char>() + (size_t)j * n * b * s; };
+    const unsigned cg = 152 * 8;
+    // pivot -> block 0 in storage precision, orthonormalised (relative deflation)
+    if (dtype == BBL_FP64)
+        BBL_CUDA(cudaMemcpyAsync(blockp(0), pivot_dev, sizeof(double) * n * b, cudaMemcpyDeviceToDevice, st));
+    else
+        convert_kernel<double, float><<<cg, 256, 0, st>>>(n * b, pivot_dev, reinterpret_cast<float*>(blockp(0)));
+    BBL_LAUNCH_CHECK();
+    const double defl_tol = o.defl_tol > 0 ? o.defl_tol : (dtype == BBL_FP64 ? 1e-10 : 1e-6);
+    const double thresh2 = (defl_tol * nrm) * (defl_tol * nrm);
+    uint64_t defl_counter = 0;
+    bool exhausted = false;
+    auto replace_deflated = [&](int nb_basis, char* Wn, const int* mask_dev) -> bbl_status {
+        // random columns where mask is set, orthogonalised against the basis
+        // and the current block, then orthonormalised among themselves
+        BBL_TRY(fill_uniform_cols(n, b, dtype, o.seed ^ 0x5DEECE66Dull, (defl_counter++) * (uint64_t)n * kMaxB, mask_dev,
+                                  Z.p, st));
+        for (int pass = 0; pass < 2; ++pass) {
+            if (nb_basis > 0) {
+                BBL_TRY(gram(n, b, nb_basis, dtype, basis.p, Z.p, coeff.as<double>(), partials, st));
+                BBL_TRY(update(n, b, nb_basis, dtype, basis.p, coeff.as<double>(), Z.p, st));
+            }
+            BBL_TRY(gram(n, b, 1, dtype, Wn, Z.p, coeff.as<double>(), partials, st));
+            BBL_TRY(update(n, b, 1, dtype, Wn, coeff.as<double>(), Z.p, st));
+        }
+        BBL_TRY(cholqr2_dev(n, b, dtype, Z.p, nullptr, -1e-20, nullptr, d_mask2, partials, small, st));
+        // a replacement that is itself dependent means the Krylov space has
+        // exhausted the whole space: the current Ritz pairs are exact
+        int hm[2 * kMaxB];
+        BBL_CUDA(cudaMemcpyAsync(hm, mask_dev, sizeof(int) * b, cudaMemcpyDeviceToHost, st));
+        BBL_CUDA(cudaMemcpyAsync(hm + kMaxB, d_mask2, sizeof(int) * b, cudaMemcpyDeviceToHost, st));
+        BBL_CUDA(cudaStreamSynchronize(st));
+        for (int c = 0; c < b; ++c)
+            if (hm[c] && hm[kMaxB + c]) exhausted = true;
+        if (dtype == BBL_FP64)
+            merge_cols_kernel<double><<<cg, 256, 0, st>>>(n, b, mask_dev, Z.as<double>(), reinterpret_cast<double*>(Wn));
+        else
+            merge_cols_kernel<float><<<cg, 256, 0, st>>>(n, b, mask_dev, Z.as<float>(), reinterpret_cast<float*>(Wn));
+        BBL_LAUNCH_CHECK();
+        return BBL_OK;
+    };
+    BBL_TRY(cholqr2_dev(n, b, dtype, blockp(0), nullptr, -1e-20, d_ndefl + 1, d_mask, partials, small, st));
+    BBL_CUDA(cudaMemcpyAsync(h_ndefl, d_ndefl + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BBL_CUDA(cudaStreamSynchronize(st));
+    if (h_ndefl[0] > 0) BBL_TRY(replace_deflated(0, blockp(0), d_mask));
+
+    Timer tm;
+    BBL_TRY(tm.init());
+    std::vector<double> prev_theta;
+    int last_defl = 0;
+    out.converged = false;
+    int j = 0;
+    for (j = 0; j < J_max; ++j) {
+        char* Vj = blockp(j);
+        char* Wn = (j + 1 < J_max) ? blockp(j + 1) : Z.as<char>();
+        BBL_CUDA(cudaEventRecord(tm.ev[0], st));
+        // W = H V_j is formed directly in the next basis slot and turned into
+        // V_{j+1} there (Gram-Schmidt only reads blocks 0..j)
+        BBL_TRY(spmm_dispatch(A, b, Vj, Wn, f64_spmm, st));
+        BBL_CUDA(cudaEventRecord(tm.ev[1], st));
+        double* C1 = coeff.as<double>();
+        double* C2 = C1 + (size_t)m_max * b;
+        BBL_TRY(gram(n, b, j + 1, dtype, basis.p, Wn, C1, partials, st));
+        BBL_TRY(update(n, b, j + 1, dtype, basis.p, C1, Wn, st));
+        fill_A_kernel<<<1, 256, 0, st>>>(j, b, C1, Tb.as<double>());
+        BBL_LAUNCH_CHECK();
+        BBL_TRY(gram(n, b, j + 1, dtype, basis.p, Wn, C2, partials, st));
+        BBL_TRY(update(n, b, j + 1, dtype, basis.p, C2, Wn, st));
+        BBL_CUDA(cudaEventRecord(tm.ev[2], st));
+        BBL_TRY(cholqr2_dev(n, b, dtype, Wn, bj.as<double>(), thresh2, d_ndefl, d_mask, partials, small, st));
+        fill_B_kernel<<<1, 256, 0, st>>>(j, b, t_rows, bj.as<double>(), Tb.as<double>());
+        BBL_LAUNCH_CHECK();
+        BBL_CUDA(cudaEventRecord(tm.ev[3], st));
+        const int m = (j + 1) * b;
+        const int k = std::min(nev, m);
+        const bool check = ((j + 1) % std::max(1, o.check_every) == 0) || (j == J_max - 1) || k < nev;
+        if (check) {
+            BBL_TRY(ritz_dev(m, b, k, Tb.as<double>(), theta_dev, S.as<double>(), rwork, st));
+            estimate_kernel<<<1, 64, 0, st>>>(m, b, k, bj.as<double>(), S.as<double>(), d_est);
+            BBL_LAUNCH_CHECK();
+            BBL_CUDA(cudaMemcpyAsync(h_theta, theta_dev, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+            BBL_CUDA(cudaMemcpyAsync(h_est, d_est, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        }
+        BBL_CUDA(cudaMemcpyAsync(h_ndefl, d_ndefl, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BBL_CUDA(cudaEventRecord(tm.ev[4], st));
+        BBL_CUDA(cudaStreamSynchronize(st));
+        out.t_spmm += tm.ms(0, 1);
+        out.t_reorth += tm.ms(1, 2);
+        out.t_chol += tm.ms(2, 3);
+        out.t_ritz += tm.ms(3, 4);
+        out.iters = j + 1;
+        out.nev_eff = k;
+        bool done = false;
+        if (check) {
+            for (int i = 0; i < k; ++i)
+                if (!std::isfinite(h_theta[i]) || !std::isfinite(h_est[i]))
+                    return set_error(BBL_ERR_NUMERICAL, "solve: non-finite Ritz value at block %d", j);
+            out.theta.assign(h_theta, h_theta + k);
+            out.est.assign(h_est, h_est + k);
+            if (k == nev) {
+                if (o.criterion == 1) {
+                    if (prev_theta.size() == (size_t)nev) {
+                        double ss = 0.0;
+                        for (int i = 0; i < nev; ++i) ss += (h_theta[i] - prev_theta[i]) * (h_theta[i] - prev_theta[i]);
+                        done = std::sqrt(ss / nev) < o.rms_tol;
+                    }
+                } else {
+                    done = true;
+                    for (int i = 0; i < nev; ++i) done = done && (h_est[i] <= tol * nrm);
+                }
+            }
+            prev_theta.assign(h_theta, h_theta + k);
+        }
+        if (done) {
+            out.converged = true;
+            break;
+        }
+        if (j == J_max - 1) break;
+        if (h_ndefl[0] > last_defl) {
+            BBL_TRY(replace_deflated(j + 1, Wn, d_mask));
+            last_defl = h_ndefl[0];
+            if (exhausted) break;  // no direction left to extend the basis with
+        }
+    }
+    out.deflations = last_defl;
+    // Ritz vectors X = Q S (k columns)
+    const int nb = out.iters;
+    const int k = out.nev_eff;
+    BBL_CUDA(cudaEventRecord(tm.ev[0], st));
+    BBL_TRY(ritz_vectors(n, b, nb, dtype, basis.p, k, S.as<double>(), X, st));
+    BBL_CUDA(cudaEventRecord(tm.ev[1], st));
+    BBL_CUDA(cudaStreamSynchronize(st));
+    out.t_other += tm.ms(0, 1);
+    return BBL_OK;
+}
+
+bbl_status solve_impl(const bbl_matrix* A, int nev, int b, const double* pivot, const bbl_options* opt, double* evals,
+                      double* evecs, double* resid, bbl_stats* stats) {
+    if (!A) return set_error(BBL_ERR_INVALID_ARG, "solve: matrix is NULL");
+    if (b < 1 || b > kMaxB) return set_error(BBL_ERR_INVALID_ARG, "solve: b=%d outside 1..16", b);
+    if (nev < 1 || nev > kMaxB) return set_error(BBL_ERR_INVALID_ARG, "solve: nev=%d outside 1..16", nev);
+    if (!evals) return set_error(BBL_ERR_INVALID_ARG, "solve: evals is NULL");
+    bbl_options o;
+    if (opt) o = *opt;
+    else bbl_options_default(&o);
+    if (!(o.tol > 0) || o.max_vectors < b) return set_error(BBL_ERR_INVALID_ARG, "solve: bad tol / max_vectors");
+    if (o.storage != A->storage)
+        return set_error(BBL_ERR_INVALID_ARG, "solve: options.storage (%d) must match the matrix storage (%d)", o.storage,
+                         A->storage);
+    if (o.criterion != 0 && o.criterion != 1) return set_error(BBL_ERR_INVALID_ARG, "solve: bad criterion");
+    cudaStream_t st = as_stream(o.stream);
+    const int64_t n = A->n;
+    if (nev > n || b > n) return set_error(BBL_ERR_INVALID_ARG, "solve: nev or b larger than n");
+    cudaEvent_t t0, t1;
+    BBL_CUDA(cudaEventCreate(&t0));
+    BBL_CUDA(cudaEventCreate(&t1));
+    BBL_CUDA(cudaEventRecord(t0, st));
+    DevBuf piv, X, theta, scratch;
+    BBL_TRY(piv.alloc(sizeof(double) * n * std::max(b, nev)));
+    if (pivot) {
+        BBL_CUDA(cudaMemcpyAsync(piv.p, pivot, sizeof(double) * n * b, cudaMemcpyDefault, st));
+    } else {
+        BBL_TRY(fill_normal(n, b, o.seed, 0, piv.as<double>(), st));
+    }
+    BBL_TRY(X.alloc(sizeof(double) * n * nev));
+    BBL_TRY(theta.alloc(sizeof(double) * 64));
+    StageOut s1, s2;
+    const bool mixed = A->storage == BBL_FP32;
+    bbl_status rc = BBL_OK;
+    std::vector<double> res(nev, 0.0);
+    if (!mixed) {
+        BBL_TRY(lanczos_stage(A, nev, b, piv.as<double>(), BBL_FP64, false, o.tol, o, st, X.as<double>(),
+                              theta.as<double>(), s1));
+    } else {
+        const double t1tol = o.polish ? std::max(o.tol, o.stage1_tol) : o.tol;
+        BBL_TRY(lanczos_stage(A, nev, b, piv.as<double>(), BBL_FP32, false, t1tol, o, st, X.as<double>(),
+                              theta.as<double>(), s1));
+    }
+    int k = s1.nev_eff;
+    BBL_TRY(finish_vectors(A, k, X.as<double>(), theta.as<double>(), res.data(), scratch, st));
+    const double nrm = A->norm_inf > 0 ? A->norm_inf : 1.0;
+    bool ok = s1.converged && k == nev;
+    if (mixed && o.polish) {
+        bool need = false;
+        for (int i = 0; i < k; ++i) need = need || !(res[i] <= o.tol * nrm);
+        if (need || k < nev) {
+            // stage 2: FP64 block Lanczos from the FP32 Ritz vectors (block size nev)
+            BBL_CUDA(cudaMemcpyAsync(piv.p, X.p, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, st));
+            bbl_options o2 = o;
+            o2.criterion = 0;
+            BBL_TRY(lanczos_stage(A, nev, k, piv.as<double>(), BBL_FP64, true, o.tol, o2, st, X.as<double>(),
+                                  theta.as<double>(), s2));
+            k = s2.nev_eff;
+            BBL_TRY(finish_vectors(A, k, X.as<double>(), theta.as<double>(), res.data(), scratch, st));
+            ok = s2.converged && k == nev;
+        } else {
+            ok = true;
+        }
+    }
+    std::vector<double> th(k);
+    BBL_CUDA(cudaMemcpyAsync(th.data(), theta.p, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    if (evecs) BBL_CUDA(cudaMemcpyAsync(evecs, X.p, sizeof(double) * n * k, cudaMemcpyDefault, st));
+    BBL_CUDA(cudaEventRecord(t1, st));
+    BBL_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < k; ++i) evals[i] = th[i];
+    if (resid)
+        for (int i = 0; i < k; ++i) resid[i] = res[i];
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->iters = s1.iters;
+        stats->vec_equiv_iters = s1.iters * b;
+        stats->polish_iters = s2.iters;
+        stats->deflations = s1.deflations + s2.deflations;
+        stats->converged = ok ? 1 : 0;
+        stats->t_spmm_ms = s1.t_spmm + s2.t_spmm;
+        stats->t_reorth_ms = s1.t_reorth + s2.t_reorth;
+        stats->t_cholqr_ms = s1.t_chol + s2.t_chol;
+        stats->t_ritz_ms = s1.t_ritz + s2.t_ritz;
+        stats->t_other_ms = s1.t_other + s2.t_other;
+        float tt = 0.f;
+        cudaEventElapsedTime(&tt, t0, t1);
+        stats->t_total_ms = tt;
+        const double sv = mixed ? 4.0 : 8.0;
+        stats->spmm_bytes = (double)A->nnz * (sv + 4.0) + (double)(n + 1) * 8.0 + 2.0 * (double)n * b * sv;
+        stats->spmm_gbs = s1.t_spmm > 0 ? stats->spmm_bytes * s1.iters / (s1.t_spmm * 1e-3) / 1e9 : 0.0;
+        stats->ns_per_op = s1.t_spmm > 0 ? s1.t_spmm * 1e6 / ((double)A->nnz * b * s1.iters) : 0.0;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (!ok) {
+        set_error(BBL_ERR_NOT_CONVERGED, "solve: basis full before convergence (%d blocks)", s1.iters);
+        rc = BBL_ERR_NOT_CONVERGED;
+    }
+    return rc;
+}
+
+}  // namespace
+}  // namespace bbl
+
+extern "C" bbl_status bbl_solve(const bbl_matrix* A, int nev, int b, const double* pivot, const bbl_options* opt,
+                                double* evals, double* evecs, double* resid, bbl_stats* stats) {
+    return bbl::solve_impl(A, nev, b, pivot, opt, evals, evecs, resid, stats);
+}

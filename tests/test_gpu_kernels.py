@@ -1,0 +1,243 @@
+"""Step-level parity of the CUDA kernels with the oracle, through the C ABI.
+
+Tolerances (FP64): every entry of a product is a sum of at most a few
+hundred terms, so the GPU and the oracle differ only by summation order:
+|W_gpu - W_ref| <= 64 * eps64 * (|H| |V|) entrywise (a bound well above the
+worst-case gamma_k for k <= 2000 terms is not needed here: rows are short).
+FP32 storage: the same bound with eps32 and the FP32-rounded inputs.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import lanczos as OL
+from oracle import rng as OR
+from oracle.spmm import spmm as ospmm
+from tests.gpu_util import abs_bound, need_gpu, principal_angle_sin, to_dev
+
+pytestmark = pytest.mark.gpu
+EPS64 = 2.0 ** -53
+EPS32 = 2.0 ** -24
+
+
+def _mat(kind):
+    if kind == "ragged":
+        # empty rows at the end, a long row (row 0 couples to 300 columns), n not a multiple of 32
+        return synth.random_sparse_symmetric(1037, 7, seed=11, empty_rows=5, long_row=300)
+    if kind == "kron":
+        return synth.kron_matrix("kron_n2e4", scale=0.4)
+    if kind == "lap2d":
+        return synth.laplacian_2d(33, 31)
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kind", ["ragged", "kron", "lap2d"])
+@pytest.mark.parametrize("b", [1, 2, 3, 4, 8, 16])
+def test_spmm_csr_fp64(kind, b):
+    torch, bbl = need_gpu()
+    A = _mat(kind)
+    M = bbl.Matrix(A, storage="fp64")
+    V = np.random.default_rng(b).standard_normal((A.n, b))
+    W = bbl.spmm(M, to_dev(torch, V)).cpu().numpy()
+    ref = ospmm(A, V)
+    assert np.all(np.abs(W - ref) <= 64 * EPS64 * abs_bound(A, V) + 1e-300)
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+def test_spmm_csr_lane_groups(lanes):
+    torch, bbl = need_gpu()
+    A = _mat("ragged")
+    M = bbl.Matrix(A)
+    for b in (1, 4, 8, 16):
+        V = np.random.default_rng(lanes + b).standard_normal((A.n, b))
+        W = bbl.spmm(M, to_dev(torch, V), lanes_per_row=lanes).cpu().numpy()
+        ref = ospmm(A, V)
+        assert np.all(np.abs(W - ref) <= 64 * EPS64 * abs_bound(A, V) + 1e-300)
+
+
+@pytest.mark.parametrize("fmt,sigma", [("csr", 0), ("sell", 32), ("sell", 256), ("sell", 1024)])
+@pytest.mark.parametrize("b", [1, 4, 5, 8, 16])
+def test_spmm_fp32_csr_and_sell(fmt, sigma, b):
+    torch, bbl = need_gpu()
+    A = _mat("ragged")
+    M = bbl.Matrix(A, storage="fp32", fmt=fmt, sell_sigma=sigma)
+    V32 = np.random.default_rng(b).standard_normal((A.n, b)).astype(np.float32)
+    W = bbl.spmm(M, to_dev(torch, V32)).cpu().numpy().astype(np.float64)
+    ref = ospmm(A, V32.astype(np.float64))
+    assert np.all(np.abs(W - ref) <= 64 * EPS32 * abs_bound(A, V32.astype(np.float64)) + 1e-30)
+
+
+@pytest.mark.parametrize("fmt", ["csr", "sell"])
+def test_spmm_f64_arithmetic_on_fp32_storage(fmt):
+    torch, bbl = need_gpu()
+    A = _mat("kron")  # FP32-exact values, so FP64 arithmetic reproduces the FP64 product
+    M = bbl.Matrix(A, storage="fp32", fmt=fmt, sell_sigma=128)
+    V = np.random.default_rng(2).standard_normal((A.n, 8))
+    W = bbl.spmm_f64(M, to_dev(torch, V)).cpu().numpy()
+    assert np.all(np.abs(W - ospmm(A, V)) <= 64 * EPS64 * abs_bound(A, V))
+
+
+def test_sell_padding_and_permutation_accounting():
+    torch, bbl = need_gpu()
+    A = _mat("ragged")
+    M = bbl.Matrix(A, storage="fp32", fmt="sell", sell_sigma=256)
+    assert M.padded_nnz >= A.nnz and M.nnz == A.nnz
+    assert M.norm_inf == pytest.approx(np.abs(A.to_dense()).sum(axis=1).max(), rel=1e-12)
+    np.testing.assert_array_equal(M.diagonal().cpu().numpy(), A.diagonal())
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+@pytest.mark.parametrize("b,nb", [(1, 7), (4, 9), (8, 5), (3, 4), (16, 3)])
+def test_block_reorth_matches_oracle_cgs2(dtype, b, nb):
+    torch, bbl = need_gpu()
+    n = 3001
+    rng = np.random.default_rng(b * 10 + nb)
+    Qf, _ = np.linalg.qr(rng.standard_normal((n, nb * b)))
+    W0 = rng.standard_normal((n, b)) + Qf @ rng.standard_normal((nb * b, b))
+    npdt = np.float64 if dtype == "fp64" else np.float32
+    Qs = Qf.astype(npdt).astype(np.float64)
+    W0s = W0.astype(npdt).astype(np.float64)
+    basis = np.stack([Qs[:, j * b:(j + 1) * b] for j in range(nb)])
+    tdt = torch.float64 if dtype == "fp64" else torch.float32
+    Wd = to_dev(torch, W0s, tdt)
+    coeff = bbl.block_reorth(to_dev(torch, basis, tdt), Wd, passes=2).cpu().numpy()
+    # oracle: the same two classical passes, in FP64
+    c1 = Qs.T @ W0s
+    W1 = W0s - Qs @ c1
+    c2 = Qs.T @ W1
+    W2 = W1 - Qs @ c2
+    if dtype == "fp64":
+        np.testing.assert_allclose(coeff[0], c1, atol=1e-12 * np.abs(c1).max())
+        np.testing.assert_allclose(coeff[1], c2, atol=1e-12 * np.abs(c1).max())
+        np.testing.assert_allclose(Wd.cpu().numpy(), W2, atol=1e-12 * np.abs(W0s).max())
+    else:
+        np.testing.assert_allclose(coeff[0], c1, atol=2e-5 * np.abs(c1).max())
+        Wg = Wd.cpu().numpy().astype(np.float64)
+        # after two passes W is orthogonal to the basis to FP32 accuracy
+        assert np.abs(Qs.T @ Wg).max() <= 1e-5 * np.abs(W0s).max()
+        np.testing.assert_allclose(Wg, W2, atol=2e-5 * np.abs(W0s).max())
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+@pytest.mark.parametrize("b", [1, 2, 4, 6, 8, 16])
+def test_cholqr2_matches_oracle(dtype, b):
+    torch, bbl = need_gpu()
+    n = 4099
+    W = np.random.default_rng(b).standard_normal((n, b)) * np.linspace(1, 3, b)
+    npdt = np.float64 if dtype == "fp64" else np.float32
+    Ws = W.astype(npdt).astype(np.float64)
+    tdt = torch.float64 if dtype == "fp64" else torch.float32
+    Wd = to_dev(torch, Ws, tdt)
+    B, nd = bbl.cholqr2(Wd)
+    Q = Wd.cpu().numpy().astype(np.float64)
+    B = B.cpu().numpy()
+    Qo, Bo, d = OL.cholqr2(Ws, 0.0)
+    assert nd == 0 and not d
+    tol = 1e-12 if dtype == "fp64" else 2e-6
+    np.testing.assert_allclose(B, Bo, atol=tol * np.abs(Bo).max())
+    np.testing.assert_allclose(Q, Qo, atol=tol * 10)
+    assert np.abs(Q.T @ Q - np.eye(b)).max() < (1e-13 if dtype == "fp64" else 2e-6)
+    assert np.allclose(np.tril(B, -1), 0.0)
+
+
+def test_cholqr2_deflates_dependent_column():
+    torch, bbl = need_gpu()
+    n = 2000
+    W = np.random.default_rng(3).standard_normal((n, 4))
+    W[:, 2] = W[:, 0] - 2.0 * W[:, 1]
+    Wd = to_dev(torch, W)
+    B, nd = bbl.cholqr2(Wd, defl_abs=1e-8)
+    Q = Wd.cpu().numpy()
+    B = B.cpu().numpy()
+    assert nd == 1
+    assert np.all(Q[:, 2] == 0.0) and np.all(B[2] == 0.0)
+    keep = [0, 1, 3]
+    assert np.abs(Q[:, keep].T @ Q[:, keep] - np.eye(3)).max() < 1e-13
+    np.testing.assert_allclose(Q @ B, W, atol=1e-10)
+
+
+def _band(T, p):
+    m = T.shape[0]
+    Tb = np.zeros((m, p + 1))
+    for i in range(m):
+        for d in range(p + 1):
+            if i - d >= 0:
+                Tb[i, d] = T[i, i - d]
+    return Tb
+
+
+def _random_band(m, p, seed):
+    rng = np.random.default_rng(seed)
+    T = np.zeros((m, m))
+    for d in range(p + 1):
+        v = rng.standard_normal(m - d)
+        T += np.diag(v, -d)
+        if d:
+            T += np.diag(v, d)
+    return T
+
+
+@pytest.mark.parametrize("m,p,nev", [(8, 4, 4), (64, 1, 5), (200, 4, 8), (333, 8, 8), (512, 16, 12), (1200, 8, 8)])
+def test_ritz_banded_random(m, p, nev):
+    torch, bbl = need_gpu()
+    T = _random_band(m, p, m + p)
+    w, U = np.linalg.eigh(T)
+    th, S = bbl.ritz_banded(to_dev(torch, _band(T, p)), nev)
+    th = th.cpu().numpy()
+    S = S.cpu().numpy()
+    scale = np.abs(w).max()
+    np.testing.assert_allclose(th, w[:nev], atol=1e-12 * scale)
+    assert np.abs(S.T @ S - np.eye(nev)).max() < 1e-10
+    assert np.abs(T @ S - S * th).max() < 1e-10 * scale
+    for i in range(nev):  # sign convention: first largest-magnitude entry positive
+        k = int(np.argmax(np.abs(S[:, i])))
+        assert S[k, i] > 0
+
+
+def test_ritz_banded_degenerate_clusters():
+    # block-diagonal T with repeated blocks: every eigenvalue has multiplicity 3
+    torch, bbl = need_gpu()
+    blk = _random_band(40, 3, 5)
+    T = np.kron(np.eye(3), blk)
+    p = 3
+    w = np.linalg.eigvalsh(T)
+    th, S = bbl.ritz_banded(to_dev(torch, _band(T, p)), 9)
+    th = th.cpu().numpy()
+    S = S.cpu().numpy()
+    np.testing.assert_allclose(th, w[:9], atol=1e-11 * np.abs(w).max())
+    assert np.abs(S.T @ S - np.eye(9)).max() < 1e-9
+    assert np.abs(T @ S - S * th).max() < 1e-9 * np.abs(w).max()
+
+
+def test_ritz_banded_from_lanczos_T_of_2d_laplacian():
+    # the T that the oracle's block Lanczos builds on a 2-D Laplacian (double eigenvalues)
+    torch, bbl = need_gpu()
+    H = synth.laplacian_2d(20, 20)
+    r = OL.block_lanczos(H, 6, 4, OR.normal_block(1, H.n, 4), tol=1e-30, max_vectors=120)
+    T = r.T
+    w = np.linalg.eigvalsh(T)
+    th, S = bbl.ritz_banded(to_dev(torch, _band(T, 4)), 6)
+    np.testing.assert_allclose(th.cpu().numpy(), w[:6], atol=1e-12 * np.abs(w).max())
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+@pytest.mark.parametrize("b,nb,k", [(4, 6, 4), (8, 3, 8), (3, 5, 2), (16, 2, 16), (1, 9, 3)])
+def test_ritz_vectors_match_basis_times_S(dtype, b, nb, k):
+    torch, bbl = need_gpu()
+    n = 2777
+    rng = np.random.default_rng(b + nb + k)
+    npdt = np.float64 if dtype == "fp64" else np.float32
+    Q = rng.standard_normal((nb, n, b)).astype(npdt)
+    S = rng.standard_normal((nb * b, k))
+    tdt = torch.float64 if dtype == "fp64" else torch.float32
+    X = bbl.ritz_vectors(to_dev(torch, Q, tdt), to_dev(torch, S)).cpu().numpy()
+    Qf = np.concatenate([Q[j].astype(np.float64) for j in range(nb)], axis=1)
+    ref = Qf @ S
+    bound = np.abs(Qf) @ np.abs(S)
+    assert np.all(np.abs(X - ref) <= 64 * EPS64 * bound + 1e-300)
+
+
+def test_pivot_random_is_the_published_generator():
+    torch, bbl = need_gpu()
+    P = bbl.pivot_random(1000, 4, seed=77).cpu().numpy()
+    np.testing.assert_allclose(P, OR.normal_block(77, 1000, 4), rtol=1e-13, atol=1e-13)

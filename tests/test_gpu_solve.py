@@ -1,0 +1,213 @@
+"""Whole-solver parity of bbl_solve with the oracle, plus method behaviour.
+
+FP64 tolerance: the nev eigenvalues agree with the oracle's to relative 1e-10
+(both are Ritz values of the same Krylov space, converged to residual
+1e-8*||H||_inf; the Ritz values are then accurate to about
+resid^2/gap, far below 1e-10).  Mixed precision with the FP64 polish must
+meet the same bar; the FP32 stage alone must be within relative 1e-6.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import lanczos as OL
+from oracle import pivot as OP
+from oracle import rng as OR
+from oracle.spmm import norm_inf, spmm as ospmm
+from tests.gpu_util import need_gpu, principal_angle_sin, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_eigs(res, ref_evals, H, tol, rel=1e-10):
+    np.testing.assert_allclose(res.evals, ref_evals, rtol=rel, atol=rel * 1e-3)
+    X = res.evecs.cpu().numpy() if hasattr(res.evecs, "cpu") else res.evecs
+    assert np.abs(X.T @ X - np.eye(X.shape[1])).max() < 1e-8
+    R = ospmm(H, X) - X * res.evals
+    true_res = np.linalg.norm(R, axis=0)
+    assert np.all(true_res <= tol * norm_inf(H) * 1.01)
+    np.testing.assert_allclose(res.resid, true_res, rtol=1e-6, atol=1e-14 * norm_inf(H))
+    return X
+
+
+@pytest.mark.parametrize("b", [1, 2, 4, 8])
+def test_solve_fp64_kron_small_vs_oracle(b):
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4", scale=0.3)  # n = 60 x 30
+    nev = 4
+    piv = OR.normal_block(5, H.n, b)
+    ref = OL.block_lanczos(H, nev, b, piv, tol=1e-8)
+    M = bbl.Matrix(H)
+    res = bbl.solve(M, nev, b, pivot=piv, tol=1e-8)
+    assert res.converged and ref.converged
+    _check_eigs(res, ref.evals, H, 1e-8)
+    assert abs(res.stats["iters"] - ref.iters) <= 1
+    # eigenvectors: same sign convention, same vectors (the spectrum is simple here)
+    X = res.evecs.cpu().numpy()
+    assert np.abs(X - ref.evecs).max() < 1e-6
+
+
+def test_solve_fp64_full_size_config_n2e4_vs_oracle():
+    """The plain FP64 configuration: n = 20,000, ~100 nnz/row, b = 4, nev = 4."""
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4")
+    piv = OR.normal_block(20221028, H.n, 4)
+    ref = OL.block_lanczos(H, 4, 4, piv, tol=1e-8)
+    res = bbl.solve(bbl.Matrix(H), 4, 4, pivot=piv, tol=1e-8)
+    assert res.converged
+    _check_eigs(res, ref.evals, H, 1e-8)
+    assert abs(res.stats["iters"] - ref.iters) <= 1
+
+
+def test_solve_random_pivot_null_uses_the_published_generator():
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4", scale=0.3)
+    ref = OL.block_lanczos(H, 4, 4, OP.random_pivot(H.n, 4, 99), tol=1e-8)
+    res = bbl.solve(bbl.Matrix(H), 4, 4, pivot=None, seed=99, tol=1e-8)
+    _check_eigs(res, ref.evals, H, 1e-8)
+    assert abs(res.stats["iters"] - ref.iters) <= 1
+
+
+def test_solve_laplacian_1d_closed_form_b1():
+    torch, bbl = need_gpu()
+    n = 300
+    H = synth.laplacian_1d(n)
+    k = np.arange(1, n + 1)
+    want = np.sort(2 - 2 * np.cos(k * np.pi / (n + 1)))[:3]
+    res = bbl.solve(bbl.Matrix(H), 3, 1, pivot=OR.normal_block(1, n, 1), tol=1e-10, max_vectors=n)
+    assert res.converged
+    np.testing.assert_allclose(res.evals, want, rtol=1e-10)
+
+
+def test_solve_laplacian_2d_multiplicities():
+    torch, bbl = need_gpu()
+    nx = 24
+    H = synth.laplacian_2d(nx, nx)
+    e1 = np.sort(2 - 2 * np.cos(np.arange(1, nx + 1) * np.pi / (nx + 1)))
+    want = np.sort((e1[:, None] + e1[None, :]).ravel())[:6]
+    res = bbl.solve(bbl.Matrix(H), 6, 4, pivot=OR.normal_block(2, H.n, 4), tol=1e-10)
+    assert res.converged
+    np.testing.assert_allclose(res.evals, want, rtol=1e-10)
+
+
+def test_solve_exact_pivot_converges_in_one_block():
+    torch, bbl = need_gpu()
+    A = synth.random_sparse_symmetric(300, 6, seed=33)
+    w, U = np.linalg.eigh(A.to_dense())
+    res = bbl.solve(bbl.Matrix(A), 4, 4, pivot=U[:, :4].copy(), tol=1e-10)
+    assert res.converged and res.stats["iters"] == 1
+    np.testing.assert_allclose(res.evals, w[:4], rtol=1e-12)
+
+
+def test_solve_symmetry_sector_pivot_misses_the_odd_ground_state():
+    import scipy.sparse as sp
+    torch, bbl = need_gpu()
+    n = 120
+    A = synth.random_sparse_symmetric(n, 6, seed=5).to_scipy()
+    J = sp.csr_matrix((np.ones(n), (np.arange(n), np.arange(n)[::-1])), shape=(n, n))
+    H = synth.csr_from_scipy(A + J @ A @ J)
+    w, U = np.linalg.eigh(H.to_dense())
+    parity = np.sign(np.sum(U * U[::-1], axis=0))
+    p = OR.normal_block(3, n, 2)
+    even = 0.5 * (p + p[::-1])
+    res = bbl.solve(bbl.Matrix(H), 3, 2, pivot=even, tol=1e-9, max_vectors=60)
+    np.testing.assert_allclose(res.evals, w[parity > 0][:3], rtol=1e-9)
+
+
+@pytest.mark.parametrize("fmt", ["csr", "sell"])
+def test_solve_mixed_precision_with_polish_matches_fp64_oracle(fmt):
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4", scale=0.5)
+    piv = OR.normal_block(7, H.n, 8)
+    ref = OL.block_lanczos(H, 8, 8, piv, tol=1e-8)
+    M = bbl.Matrix(H, storage="fp32", fmt=fmt, sell_sigma=256)
+    res = bbl.solve(M, 8, 8, pivot=piv, tol=1e-8)
+    assert res.converged
+    _check_eigs(res, ref.evals, H, 1e-8)
+    assert res.stats["polish_iters"] >= 1
+
+
+def test_solve_mixed_precision_stage1_error_below_1e6():
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4", scale=0.5)
+    piv = OR.normal_block(7, H.n, 8)
+    ref = OL.block_lanczos(H, 8, 8, piv, tol=1e-8)
+    M = bbl.Matrix(H, storage="fp32", fmt="sell", sell_sigma=256)
+    res = bbl.solve(M, 8, 8, pivot=piv, tol=2e-6, polish=0)
+    rel = np.abs(res.evals - ref.evals) / np.abs(ref.evals)
+    assert rel.max() <= 1e-6, rel
+
+
+def test_bootstrap_pivot_matches_oracle_subspace():
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4", scale=0.4)
+    trunc = 600
+    Po, S, th = OP.bootstrap_pivot(H, trunc, 4)
+    M = bbl.Matrix(H)
+    Pg = bbl.pivot_bootstrap(M, trunc, 4, sub_tol=1e-11).cpu().numpy()
+    # same support, same (orthonormal) subspace
+    assert set(np.nonzero(np.abs(Pg).sum(axis=1))[0]) <= set(S.tolist())
+    Qg, _ = np.linalg.qr(Pg)
+    assert principal_angle_sin(Qg, Po) < 1e-6
+
+
+def test_bootstrap_pivot_full_space_gives_one_block():
+    torch, bbl = need_gpu()
+    A = synth.random_sparse_symmetric(200, 6, seed=8)
+    M = bbl.Matrix(A)
+    P = bbl.pivot_bootstrap(M, A.n, 4, sub_tol=1e-12)
+    res = bbl.solve(M, 4, 4, pivot=P, tol=1e-9)
+    assert res.converged and res.stats["iters"] == 1
+
+
+def test_bootstrap_small_truncation_pads_random_columns():
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4", scale=0.2)
+    M = bbl.Matrix(H)
+    P = bbl.pivot_bootstrap(M, 2, 4, seed=5).cpu().numpy()
+    S = OP.truncated_set(H.diagonal(), 2)
+    assert np.count_nonzero(P[:, 0]) == 1 and np.count_nonzero(P[:, 1]) == 1
+    assert set(np.nonzero(P[:, :2])[0]) == set(S.tolist())
+    np.testing.assert_allclose(P[:, 2:], OR.normal_block(5, H.n, 4)[:, 2:], rtol=1e-13)
+
+
+# ----------------------------------------------------------------- errors
+def test_invalid_csr_is_rejected_before_solving():
+    torch, bbl = need_gpu()
+    A = synth.random_sparse_symmetric(50, 4, seed=1)
+    bad = synth.CSR(A.n, A.row_ptr.copy(), A.col.copy(), A.val.copy())
+    bad.col[3] = 10_000
+    with pytest.raises(bbl.BBLError) as e:
+        bbl.Matrix(bad)
+    assert e.value.status == 1
+    uns = synth.CSR(A.n, A.row_ptr.copy(), A.col.copy(), A.val.copy())
+    r = int(np.argmax(np.diff(A.row_ptr)))
+    s0 = A.row_ptr[r]
+    uns.col[s0], uns.col[s0 + 1] = uns.col[s0 + 1], uns.col[s0]
+    with pytest.raises(bbl.BBLError):
+        bbl.Matrix(uns)
+
+
+def test_asymmetric_matrix_is_detected_when_asked():
+    torch, bbl = need_gpu()
+    A = synth.random_sparse_symmetric(50, 4, seed=1)
+    asym = synth.CSR(A.n, A.row_ptr.copy(), A.col.copy(), A.val.copy())
+    k = int(np.nonzero(A.col != np.repeat(np.arange(A.n), np.diff(A.row_ptr)))[0][0])
+    asym.val[k] += 1.0
+    bbl.Matrix(asym)  # accepted without the check
+    with pytest.raises(bbl.BBLError) as e:
+        bbl.Matrix(asym, check_symmetry=True)
+    assert e.value.status == 2
+
+
+def test_bad_arguments_and_not_converged():
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4", scale=0.3)
+    M = bbl.Matrix(H)
+    with pytest.raises(bbl.BBLError):
+        bbl.solve(M, 4, 17)
+    with pytest.raises(bbl.BBLError):
+        bbl.solve(M, 0, 4)
+    res = bbl.solve(M, 4, 4, pivot=OR.normal_block(5, H.n, 4), tol=1e-12, max_vectors=12)
+    assert res.status == "BBL_ERR_NOT_CONVERGED" and res.stats["iters"] == 3
+    assert np.all(np.isfinite(res.evals)) and np.all(res.resid > 0)
