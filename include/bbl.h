@@ -94,12 +94,17 @@ typedef struct {
     double spmm_gbs;            /* spmm_bytes * iters / t_spmm                     */
     double ns_per_op;           /* t_spmm / (nnz * b * iters)  (Tables I-II)       */
     double ortho_err;           /* max |V^T V - I| over the final basis (if measured) */
+    double spmm_bytes_total;    /* algorithmic bytes of every SpMM of the call     */
+    double reorth_bytes_total;  /* algorithmic bytes of every Gram-Schmidt pass:
+                                   per pass 2*n*m*s + 3*n*b*s (m basis columns)    */
 } bbl_stats;
 
 void bbl_options_default(bbl_options* opt);
 const char* bbl_last_error(void);
 const char* bbl_status_string(bbl_status s);
 int bbl_version(void);
+/* Number of kernels this library has launched in the process so far. */
+uint64_t bbl_kernel_launches(void);
 
 /* ---------------------------------------------------------------- matrix
  * Copies a CSR matrix (host or device arrays) to the device.

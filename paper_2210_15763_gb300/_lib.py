@@ -24,7 +24,8 @@ class Stats(C.Structure):
                 ("converged", C.c_int), ("t_spmm_ms", C.c_double), ("t_reorth_ms", C.c_double),
                 ("t_cholqr_ms", C.c_double), ("t_ritz_ms", C.c_double), ("t_other_ms", C.c_double),
                 ("t_total_ms", C.c_double), ("spmm_bytes", C.c_double), ("spmm_gbs", C.c_double),
-                ("ns_per_op", C.c_double), ("ortho_err", C.c_double)]
+                ("ns_per_op", C.c_double), ("ortho_err", C.c_double), ("spmm_bytes_total", C.c_double),
+                ("reorth_bytes_total", C.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -42,6 +43,7 @@ SIGNATURES = {
     "bbl_last_error": (C.c_char_p, []),
     "bbl_status_string": (C.c_char_p, [ST]),
     "bbl_version": (C.c_int, []),
+    "bbl_kernel_launches": (C.c_uint64, []),
     "bbl_matrix_create": (ST, [I64, I64, P, P, P, I32, I32, I32, I32, I32, I32, P, C.POINTER(P)]),
     "bbl_matrix_destroy": (None, [P]),
     "bbl_matrix_info": (ST, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(D), C.POINTER(I64), C.POINTER(I32),

@@ -1,6 +1,6 @@
 // Error state, option defaults and small ABI helpers.
+#include <atomic>
 #include <cstring>
-#include <mutex>
 
 #include "common.cuh"
 
@@ -19,6 +19,9 @@ bbl_status set_error(bbl_status s, const char* fmt, ...) {
 }
 
 void clear_error() { g_last_error.clear(); }
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 bool is_device_pointer(const void* p) {
     if (!p) return false;
@@ -53,6 +56,8 @@ const char* bbl_status_string(bbl_status s) {
 }
 
 int bbl_version(void) { return 100; }
+
+uint64_t bbl_kernel_launches(void) { return bbl::g_launches.load(); }
 
 void bbl_options_default(bbl_options* o) {
     if (!o) return;

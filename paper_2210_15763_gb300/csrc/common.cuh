@@ -39,7 +39,13 @@ void clear_error();
         if (s_ != BBL_OK) return s_;                                                   \
     } while (0)
 
-#define BBL_LAUNCH_CHECK() BBL_CUDA(cudaGetLastError())
+// Every kernel launch is followed by BBL_LAUNCH_CHECK(), which also counts it.
+void count_launch();
+#define BBL_LAUNCH_CHECK()            \
+    do {                              \
+        ::bbl::count_launch();        \
+        BBL_CUDA(cudaGetLastError()); \
+    } while (0)
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 

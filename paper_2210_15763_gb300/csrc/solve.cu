@@ -169,6 +169,7 @@ struct StageOut {
     int iters = 0, deflations = 0, nev_eff = 0;
     bool converged = false;
     double t_spmm = 0, t_reorth = 0, t_chol = 0, t_ritz = 0, t_other = 0;
+    double spmm_bytes = 0, reorth_bytes = 0;
 };
 
 // Normalise columns of X (FP64, n x k) to the sign convention and compute the
@@ -362,6 +363,12 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         out.t_ritz += tm.ms(3, 4);
         out.iters = j + 1;
         out.nev_eff = k;
+        {
+            const double sx = (double)s;
+            const double sv = (A->storage == BBL_FP64 || (f64_spmm && A->val64.p)) ? 8.0 : 4.0;
+            out.spmm_bytes += (double)A->nnz * (sv + 4.0) + (double)(n + 1) * 8.0 + 2.0 * (double)n * b * sx;
+            out.reorth_bytes += 2.0 * (2.0 * (double)n * m * sx + 3.0 * (double)n * b * sx);
+        }
         bool done = false;
         if (check) {
             for (int i = 0; i < k; ++i)
@@ -496,6 +503,8 @@ bbl_status solve_impl(const bbl_matrix* A, int nev, int b, const double* pivot, 
         stats->spmm_bytes = (double)A->nnz * (sv + 4.0) + (double)(n + 1) * 8.0 + 2.0 * (double)n * b * sv;
         stats->spmm_gbs = s1.t_spmm > 0 ? stats->spmm_bytes * s1.iters / (s1.t_spmm * 1e-3) / 1e9 : 0.0;
         stats->ns_per_op = s1.t_spmm > 0 ? s1.t_spmm * 1e6 / ((double)A->nnz * b * s1.iters) : 0.0;
+        stats->spmm_bytes_total = s1.spmm_bytes + s2.spmm_bytes;
+        stats->reorth_bytes_total = s1.reorth_bytes + s2.reorth_bytes;
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
