@@ -149,6 +149,12 @@ bbl_status bbl_spmm_f64(const bbl_matrix* A, int b, const double* V, double* W, 
 bbl_status bbl_block_reorth(int64_t n, int b, int nblocks, bbl_dtype dtype, const void* basis, void* W,
                             double* coeff, int passes, void* stream);
 
+/* C = Q^T W (FP64, m x b row-major, device) without modifying W: the Gram
+ * step of the reorthogonalisation alone (also used for the learned pivot's
+ * training targets U^T X).  Layouts as in bbl_block_reorth.              */
+bbl_status bbl_block_gram(int64_t n, int b, int nblocks, bbl_dtype dtype, const void* basis, const void* W,
+                          double* C, void* stream);
+
 /* ---------------------------------------------------------------- S3: CholQR2
  * W = Q B with Q orthonormal (overwrites W), B upper triangular b x b:
  * G1 = W^T W, R1 = chol(G1), W <- W R1^{-1}, G2, R2, W <- W R2^{-1}, B = R2 R1.
@@ -191,6 +197,44 @@ bbl_status bbl_pivot_random(int64_t n, int b, uint64_t seed, double* P, void* st
  * row-major).  If b > trunc_dim the remaining columns are random.       */
 bbl_status bbl_pivot_bootstrap(const bbl_matrix* A, int64_t trunc_dim, int b, double sub_tol, uint64_t seed,
                                double* P, void* stream);
+
+/* Rayleigh-Ritz on the span of a pivot block P (host or device FP64 n x b):
+ * Q = orth(P), the b Ritz values of Q^T H Q (theta, host, ascending) and the
+ * residual norms ||H Q s_i - theta_i Q s_i||_2 (resid, host).  This is the
+ * cheap one-SpMM judge used to choose between a learned and a bootstrapped
+ * pivot (the paper's Sec. II.B condition: the pivot must overlap the wanted
+ * eigenvectors).                                                          */
+bbl_status bbl_pivot_rr_residual(const bbl_matrix* A, int b, const double* P, double* theta, double* resid,
+                                 void* stream);
+
+/* ---------------------------------------------------------------- learned pivot (MLP)
+ * A small network g -> y = f(g) (1 -> H -> H -> O, exact-erf GELU), FP32
+ * master weights used in BF16, FP32 activations and accumulation, MSE loss,
+ * Adam; no counterpart in the paper (a proposal step in front of the
+ * bootstrapped pivot).  Parameters are packed FP32:
+ *   W1[H] b1[H] W2[H*H] b2[H] W3[O*H] b3[O]   (matrices row-major out x in).
+ * g, target, y: device FP32 (batch, batch x O, batch x O).                */
+typedef struct bbl_mlp bbl_mlp;
+bbl_status bbl_mlp_create(int hidden, int out_dim, bbl_mlp** out);
+void bbl_mlp_destroy(bbl_mlp* M);
+int bbl_mlp_num_params(const bbl_mlp* M);
+/* host or device packed parameters; resets the Adam state */
+bbl_status bbl_mlp_set_params(bbl_mlp* M, const float* packed, void* stream);
+/* parameters and/or the last gradients (host or device; either may be NULL) */
+bbl_status bbl_mlp_get_params(const bbl_mlp* M, float* packed, float* grads, void* stream);
+bbl_status bbl_mlp_forward(bbl_mlp* M, int batch, const float* g, float* y, void* stream);
+/* forward + MSE loss (host) + backward into the internal gradient buffer */
+bbl_status bbl_mlp_loss_grad(bbl_mlp* M, int batch, const float* g, const float* target, float* loss, void* stream);
+/* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) from the stored gradients */
+bbl_status bbl_mlp_adam_step(bbl_mlp* M, float lr, void* stream);
+/* `epochs` full-batch steps (one CUDA graph per epoch); loss_hist host [epochs] or NULL */
+bbl_status bbl_mlp_train(bbl_mlp* M, int batch, const float* g, const float* target, int epochs, float lr,
+                         float* loss_hist, void* stream);
+/* P = U C(g): C = f(g) reshaped (nblocks_U*b_U) x b, U device FP32 basis of
+ * nblocks_U row-major n x b_U blocks, P device FP64 n x b.  Requires
+ * nblocks_U * b_U * b == out_dim.                                        */
+bbl_status bbl_pivot_learned(bbl_mlp* M, float g, int64_t n, int b_U, int nblocks_U, const float* U, int b,
+                             double* P, void* stream);
 
 /* ---------------------------------------------------------------- solve
  * Block Lanczos for the nev lowest eigenpairs (Sec. II.B, Eqs. 4-12).

@@ -207,6 +207,90 @@ def pivot_bootstrap(A: Matrix, trunc_dim: int, b: int, sub_tol: float = 1e-10, s
     return P
 
 
+def block_gram(basis, W, stream=None):
+    """C = Q^T W (FP64 m x b) without modifying W."""
+    torch = _torch()
+    nb, n, b = basis.shape
+    C_ = torch.empty((nb * b, b), dtype=torch.float64, device=W.device)
+    _lib.check(_lib.load().bbl_block_gram(n, b, nb, _dtype_code(W.dtype), _ptr(basis), _ptr(W), _ptr(C_),
+                                          _stream(stream)))
+    return C_
+
+
+def pivot_rr_residual(A: Matrix, P, stream=None):
+    """Rayleigh-Ritz values and residual norms of span(P) (the pivot judge)."""
+    b = P.shape[1]
+    th = np.zeros(b)
+    rs = np.zeros(b)
+    if isinstance(P, np.ndarray):
+        P = np.ascontiguousarray(P, dtype=np.float64)
+    _lib.check(A._lib.bbl_pivot_rr_residual(A.handle, b, _ptr(P), _ptr(th), _ptr(rs), _stream(stream)))
+    return th, rs
+
+
+class MLP:
+    """The learned-pivot network (bbl_mlp): 1 -> hidden -> hidden -> out."""
+
+    def __init__(self, hidden: int, out_dim: int):
+        self._lib = _lib.load()
+        h = C.c_void_p()
+        _lib.check(self._lib.bbl_mlp_create(hidden, out_dim, C.byref(h)))
+        self.handle = h
+        self.hidden, self.out = hidden, out_dim
+        self.nparams = self._lib.bbl_mlp_num_params(h)
+
+    def set_params(self, packed, stream=None):
+        packed = np.ascontiguousarray(packed, dtype=np.float32) if isinstance(packed, np.ndarray) else packed
+        _lib.check(self._lib.bbl_mlp_set_params(self.handle, _ptr(packed), _stream(stream)))
+
+    def get_params(self, stream=None):
+        p = np.zeros(self.nparams, dtype=np.float32)
+        g = np.zeros(self.nparams, dtype=np.float32)
+        _lib.check(self._lib.bbl_mlp_get_params(self.handle, _ptr(p), _ptr(g), _stream(stream)))
+        return p, g
+
+    def forward(self, g, stream=None):
+        torch = _torch()
+        y = torch.empty((g.shape[0], self.out), dtype=torch.float32, device="cuda")
+        _lib.check(self._lib.bbl_mlp_forward(self.handle, g.shape[0], _ptr(g), _ptr(y), _stream(stream)))
+        return y
+
+    def loss_grad(self, g, target, stream=None):
+        loss = C.c_float()
+        _lib.check(self._lib.bbl_mlp_loss_grad(self.handle, g.shape[0], _ptr(g), _ptr(target), C.byref(loss),
+                                               _stream(stream)))
+        return loss.value
+
+    def adam_step(self, lr: float, stream=None):
+        _lib.check(self._lib.bbl_mlp_adam_step(self.handle, float(lr), _stream(stream)))
+
+    def train(self, g, target, epochs: int, lr: float, stream=None):
+        hist = np.zeros(max(epochs, 1), dtype=np.float32)
+        _lib.check(self._lib.bbl_mlp_train(self.handle, g.shape[0], _ptr(g), _ptr(target), int(epochs), float(lr),
+                                           _ptr(hist), _stream(stream)))
+        return hist[:epochs]
+
+    def pivot(self, g: float, U, b: int, stream=None):
+        """P = U C(g); U: (nblocks, n, bU) FP32 CUDA tensor."""
+        torch = _torch()
+        nbU, n, bU = U.shape
+        P = torch.empty((n, b), dtype=torch.float64, device="cuda")
+        _lib.check(self._lib.bbl_pivot_learned(self.handle, float(g), n, bU, nbU, _ptr(U), b, _ptr(P),
+                                               _stream(stream)))
+        return P
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.bbl_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 @dataclasses.dataclass
 class SolveResult:
     evals: np.ndarray

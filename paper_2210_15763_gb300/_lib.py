@@ -59,6 +59,18 @@ SIGNATURES = {
     "bbl_pivot_random": (ST, [I64, I32, C.c_uint64, P, P]),
     "bbl_pivot_bootstrap": (ST, [P, I64, I32, D, C.c_uint64, P, P]),
     "bbl_solve": (ST, [P, I32, I32, P, C.POINTER(Options), P, P, P, C.POINTER(Stats)]),
+    "bbl_block_gram": (ST, [I64, I32, I32, I32, P, P, P, P]),
+    "bbl_pivot_rr_residual": (ST, [P, I32, P, P, P, P]),
+    "bbl_mlp_create": (ST, [I32, I32, C.POINTER(P)]),
+    "bbl_mlp_destroy": (None, [P]),
+    "bbl_mlp_num_params": (C.c_int, [P]),
+    "bbl_mlp_set_params": (ST, [P, P, P]),
+    "bbl_mlp_get_params": (ST, [P, P, P, P]),
+    "bbl_mlp_forward": (ST, [P, I32, P, P, P]),
+    "bbl_mlp_loss_grad": (ST, [P, I32, P, P, C.POINTER(C.c_float), P]),
+    "bbl_mlp_adam_step": (ST, [P, C.c_float, P]),
+    "bbl_mlp_train": (ST, [P, I32, P, P, I32, C.c_float, P, P]),
+    "bbl_pivot_learned": (ST, [P, C.c_float, I64, I32, I32, P, I32, P, P]),
 }
 
 _lib = None

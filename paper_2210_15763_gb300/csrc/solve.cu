@@ -522,3 +522,78 @@ extern "C" bbl_status bbl_solve(const bbl_matrix* A, int nev, int b, const doubl
                                 double* evals, double* evecs, double* resid, bbl_stats* stats) {
     return bbl::solve_impl(A, nev, b, pivot, opt, evals, evecs, resid, stats);
 }
+
+namespace bbl {
+namespace {
+// dense symmetric b x b (row-major) -> lower band storage with p = b - 1
+__global__ void dense_to_band_kernel(int b, const double* __restrict__ G, double* __restrict__ Tb) {
+    const int e = threadIdx.x;
+    if (e >= b * b) return;
+    const int r = e / b, c = e % b;
+    if (c > r) return;
+    Tb[r * b + (r - c)] = 0.5 * (G[r * b + c] + G[c * b + r]);
+}
+}  // namespace
+}  // namespace bbl
+
+// Rayleigh-Ritz on the span of a pivot block: Q = orth(P), T = Q^T H Q,
+// theta, S = eig(T), residuals ||H Q s_i - theta_i Q s_i||_2 (FP64).
+extern "C" bbl_status bbl_pivot_rr_residual(const bbl_matrix* A, int b, const double* P, double* theta_out,
+                                            double* resid_out, void* stream) {
+    using namespace bbl;
+    if (!A || !P || !theta_out || !resid_out || b < 1 || b > kMaxB || b > A->n)
+        return set_error(BBL_ERR_INVALID_ARG, "pivot_rr_residual: bad arguments");
+    cudaStream_t st = as_stream(stream);
+    const int64_t n = A->n;
+    DevBuf Q, W, G, Tb, th, S, X, Y, partials, small, rwork, scratch;
+    BBL_TRY(Q.alloc(sizeof(double) * n * b));
+    BBL_TRY(W.alloc(sizeof(double) * n * b));
+    BBL_TRY(X.alloc(sizeof(double) * n * b));
+    BBL_TRY(Y.alloc(sizeof(double) * n * b));
+    BBL_TRY(G.alloc(sizeof(double) * b * b));
+    BBL_TRY(Tb.alloc(sizeof(double) * b * b));
+    BBL_TRY(th.alloc(sizeof(double) * 64));
+    BBL_TRY(S.alloc(sizeof(double) * b * b));
+    BBL_TRY(small.alloc(sizeof(double) * 8 * kMaxB * kMaxB + sizeof(int) * 4 * kMaxB));
+    BBL_CUDA(cudaMemsetAsync(small.p, 0, small.bytes, st));
+    BBL_CUDA(cudaMemsetAsync(Tb.p, 0, Tb.bytes, st));
+    BBL_CUDA(cudaMemcpyAsync(Q.p, P, sizeof(double) * n * b, cudaMemcpyDefault, st));
+    BBL_TRY(cholqr2_dev(n, b, BBL_FP64, Q.p, nullptr, -1e-20, nullptr, nullptr, partials, small, st));
+    BBL_TRY(spmm_dispatch(A, b, Q.p, W.p, true, st));
+    BBL_TRY(gram(n, b, 1, BBL_FP64, Q.p, W.p, G.as<double>(), partials, st));
+    dense_to_band_kernel<<<1, 256, 0, st>>>(b, G.as<double>(), Tb.as<double>());
+    BBL_LAUNCH_CHECK();
+    BBL_TRY(ritz_dev(b, b - 1, b, Tb.as<double>(), th.as<double>(), S.as<double>(), rwork, st));
+    BBL_TRY(ritz_vectors(n, b, 1, BBL_FP64, Q.p, b, S.as<double>(), X.as<double>(), st));
+    BBL_TRY(ritz_vectors(n, b, 1, BBL_FP64, W.p, b, S.as<double>(), Y.as<double>(), st));
+    const size_t need = sizeof(double) * (size_t)kRedBlocks * b;
+    BBL_TRY(scratch.alloc(need));
+    resid_partial_kernel<<<kRedBlocks, 256, 0, st>>>(n, b, Y.as<double>(), X.as<double>(), th.as<double>(),
+                                                      scratch.as<double>());
+    BBL_LAUNCH_CHECK();
+    std::vector<double> hp((size_t)kRedBlocks * b);
+    BBL_CUDA(cudaMemcpyAsync(hp.data(), scratch.p, need, cudaMemcpyDeviceToHost, st));
+    BBL_CUDA(cudaMemcpyAsync(theta_out, th.p, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
+    BBL_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < b; ++i) {
+        double s = 0.0;
+        for (int blk = 0; blk < kRedBlocks; ++blk) s += hp[(size_t)blk * b + i];
+        resid_out[i] = std::sqrt(s);
+    }
+    return BBL_OK;
+}
+
+// C = Q^T W without modifying W (FP64 coefficients), Q as in bbl_block_reorth.
+extern "C" bbl_status bbl_block_gram(int64_t n, int b, int nblocks, bbl_dtype dtype, const void* basis, const void* W,
+                                     double* C, void* stream) {
+    using namespace bbl;
+    if (n < 1 || b < 1 || b > kMaxB || nblocks < 1 || !basis || !W || !C)
+        return set_error(BBL_ERR_INVALID_ARG, "block_gram: bad arguments");
+    if (dtype != BBL_FP64 && dtype != BBL_FP32) return set_error(BBL_ERR_INVALID_ARG, "block_gram: bad dtype");
+    if (!aligned16(basis) || !aligned16(W)) return set_error(BBL_ERR_INVALID_ARG, "block_gram: pointers must be 16-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    DevBuf partials;
+    BBL_TRY(gram(n, b, nblocks, dtype, basis, W, C, partials, st));
+    BBL_CUDA(cudaStreamSynchronize(st));
+    return BBL_OK;
+}
