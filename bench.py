@@ -307,8 +307,69 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_kernels(args):
+    """Each hot kernel alone on a smaller matrix of the same family (inputs
+    still larger than L2): used for ncu captures and per-kernel bandwidths."""
+    import torch
+    import synth
+    import paper_2210_15763_gb300 as bbl
+    A = synth.kron_matrix(WORKLOAD, scale=args.scale)
+    n = A.n
+    M = bbl.Matrix(A, storage="fp32", fmt="sell", sell_sigma=SELL_SIGMA)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    V = torch.randn(n, B, device="cuda", dtype=torch.float32, generator=g)
+    W = torch.empty_like(V)
+    nb = args.blocks
+    basis = torch.randn(nb, n, B, device="cuda", dtype=torch.float32, generator=g)
+    Wr = torch.randn(n, B, device="cuda", dtype=torch.float32, generator=g)
+
+    def timeit(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"n": n, "nnz": A.nnz, "b": B, "basis_blocks": nb}
+    t = timeit(lambda: bbl.spmm(M, V, W), args.reps)
+    by = A.nnz * 8 + (n + 1) * 8 + 2 * n * B * 4
+    out["spmm_sell_fp32"] = {"ms": t, "GBs": by / t / 1e6}
+    Mc = bbl.Matrix(A, storage="fp32", fmt="csr")
+    t = timeit(lambda: bbl.spmm(Mc, V, W), args.reps)
+    out["spmm_csr_fp32"] = {"ms": t, "GBs": by / t / 1e6}
+    del Mc
+    m = nb * B
+    t = timeit(lambda: bbl.block_gram(basis, Wr), args.reps)
+    out["gram_fp32"] = {"ms": t, "GBs": (n * m * 4 + n * B * 4) / t / 1e6}
+    t = timeit(lambda: bbl.block_reorth(basis, Wr, passes=1), args.reps)
+    out["gram_update_fp32"] = {"ms": t, "GBs": (2 * n * m * 4 + 3 * n * B * 4) / t / 1e6}
+    Wc = Wr.clone()
+    t = timeit(lambda: bbl.cholqr2(Wc.copy_(Wr)), args.reps)
+    out["cholqr2_fp32"] = {"ms": t, "GBs": 6 * n * B * 4 / t / 1e6}
+    rng = np.random.default_rng(0)
+    mT, p = args.ritz_m, B
+    Tb = np.zeros((mT, p + 1))
+    Tb[:, 0] = rng.standard_normal(mT)
+    for d in range(1, p + 1):
+        Tb[d:, d] = rng.standard_normal(mT - d)
+    Td = torch.from_numpy(Tb).cuda()
+    t = timeit(lambda: bbl.ritz_banded(Td, NEV), max(1, args.reps // 2))
+    out["ritz_banded"] = {"ms": t, "m": mT, "p": p, "nev": NEV}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--mode", default="solve", choices=["solve", "kernels"])
+    ap.add_argument("--scale", type=float, default=0.5)
+    ap.add_argument("--blocks", type=int, default=50)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--ritz-m", type=int, default=728)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -316,7 +377,9 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.mode == "kernels":
+        run_kernels(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
