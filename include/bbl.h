@@ -155,6 +155,25 @@ bbl_status bbl_block_reorth(int64_t n, int b, int nblocks, bbl_dtype dtype, cons
 bbl_status bbl_block_gram(int64_t n, int b, int nblocks, bbl_dtype dtype, const void* basis, const void* W,
                           double* C, void* stream);
 
+/* Allocation-free variant of bbl_block_gram (no counterpart in the paper).
+ * For callers that must not allocate device memory: e.g. a process whose
+ * device memory is already handed out under a fixed budget by a framework's
+ * caching allocator, or a latency-critical loop that cannot afford the
+ * implicit device synchronisation of cudaFree.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine: the per-chunk partial sums live in
+ * a fixed 8 MiB file-scope device array that every device loading the
+ * library holds until the process exits.
+ *   Limit: nblocks*b*b <= 2^20 (otherwise BBL_ERR_INVALID_ARG with a message);
+ *   b in {1, 2, 4, 8, 16}.  Arguments and layouts as in bbl_block_gram.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.  All calls share the one array and it
+ * keeps the last call's contents (every partial a call reads is written by
+ * that call first), so calls that overlap on the GPU race with each other:
+ * serialise them, e.g. on one stream.  The call synchronises `stream`.     */
+bbl_status bbl_block_gram_noalloc(int64_t n, int b, int nblocks, bbl_dtype dtype, const void* basis, const void* W,
+                                  double* C, void* stream);
+
 /* ---------------------------------------------------------------- S3: CholQR2
  * W = Q B with Q orthonormal (overwrites W), B upper triangular b x b:
  * G1 = W^T W, R1 = chol(G1), W <- W R1^{-1}, G2, R2, W <- W R2^{-1}, B = R2 R1.

@@ -60,6 +60,7 @@ SIGNATURES = {
     "bbl_pivot_bootstrap": (ST, [P, I64, I32, D, C.c_uint64, P, P]),
     "bbl_solve": (ST, [P, I32, I32, P, C.POINTER(Options), P, P, P, C.POINTER(Stats)]),
     "bbl_block_gram": (ST, [I64, I32, I32, I32, P, P, P, P]),
+    "bbl_block_gram_noalloc": (ST, [I64, I32, I32, I32, P, P, P, P]),
     "bbl_pivot_rr_residual": (ST, [P, I32, P, P, P, P]),
     "bbl_mlp_create": (ST, [I32, I32, C.POINTER(P)]),
     "bbl_mlp_destroy": (None, [P]),

@@ -16,6 +16,7 @@
 //  cholqr2  G = W^T W -> R = chol(G) (one thread, b <= 16) -> W <- W R^{-1},
 //           twice; B = R2 R1 (Sec. II.B normalisation, CholQR2 form).
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -569,3 +570,112 @@ bbl_status bbl_ritz_vectors(int64_t n, int b, int nblocks, bbl_dtype dtype, cons
 }
 
 }  // extern "C"
+
+// -------------------------------------------------------------------- allocation-free Gram
+// For callers that must not allocate device memory: for example a process
+// whose device memory is already handed out by a framework's caching
+// allocator under a fixed budget, or a latency-critical loop that cannot
+// afford the implicit device synchronisation of cudaFree.  The per-chunk
+// partial sums of the Gram product live in a fixed file-scope device array
+// instead of a cudaMalloc'ed buffer.  Every device that loads this library
+// holds the array (8 MiB) until the process exits.
+namespace bbl {
+namespace {
+
+constexpr int64_t kNoAllocScratchDoubles = int64_t(1) << 20;  // 8 MiB of FP64 partial sums
+__device__ __align__(256) double g_noalloc_gram_scratch[kNoAllocScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array for the current device.  Host code
+// only holds a host-side stand-in for the array's name, so the address is
+// looked up once per device with that device current.
+bbl_status noalloc_scratch(double** out) {
+    int dev = 0;
+    BBL_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return set_error(BBL_ERR_UNSUPPORTED, "block_gram_noalloc: device %d", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_gram_scratch);
+        if (e != cudaSuccess || !p)
+            return set_error(BBL_ERR_CUDA, "block_gram_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        g_noalloc_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return BBL_OK;
+}
+
+template <typename T, int B, int CPT>
+bbl_status launch_gram_fixed(int64_t n, int m, const T* Q, const T* W, double* C, double* scratch, cudaStream_t st) {
+    int cols = (m + CPT - 1) / CPT;
+    int TC = 1;
+    while (TC < cols && TC < kThreads) TC <<= 1;
+    const int gy = (cols + TC - 1) / TC;
+    const int RS = kThreads / TC;
+    const int64_t per_chunk = (int64_t)m * B;
+    if (per_chunk > kNoAllocScratchDoubles)
+        return set_error(BBL_ERR_INVALID_ARG,
+                         "block_gram_noalloc: nblocks*b*b = %lld exceeds the fixed scratch of %lld doubles",
+                         (long long)per_chunk, (long long)kNoAllocScratchDoubles);
+    const int64_t max_chunks = kNoAllocScratchDoubles / per_chunk;
+    int64_t target = std::max<int64_t>(1, std::min<int64_t>((152 * 4) / gy, max_chunks));
+    int64_t rpc = std::max<int64_t>(kRT * 4, ceil_div(n, target));
+    rpc = ceil_div(rpc, kRT) * kRT;
+    int64_t nch = std::max<int64_t>(1, ceil_div(n, rpc));
+    while (nch > max_chunks) {  // grow the chunks until the partials fit
+        rpc += kRT;
+        nch = ceil_div(n, rpc);
+    }
+    const size_t smem = RS > 1 ? sizeof(double) * kThreads * CPT * B : 0;
+    BBL_CUDA(cudaFuncSetAttribute(gram_kernel<T, B, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(double) * kThreads * CPT * B)));
+    dim3 grid((unsigned)nch, (unsigned)gy);
+    gram_kernel<T, B, CPT><<<grid, kThreads, smem, st>>>(n, m, rpc, TC, Q, W, scratch);
+    BBL_LAUNCH_CHECK();
+    reduce_partials_kernel<<<(unsigned)ceil_div(per_chunk, 256), 256, 0, st>>>(per_chunk, (int)nch, scratch, C);
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
+}
+
+template <typename T>
+bbl_status gram_fixed_typed(int64_t n, int b, int m, const T* Q, const T* W, double* C, double* scratch,
+                            cudaStream_t st) {
+    constexpr bool F = sizeof(T) == 4;
+    switch (b) {
+        case 1: return launch_gram_fixed<T, 1, 1>(n, m, Q, W, C, scratch, st);
+        case 2: return launch_gram_fixed<T, 2, 2>(n, m, Q, W, C, scratch, st);
+        case 4: return launch_gram_fixed<T, 4, F ? 4 : 2>(n, m, Q, W, C, scratch, st);
+        case 8: return launch_gram_fixed<T, 8, F ? 4 : 2>(n, m, Q, W, C, scratch, st);
+        case 16: return launch_gram_fixed<T, 16, 2>(n, m, Q, W, C, scratch, st);
+        default:
+            return set_error(BBL_ERR_UNSUPPORTED, "block_gram_noalloc: b=%d (supported: 1, 2, 4, 8, 16)", b);
+    }
+}
+
+}  // namespace
+}  // namespace bbl
+
+extern "C" bbl_status bbl_block_gram_noalloc(int64_t n, int b, int nblocks, bbl_dtype dtype, const void* basis,
+                                             const void* W, double* C, void* stream) {
+    using namespace bbl;
+    if (n < 1 || b < 1 || b > kMaxB || nblocks < 1 || !basis || !W || !C)
+        return set_error(BBL_ERR_INVALID_ARG, "block_gram_noalloc: bad arguments");
+    if (dtype != BBL_FP64 && dtype != BBL_FP32) return set_error(BBL_ERR_INVALID_ARG, "block_gram_noalloc: bad dtype");
+    if (!aligned16(basis) || !aligned16(W))
+        return set_error(BBL_ERR_INVALID_ARG, "block_gram_noalloc: pointers must be 16-byte aligned");
+    double* scratch = nullptr;
+    BBL_TRY(noalloc_scratch(&scratch));
+    cudaStream_t st = as_stream(stream);
+    const int m = nblocks * b;
+    if (dtype == BBL_FP64)
+        BBL_TRY(gram_fixed_typed<double>(n, b, m, static_cast<const double*>(basis), static_cast<const double*>(W), C,
+                                         scratch, st));
+    else
+        BBL_TRY(gram_fixed_typed<float>(n, b, m, static_cast<const float*>(basis), static_cast<const float*>(W), C,
+                                        scratch, st));
+    BBL_CUDA(cudaStreamSynchronize(st));
+    return BBL_OK;
+}
