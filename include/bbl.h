@@ -130,6 +130,13 @@ void bbl_matrix_destroy(bbl_matrix* A);
 bbl_status bbl_matrix_info(const bbl_matrix* A, int64_t* n, int64_t* nnz, double* norm_inf,
                            int64_t* device_bytes, int* fmt, int* storage, int64_t* padded_nnz);
 
+/* SpMM schedule for the CSR path chosen by an autotuner: lanes per row (a
+ * power of two <= 32; 0 restores the built-in rule).  Used by bbl_spmm and by
+ * every solve on this matrix.                                            */
+bbl_status bbl_matrix_set_spmm_lanes(bbl_matrix* A, int lanes_per_row);
+/* diag(H) into a caller device buffer (FP64 [n]) */
+bbl_status bbl_matrix_diagonal(const bbl_matrix* A, double* d, void* stream);
+
 /* ---------------------------------------------------------------- S1: SpMM
  * W = H V (Sec. II.B, Eq. 3; w_{a,i} = sum_j H_ij v_{a,j}).  V, W: device,
  * n x b row-major, element type = the matrix storage type.  b in 1..16.   */
@@ -163,7 +170,7 @@ bbl_status bbl_block_gram(int64_t n, int b, int nblocks, bbl_dtype dtype, const 
  * cudaFree or allocating library routine: the per-chunk partial sums live in
  * a fixed 8 MiB file-scope device array that every device loading the
  * library holds until the process exits.
- *   Limit: nblocks*b*b <= 2^20 (otherwise BBL_ERR_INVALID_ARG with a message);
+ *   Limit: nblocks*b*b <= 2^20 - 64 (otherwise BBL_ERR_INVALID_ARG with a message);
  *   b in {1, 2, 4, 8, 16}.  Arguments and layouts as in bbl_block_gram.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
@@ -254,6 +261,34 @@ bbl_status bbl_mlp_train(bbl_mlp* M, int batch, const float* g, const float* tar
  * nblocks_U * b_U * b == out_dim.                                        */
 bbl_status bbl_pivot_learned(bbl_mlp* M, float g, int64_t n, int b_U, int nblocks_U, const float* U, int b,
                              double* P, void* stream);
+
+/* ---------------------------------------------------------------- batched form
+ * Many independent solves in one graph launch (no counterpart in the paper;
+ * its use here: many truncated-space bootstraps or training-data solves).
+ * The problems are stacked row-wise into one block-diagonal CSR matrix:
+ * problem s owns rows [offsets[s], offsets[s+1]) and may only reference
+ * columns in the same range (checked, BBL_ERR_INVALID_ARG otherwise).
+ * Arrays as in bbl_matrix_create (host or device, copied).               */
+typedef struct bbl_batch bbl_batch;
+bbl_status bbl_batch_create(int count, const int64_t* offsets, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                            const void* val, bbl_dtype val_dtype, bbl_dtype storage, bbl_format fmt, int sell_sigma,
+                            void* stream, bbl_batch** out);
+void bbl_batch_destroy(bbl_batch* B);
+/* the stacked block-diagonal matrix (owned by the batch), e.g. for timing SpMM schedules */
+bbl_status bbl_batch_matrix(bbl_batch* B, bbl_matrix** A);
+/* SpMM schedule chosen by an autotuner: CSR lanes per row (0 = built-in rule) */
+bbl_status bbl_batch_set_schedule(bbl_batch* B, int lanes_per_row);
+/* Block Lanczos on every problem, in lock-step: one iteration is one fixed
+ * kernel sequence over all problems; with use_graph = 1 it is captured as the
+ * body of a CUDA graph while-node and the whole solve is one graph launch,
+ * with use_graph = 0 the host drives the same sequence.  Each problem stops
+ * when its nev estimates ||B_j s_i[last b]|| are <= tol*||H_s||_inf; random
+ * pivots (opt->seed).  Outputs (host): evals, resid [count x nev] (true FP64
+ * residuals), iters [count], status [count] (BBL_OK, BBL_ERR_NOT_CONVERGED,
+ * BBL_ERR_NUMERICAL for a breakdown).  b in {1, 2, 4, 8, 16}, nev <= 16.
+ * Returns BBL_OK when every problem converged.                           */
+bbl_status bbl_batch_solve(bbl_batch* B, int nev, int b, const bbl_options* opt, int use_graph, double* evals,
+                           double* resid, int* iters, int* status, bbl_stats* stats);
 
 /* ---------------------------------------------------------------- solve
  * Block Lanczos for the nev lowest eigenpairs (Sec. II.B, Eqs. 4-12).

@@ -110,6 +110,9 @@ class Matrix:
         torch = _torch()
         return torch.float32 if self.storage == "fp32" else torch.float64
 
+    def set_spmm_lanes(self, lanes_per_row: int):
+        _lib.check(self._lib.bbl_matrix_set_spmm_lanes(self.handle, int(lanes_per_row)))
+
     def diagonal(self, stream=None):
         torch = _torch()
         d = torch.empty(self.n, dtype=torch.float64, device="cuda")
@@ -282,6 +285,75 @@ class MLP:
     def close(self):
         if getattr(self, "handle", None):
             self._lib.bbl_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stack_block_diagonal(mats):
+    """Stacks square CSR matrices row-wise into one block-diagonal CSR (layout
+    conversion for bbl_batch_create): returns (offsets, row_ptr, col, val)."""
+    ns = [int(m.n) for m in mats]
+    offsets = np.zeros(len(mats) + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(ns)
+    nnzs = [int(m.row_ptr[-1]) for m in mats]
+    nz_off = np.zeros(len(mats) + 1, dtype=np.int64)
+    nz_off[1:] = np.cumsum(nnzs)
+    row_ptr = np.empty(offsets[-1] + 1, dtype=np.int64)
+    col = np.empty(nz_off[-1], dtype=np.int32)
+    vdt = np.float32 if all(m.val.dtype == np.float32 for m in mats) else np.float64
+    val = np.empty(nz_off[-1], dtype=vdt)
+    for s, m in enumerate(mats):
+        row_ptr[offsets[s]:offsets[s + 1]] = m.row_ptr[:-1] + nz_off[s]
+        col[nz_off[s]:nz_off[s + 1]] = m.col + offsets[s]
+        val[nz_off[s]:nz_off[s + 1]] = m.val
+    row_ptr[-1] = nz_off[-1]
+    return offsets, row_ptr, col, val
+
+
+class Batch:
+    """Many independent problems solved in lock-step (bbl_batch)."""
+
+    def __init__(self, mats, storage: str = "fp32", fmt: str = "csr", sell_sigma: int = 0, stream=None):
+        self._lib = _lib.load()
+        offsets, rp, col, val = stack_block_diagonal(mats)
+        self.count = len(mats)
+        self.offsets = offsets
+        self.n = int(offsets[-1])
+        self.nnz = int(rp[-1])
+        self.storage = storage
+        h = C.c_void_p()
+        _lib.check(self._lib.bbl_batch_create(len(mats), _ptr(offsets), self.nnz, _ptr(rp), _ptr(col), _ptr(val),
+                                              FP64 if val.dtype == np.float64 else FP32,
+                                              FP32 if storage == "fp32" else FP64, SELL if fmt == "sell" else CSR,
+                                              int(sell_sigma), _stream(stream), C.byref(h)))
+        self.handle = h
+
+    def set_schedule(self, lanes_per_row: int):
+        _lib.check(self._lib.bbl_batch_set_schedule(self.handle, int(lanes_per_row)))
+
+    def solve(self, nev: int, b: int, use_graph: bool = True, **opts):
+        o = options(**opts)
+        o.storage = FP32 if self.storage == "fp32" else FP64
+        if "stream" not in opts:
+            o.stream = _stream(None)
+        ev = np.zeros((self.count, nev))
+        rs = np.zeros((self.count, nev))
+        it = np.zeros(self.count, dtype=np.int32)
+        stt = np.zeros(self.count, dtype=np.int32)
+        st = Stats()
+        s = self._lib.bbl_batch_solve(self.handle, nev, b, C.byref(o), int(bool(use_graph)), _ptr(ev), _ptr(rs),
+                                      _ptr(it), _ptr(stt), C.byref(st))
+        _lib.check(s, allow=(0, 5))
+        return ev, rs, it, stt, st.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.bbl_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -49,6 +49,7 @@ SIGNATURES = {
     "bbl_matrix_info": (ST, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(D), C.POINTER(I64), C.POINTER(I32),
                              C.POINTER(I32), C.POINTER(I64)]),
     "bbl_matrix_diagonal": (ST, [P, P, P]),
+    "bbl_matrix_set_spmm_lanes": (ST, [P, I32]),
     "bbl_spmm": (ST, [P, I32, P, P, P]),
     "bbl_spmm_f64": (ST, [P, I32, P, P, P]),
     "bbl_spmm_group": (ST, [P, I32, P, P, I32, P]),
@@ -72,6 +73,11 @@ SIGNATURES = {
     "bbl_mlp_adam_step": (ST, [P, C.c_float, P]),
     "bbl_mlp_train": (ST, [P, I32, P, P, I32, C.c_float, P, P]),
     "bbl_pivot_learned": (ST, [P, C.c_float, I64, I32, I32, P, I32, P, P]),
+    "bbl_batch_create": (ST, [I32, P, I64, P, P, P, I32, I32, I32, I32, P, C.POINTER(P)]),
+    "bbl_batch_destroy": (None, [P]),
+    "bbl_batch_matrix": (ST, [P, C.POINTER(P)]),
+    "bbl_batch_set_schedule": (ST, [P, I32]),
+    "bbl_batch_solve": (ST, [P, I32, I32, C.POINTER(Options), I32, P, P, P, P, C.POINTER(Stats)]),
 }
 
 _lib = None

@@ -47,30 +47,42 @@ __device__ __forceinline__ void ldvec(const T* p, T (&out)[N]) {
     }
 }
 
-constexpr int kRT = 64;    // rows per shared-memory tile in gram
+constexpr int kRT = 256;   // rows per shared-memory tile in gram
 constexpr int kThreads = 256;
 
 // -------------------------------------------------------------------- gram
-template <typename T, int B, int CPT>
-__global__ void __launch_bounds__(kThreads) gram_kernel(int64_t n, int m, int64_t rows_per_chunk, int TC,
-                                                        const T* __restrict__ Q, const T* __restrict__ W,
-                                                        double* __restrict__ partial) {
+// One CTA: the partial Gram of the row ranges handed out by next(r0, r1)
+// (called by every thread, in step) for the Q columns of column group
+// `cgrp`, written to out[m][B] (this CTA's partial slot).
+template <typename T, int B, int CPT, typename Next>
+__device__ __forceinline__ void gram_body(int64_t n, int m, Next next, int TC, int cgrp, const T* __restrict__ Q,
+                                          const T* __restrict__ W, double* __restrict__ partial_slot) {
     __shared__ T ws[kRT * B];
     extern __shared__ double sred[];
     const int tid = threadIdx.x;
     const int RS = kThreads / TC;
     const int cg = tid % TC, rs = tid / TC;
-    const int a0 = (blockIdx.y * TC + cg) * CPT;
+    const int a0 = (cgrp * TC + cg) * CPT;
     const bool active = a0 < m;
     const int j = active ? a0 / B : 0, off = a0 % B;
     const T* qb = Q + (int64_t)j * n * B + off;
-    double acc64[CPT][B];
+    // FP64 running sums: in registers for FP64 data; for FP32 data the
+    // per-tile FP32 sums are added into this thread's shared-memory slot, so
+    // that registers go to loads in flight instead.
+    constexpr bool kF32 = sizeof(T) == 4;
+    constexpr int U = 8;  // rows whose loads are issued together
+    double* mine = sred + (size_t)tid * CPT * B;
+    double acc64[kF32 ? 1 : CPT][kF32 ? 1 : B];
+    if constexpr (kF32) {
+        for (int e = 0; e < CPT * B; ++e) mine[e] = 0.0;
+    } else {
 #pragma unroll
-    for (int i = 0; i < CPT; ++i)
+        for (int i = 0; i < CPT; ++i)
 #pragma unroll
-        for (int c = 0; c < B; ++c) acc64[i][c] = 0.0;
-    const int64_t r_begin = (int64_t)blockIdx.x * rows_per_chunk;
-    const int64_t r_end = min(n, r_begin + rows_per_chunk);
+            for (int c = 0; c < B; ++c) acc64[i][c] = 0.0;
+    }
+    int64_t r_begin = 0, r_end = 0;
+    while (next(r_begin, r_end))
     for (int64_t t0 = r_begin; t0 < r_end; t0 += kRT) {
         const int rows = (int)min((int64_t)kRT, r_end - t0);
         __syncthreads();
@@ -82,7 +94,23 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(int64_t n, int m, int64_
             for (int i = 0; i < CPT; ++i)
 #pragma unroll
                 for (int c = 0; c < B; ++c) acc[i][c] = T(0);
-            for (int r = rs; r < rows; r += RS) {
+            int r = rs;
+            for (; r + (U - 1) * RS < rows; r += U * RS) {
+                T q[U][CPT];
+#pragma unroll
+                for (int u = 0; u < U; ++u) ldvec<T, CPT>(qb + (t0 + r + u * RS) * B, q[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const T* wr = ws + (r + u * RS) * B;
+#pragma unroll
+                    for (int c = 0; c < B; ++c) {
+                        const T w = wr[c];
+#pragma unroll
+                        for (int i = 0; i < CPT; ++i) acc[i][c] = fma(q[u][i], w, acc[i][c]);
+                    }
+                }
+            }
+            for (; r < rows; r += RS) {
                 T q[CPT];
                 ldvec<T, CPT>(qb + (t0 + r) * B, q);
                 const T* wr = ws + r * B;
@@ -93,19 +121,29 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(int64_t n, int m, int64_
                     for (int i = 0; i < CPT; ++i) acc[i][c] = fma(q[i], w, acc[i][c]);
                 }
             }
+            if constexpr (kF32) {
+#pragma unroll
+                for (int i = 0; i < CPT; ++i)
+#pragma unroll
+                    for (int c = 0; c < B; ++c) mine[i * B + c] += (double)acc[i][c];
+            } else {
+#pragma unroll
+                for (int i = 0; i < CPT; ++i)
+#pragma unroll
+                    for (int c = 0; c < B; ++c) acc64[i][c] += (double)acc[i][c];
+            }
+        }
+    }
+    if constexpr (!kF32) {
+        if (RS > 1) {
 #pragma unroll
             for (int i = 0; i < CPT; ++i)
 #pragma unroll
-                for (int c = 0; c < B; ++c) acc64[i][c] += (double)acc[i][c];
+                for (int c = 0; c < B; ++c) mine[i * B + c] = acc64[i][c];
         }
     }
     if (RS > 1) {
         // deterministic tree over the row slots
-        double* mine = sred + (size_t)tid * CPT * B;
-#pragma unroll
-        for (int i = 0; i < CPT; ++i)
-#pragma unroll
-            for (int c = 0; c < B; ++c) mine[i * B + c] = acc64[i][c];
         __syncthreads();
         for (int s = RS / 2; s > 0; s >>= 1) {
             if (rs < s) {
@@ -115,16 +153,76 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(int64_t n, int m, int64_
             __syncthreads();
         }
         if (rs == 0 && active) {
-            double* out = partial + ((int64_t)blockIdx.x * m + a0) * B;
+            double* out = partial_slot + (int64_t)a0 * B;
             for (int e = 0; e < CPT * B; ++e) out[e] = mine[e];
         }
     } else if (active) {
-        double* out = partial + ((int64_t)blockIdx.x * m + a0) * B;
+        double* out = partial_slot + (int64_t)a0 * B;
+        if constexpr (kF32) {
+            for (int e = 0; e < CPT * B; ++e) out[e] = mine[e];
+        } else {
 #pragma unroll
-        for (int i = 0; i < CPT; ++i)
+            for (int i = 0; i < CPT; ++i)
 #pragma unroll
-            for (int c = 0; c < B; ++c) out[i * B + c] = acc64[i][c];
+                for (int c = 0; c < B; ++c) out[i * B + c] = acc64[i][c];
+        }
     }
+}
+
+// Hands out [r0, r1) once (one fixed range per CTA).
+struct OneRange {
+    int64_t r0, r1;
+    bool done = false;
+    __device__ bool operator()(int64_t& a, int64_t& b) {
+        if (done) return false;
+        done = true;
+        a = r0;
+        b = r1;
+        return r1 > r0;
+    }
+};
+
+// Hands out chunks of a shared ticket counter: CTAs that start late (their
+// SM was busy) simply take fewer chunks, so there is no tail wave.
+struct TicketRanges {
+    int* ticket;
+    int64_t n, rows_per_chunk;
+    int nchunks;
+    __device__ bool operator()(int64_t& a, int64_t& b) {
+        __shared__ int s_c;
+        __syncthreads();
+        if (threadIdx.x == 0) s_c = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int c = s_c;
+        if (c >= nchunks) return false;
+        a = (int64_t)c * rows_per_chunk;
+        b = min(n, a + rows_per_chunk);
+        return true;
+    }
+};
+
+// Split-K Gram: persistent CTAs (x, y) = worker x of column group y; the row
+// chunks of each column group are taken from ticket[y].
+template <typename T, int B, int CPT>
+__global__ void __launch_bounds__(kThreads) gram_kernel(int64_t n, int m, int64_t rows_per_chunk, int nchunks, int TC,
+                                                        const T* __restrict__ Q, const T* __restrict__ W,
+                                                        double* __restrict__ partial, int* __restrict__ tickets) {
+    TicketRanges next{tickets + blockIdx.y, n, rows_per_chunk, nchunks};
+    gram_body<T, B, CPT>(n, m, next, TC, blockIdx.y, Q, W, partial + (int64_t)blockIdx.x * m * B);
+}
+
+// Segmented Gram for a batch of independent problems stacked row-wise:
+// chunk x covers rows [chunks[3x+1], chunks[3x+2]) of segment chunks[3x];
+// chunks of inactive segments do nothing.
+template <typename T, int B, int CPT>
+__global__ void __launch_bounds__(kThreads) gram_seg_kernel(int64_t n, int m, const int64_t* __restrict__ chunks,
+                                                            const int* __restrict__ seg_active, int TC,
+                                                            const T* __restrict__ Q, const T* __restrict__ W,
+                                                            double* __restrict__ partial) {
+    const int64_t seg = chunks[3 * blockIdx.x];
+    if (seg_active && !seg_active[seg]) return;
+    gram_body<T, B, CPT>(n, m, OneRange{chunks[3 * blockIdx.x + 1], chunks[3 * blockIdx.x + 2]}, TC, blockIdx.y, Q, W,
+                         partial + (int64_t)blockIdx.x * m * B);
 }
 
 // any b (runtime), one Q column per thread
@@ -185,33 +283,142 @@ __global__ void reduce_partials_kernel(int64_t count, int nparts, const double* 
     out[e] = s;
 }
 
+// Self Gram G = W^T W for b <= 8 (CholQR2): a thread per row (grid-strided),
+// the b(b+1)/2 distinct products in registers, then a warp-shuffle and
+// shared-memory reduction to one B x B partial per CTA.
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads) syrk_kernel(int64_t n, const T* __restrict__ W, double* __restrict__ partial) {
+    constexpr int NP = B * (B + 1) / 2;
+    __shared__ double red[kThreads / 32][NP];
+    T acc[NP];
+#pragma unroll
+    for (int e = 0; e < NP; ++e) acc[e] = T(0);
+    double acc64[NP];
+#pragma unroll
+    for (int e = 0; e < NP; ++e) acc64[e] = 0.0;
+    int cnt = 0;
+    for (int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x; r < n; r += (int64_t)gridDim.x * kThreads) {
+        T w[B];
+        if constexpr (B * sizeof(T) >= 16) {
+            constexpr int CH = 16 / (int)sizeof(T);
+#pragma unroll
+            for (int ch = 0; ch < B / CH; ++ch) {
+                T t[CH];
+                ldvec<T, CH>(W + r * B + ch * CH, t);
+#pragma unroll
+                for (int q = 0; q < CH; ++q) w[ch * CH + q] = t[q];
+            }
+        } else {
+            ldvec<T, B>(W + r * B, w);
+        }
+        int e = 0;
+#pragma unroll
+        for (int i = 0; i < B; ++i)
+#pragma unroll
+            for (int k = i; k < B; ++k) {
+                acc[e] = fma(w[i], w[k], acc[e]);
+                ++e;
+            }
+        if (++cnt == 64) {  // FP32 runs of at most 64 rows, summed in FP64
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                acc64[q] += (double)acc[q];
+                acc[q] = T(0);
+            }
+            cnt = 0;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        double v = acc64[q] + (double)acc[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NP) {
+        double v = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) v += red[w][threadIdx.x];
+        // unpack the upper-triangle index into (i, k) and store both halves
+        int i = 0, e = threadIdx.x;
+        while (e >= B - i) {
+            e -= B - i;
+            ++i;
+        }
+        const int k = i + e;
+        partial[(int64_t)blockIdx.x * B * B + i * B + k] = v;
+        partial[(int64_t)blockIdx.x * B * B + k * B + i] = v;
+    }
+}
+
+template <typename T, int B>
+bbl_status launch_syrk(int64_t n, const T* W, double* G, DevBuf& partials, cudaStream_t st) {
+    const int grid = (int)std::min<int64_t>(152 * 4, std::max<int64_t>(1, ceil_div(n, kThreads)));
+    const size_t need = sizeof(double) * (size_t)grid * B * B;
+    if (partials.bytes < need) BBL_TRY(partials.alloc(need));
+    syrk_kernel<T, B><<<grid, kThreads, 0, st>>>(n, W, partials.as<double>());
+    BBL_LAUNCH_CHECK();
+    reduce_partials_kernel<<<1, 256, 0, st>>>((int64_t)B * B, grid, partials.as<double>(), G);
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    }
+    return n;
+}
+
+// Launches the persistent split-K Gram and the reduction of its per-worker
+// partials.  partial: room for `cap` doubles; tickets: gy ints (zeroed here).
 template <typename T, int B, int CPT>
-bbl_status launch_gram(int64_t n, int m, const T* Q, const T* W, double* C, DevBuf& partials, cudaStream_t st) {
+bbl_status gram_core(int64_t n, int m, const T* Q, const T* W, double* C, double* partial, int64_t cap, int* tickets,
+                     cudaStream_t st) {
     int cols = (m + CPT - 1) / CPT;
     int TC = 1;
     while (TC < cols && TC < kThreads) TC <<= 1;
     const int gy = (cols + TC - 1) / TC;
     const int RS = kThreads / TC;
-    int64_t target = std::max<int64_t>(1, (152 * 4) / gy);
-    int64_t rpc = std::max<int64_t>(kRT * 4, ceil_div(n, target));
-    rpc = ceil_div(rpc, kRT) * kRT;
-    const int64_t nch = std::max<int64_t>(1, ceil_div(n, rpc));
-    const size_t need = sizeof(double) * (size_t)nch * m * B;
-    if (partials.bytes < need) BBL_TRY(partials.alloc(need));
-    const size_t smem = RS > 1 ? sizeof(double) * kThreads * CPT * B : 0;
-    static bool attr_set = false;
-    if (!attr_set) {
-        BBL_CUDA(cudaFuncSetAttribute(gram_kernel<T, B, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(double) * kThreads * CPT * B)));
-        attr_set = true;
+    // FP32 data keeps its FP64 running sums in shared memory; FP64 data needs
+    // the buffer only for the reduction over row slots
+    const size_t smem_max = sizeof(double) * kThreads * CPT * B;
+    const size_t smem = (RS > 1 || sizeof(T) == 4) ? smem_max : 0;
+    static int occ = 0;
+    if (occ == 0) {
+        BBL_CUDA(cudaFuncSetAttribute(gram_kernel<T, B, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+        BBL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gram_kernel<T, B, CPT>, kThreads, smem_max));
+        if (occ < 1) occ = 1;
     }
-    dim3 grid((unsigned)nch, (unsigned)gy);
-    gram_kernel<T, B, CPT><<<grid, kThreads, smem, st>>>(n, m, rpc, TC, Q, W, partials.as<double>());
+    const int64_t rpc = 4 * kRT;
+    const int nch = (int)std::max<int64_t>(1, ceil_div(n, rpc));
+    const int64_t per = (int64_t)m * B;
+    int64_t workers = std::max<int64_t>(1, (int64_t)sm_count() * occ / gy);
+    workers = std::min<int64_t>(workers, nch);
+    workers = std::min<int64_t>(workers, cap / per);
+    if (workers < 1)
+        return set_error(BBL_ERR_INVALID_ARG, "gram: %lld partial sums exceed the %lld-double scratch", (long long)per,
+                         (long long)cap);
+    BBL_CUDA(cudaMemsetAsync(tickets, 0, sizeof(int) * gy, st));
+    dim3 grid((unsigned)workers, (unsigned)gy);
+    gram_kernel<T, B, CPT><<<grid, kThreads, smem, st>>>(n, m, rpc, nch, TC, Q, W, partial, tickets);
     BBL_LAUNCH_CHECK();
-    const int64_t count = (int64_t)m * B;
-    reduce_partials_kernel<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(count, (int)nch, partials.as<double>(), C);
+    reduce_partials_kernel<<<(unsigned)ceil_div(per, 256), 256, 0, st>>>(per, (int)workers, partial, C);
     BBL_LAUNCH_CHECK();
     return BBL_OK;
+}
+
+template <typename T, int B, int CPT>
+bbl_status launch_gram(int64_t n, int m, const T* Q, const T* W, double* C, DevBuf& partials, cudaStream_t st) {
+    const int64_t per = (int64_t)m * B;
+    const int64_t cap = per * (int64_t)sm_count() * 8;        // enough for any occupancy
+    const size_t need = sizeof(double) * (size_t)cap + 4096;   // + tickets
+    if (partials.bytes < need) BBL_TRY(partials.alloc(need));
+    int* tickets = reinterpret_cast<int*>(partials.as<char>() + sizeof(double) * (size_t)cap);
+    return gram_core<T, B, CPT>(n, m, Q, W, C, partials.as<double>(), cap, tickets, st);
 }
 
 template <typename T>
@@ -220,7 +427,7 @@ bbl_status launch_gram_generic(int64_t n, int m, int b, const T* Q, const T* W, 
     int TC = 1;
     while (TC < m && TC < kThreads) TC <<= 1;
     const int gy = (m + TC - 1) / TC;
-    int64_t target = std::max<int64_t>(1, (152 * 4) / gy);
+    int64_t target = std::max<int64_t>(1, (152 * 2) / gy);
     int64_t rpc = std::max<int64_t>(kRT * 4, ceil_div(n, target));
     rpc = ceil_div(rpc, kRT) * kRT;
     const int64_t nch = std::max<int64_t>(1, ceil_div(n, rpc));
@@ -258,13 +465,15 @@ bbl_status gram_typed(int64_t n, int b, int m, const T* Q, const T* W, double* C
 // W[r][c] (SUB ? -= : =) sum_a Q[r][a] C[a][c], c < kc.  Q: nblocks blocks of
 // n x B; C: m x kc FP64 row-major; W: n x kc (type TO).  TA: accumulation type.
 constexpr int kKT = 256;
+// One CTA: rows r = row0 + threadIdx.x (r < row_end) of W (-)= Q C.
 template <typename T, int B, int KCT, bool SUB, typename TA, typename TO>
-__global__ void __launch_bounds__(kThreads) apply_kernel(int64_t n, int m, int kc, const T* Q, const double* __restrict__ C,
-                                                         TO* W) {
+__device__ __forceinline__ void apply_body(int64_t n, int m, int kc, int64_t row0, int64_t row_end, const T* Q,
+                                           const double* __restrict__ C, TO* W) {
     constexpr int KM = KCT > 0 ? KCT : kMaxB;
     __shared__ TA cs[kKT * KM];
     const int tid = threadIdx.x;
-    const int64_t r = (int64_t)blockIdx.x * kThreads + tid;
+    const int64_t r = row0 + tid;
+    const int64_t rlim = row_end;
     TA acc[KM];
 #pragma unroll
     for (int c = 0; c < KM; ++c) acc[c] = TA(0);
@@ -276,7 +485,8 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(int64_t n, int m, int k
             cs[e] = (c < kc) ? (TA)C[(int64_t)(a0 + a) * kc + c] : TA(0);
         }
         __syncthreads();
-        if (r < n) {
+        if (r < rlim) {
+#pragma unroll 4
             for (int jb = 0; jb < rows; jb += B) {
                 const int j = (a0 + jb) / B;
                 T q[B];
@@ -302,7 +512,7 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(int64_t n, int m, int k
             }
         }
     }
-    if (r < n) {
+    if (r < rlim) {
 #pragma unroll
         for (int c = 0; c < KM; ++c) {
             if (c < kc) {
@@ -312,6 +522,29 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(int64_t n, int m, int k
             }
         }
     }
+}
+
+template <typename T, int B, int KCT, bool SUB, typename TA, typename TO>
+__global__ void __launch_bounds__(kThreads) apply_kernel(int64_t n, int m, int kc, const T* Q, const double* __restrict__ C,
+                                                         TO* W) {
+    apply_body<T, B, KCT, SUB, TA, TO>(n, m, kc, (int64_t)blockIdx.x * kThreads, n, Q, C, W);
+}
+
+// Segmented apply: CTA x handles rows [ctas[3x+1], ctas[3x+2]) (at most 256)
+// of segment s = ctas[3x], with that segment's coefficients C + s*cstride and
+// m = ms[s * ms_stride] basis columns (ms_stride 0: one shared count; ms NULL:
+// m_all); inactive segments skip.
+template <typename T, int B, int KCT, bool SUB, typename TA, typename TO>
+__global__ void __launch_bounds__(kThreads) apply_seg_kernel(int64_t n, int m_all, const int* __restrict__ ms,
+                                                             int ms_stride, int kc,
+                                                             const int64_t* __restrict__ ctas,
+                                                             const int* __restrict__ seg_active, const T* Q,
+                                                             const double* __restrict__ C, int64_t cstride, TO* W) {
+    const int64_t seg = ctas[3 * blockIdx.x];
+    if (seg_active && !seg_active[seg]) return;
+    const int m = ms ? ms[seg * ms_stride] : m_all;
+    apply_body<T, B, KCT, SUB, TA, TO>(n, m, kc, ctas[3 * blockIdx.x + 1], ctas[3 * blockIdx.x + 2], Q,
+                                       C + seg * cstride, W);
 }
 
 // any b (runtime)
@@ -375,10 +608,43 @@ bbl_status apply_typed(int64_t n, int b, int m, int kc, const T* Q, const double
 
 // -------------------------------------------------------------------- Cholesky of the b x b Gram
 // status bits: 1 = non-finite Gram.  mask[i] = 1 for deflated columns.
+__device__ void chol_body(int b, const double* __restrict__ G, double thresh2, int relative, double* __restrict__ R,
+                          double* __restrict__ Rinv, int* __restrict__ ndefl, int* __restrict__ mask,
+                          int* __restrict__ status);
+
 __global__ void chol_kernel(int b, const double* __restrict__ G, double thresh2, int relative, double* __restrict__ R,
                             double* __restrict__ Rinv, int* __restrict__ ndefl, int* __restrict__ mask,
                             int* __restrict__ status) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    chol_body(b, G, thresh2, relative, R, Rinv, ndefl, mask, status);
+}
+
+// One thread per segment: Cholesky of G + s*b*b with threshold thresh2[s].
+__global__ void chol_seg_kernel(int b, int nseg, const double* __restrict__ G, const double* __restrict__ thresh2,
+                                int relative, double* __restrict__ R, double* __restrict__ Rinv, int* __restrict__ ndefl,
+                                int* __restrict__ mask, int* __restrict__ status, const int* __restrict__ active) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg || (active && !active[s])) return;
+    const int64_t o = (int64_t)s * b * b;
+    chol_body(b, G + o, thresh2 ? thresh2[s] : 0.0, relative, R + o, Rinv + o, ndefl ? ndefl + s : nullptr,
+              mask ? mask + (int64_t)s * b : nullptr, status ? status + s : nullptr);
+}
+
+__global__ void trmul_seg_kernel(int b, int nseg, const double* __restrict__ R2, const double* __restrict__ R1,
+                                 double* __restrict__ B, const int* __restrict__ active) {
+    const int s = blockIdx.y;
+    const int e = threadIdx.x;
+    if (s >= nseg || e >= b * b || (active && !active[s])) return;
+    const int64_t o = (int64_t)s * b * b;
+    const int i = e / b, k = e % b;
+    double acc = 0.0;
+    for (int l = 0; l < b; ++l) acc += R2[o + i * b + l] * R1[o + l * b + k];
+    B[o + e] = acc;
+}
+
+__device__ void chol_body(int b, const double* __restrict__ G, double thresh2, int relative, double* __restrict__ R,
+                          double* __restrict__ Rinv, int* __restrict__ ndefl, int* __restrict__ mask,
+                          int* __restrict__ status) {
     double Rl[kMaxB * kMaxB];
     int dm[kMaxB];
     bool bad = false;
@@ -466,6 +732,30 @@ bbl_status ritz_vectors(int64_t n, int b, int nblocks, int dtype, const void* Q,
 }
 
 // small: >= 8*b*b doubles + 4*b ints.  B (device, b x b) receives R2 R1.
+// G = W^T W (b x b): the dedicated kernel for b in {1, 2, 4, 8}, else the general Gram.
+bbl_status self_gram(int64_t n, int b, int dtype, const void* W, double* G, DevBuf& partials, cudaStream_t st) {
+    if (dtype == BBL_FP64) {
+        auto w = static_cast<const double*>(W);
+        switch (b) {
+            case 1: return launch_syrk<double, 1>(n, w, G, partials, st);
+            case 2: return launch_syrk<double, 2>(n, w, G, partials, st);
+            case 4: return launch_syrk<double, 4>(n, w, G, partials, st);
+            case 8: return launch_syrk<double, 8>(n, w, G, partials, st);
+            default: break;
+        }
+    } else {
+        auto w = static_cast<const float*>(W);
+        switch (b) {
+            case 1: return launch_syrk<float, 1>(n, w, G, partials, st);
+            case 2: return launch_syrk<float, 2>(n, w, G, partials, st);
+            case 4: return launch_syrk<float, 4>(n, w, G, partials, st);
+            case 8: return launch_syrk<float, 8>(n, w, G, partials, st);
+            default: break;
+        }
+    }
+    return gram(n, b, 1, dtype, W, W, G, partials, st);
+}
+
 bbl_status cholqr2_dev(int64_t n, int b, int dtype, void* W, double* B, double defl_abs2, int* d_ndefl, int* d_mask,
                        DevBuf& partials, DevBuf& small, cudaStream_t st) {
     const size_t need = sizeof(double) * 8 * kMaxB * kMaxB + sizeof(int) * 4 * kMaxB;
@@ -478,7 +768,7 @@ bbl_status cholqr2_dev(int64_t n, int b, int dtype, void* W, double* B, double d
     int* status = reinterpret_cast<int*>(G + 8 * kMaxB * kMaxB);
     const int relative = defl_abs2 < 0 ? 1 : 0;
     const double t1 = relative ? -defl_abs2 : defl_abs2;
-    BBL_TRY(gram(n, b, 1, dtype, W, W, G, partials, st));
+    BBL_TRY(self_gram(n, b, dtype, W, G, partials, st));
     chol_kernel<<<1, 32, 0, st>>>(b, G, t1, relative, R1, R1i, d_ndefl, d_mask, status);
     BBL_LAUNCH_CHECK();
     if (dtype == BBL_FP64)
@@ -487,7 +777,7 @@ bbl_status cholqr2_dev(int64_t n, int b, int dtype, void* W, double* B, double d
     else
         BBL_TRY((apply_typed<float, false, float, float>(n, b, b, b, static_cast<float*>(W), R1i,
                                                           static_cast<float*>(W), st)));
-    BBL_TRY(gram(n, b, 1, dtype, W, W, G, partials, st));
+    BBL_TRY(self_gram(n, b, dtype, W, G, partials, st));
     // second pass: columns of Q1 have norm ~1; a pivot below 1e-6 means the
     // first pass produced no usable direction (it was deflated or lost).
     chol_kernel<<<1, 32, 0, st>>>(b, G, 1e-6, 0, R2, R2i, nullptr, nullptr, status);
@@ -502,6 +792,159 @@ bbl_status cholqr2_dev(int64_t n, int b, int dtype, void* W, double* B, double d
         trmul_kernel<<<1, 256, 0, st>>>(b, R2, R1, B);
         BBL_LAUNCH_CHECK();
     }
+    return BBL_OK;
+}
+
+// -------------------------------------------------------------------- segmented (batched) forms
+// A batch of independent problems is stacked row-wise: segment s owns rows
+// [off[s], off[s+1]) of every n_tot x b block.  Work tables are built once
+// on the host: gram chunks (seg, r0, r1) never cross a segment, apply CTAs
+// (seg, r0, r1) cover at most 256 rows of one segment.  The current number of
+// basis columns may be read from device memory (d_m), so that one captured
+// graph serves every iteration.
+namespace {
+
+__global__ void reduce_seg_kernel(int m_max, int b, const int* __restrict__ d_m, const int* __restrict__ seg_chunk_ptr,
+                                  const int* __restrict__ active, const double* __restrict__ partial,
+                                  double* __restrict__ C) {
+    const int s = blockIdx.y;
+    if (active && !active[s]) return;
+    const int m = d_m ? *d_m : m_max;
+    const int64_t count = (int64_t)m * b;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    double acc = 0.0;
+    for (int c = seg_chunk_ptr[s]; c < seg_chunk_ptr[s + 1]; ++c) acc += partial[(int64_t)c * count + e];
+    C[(int64_t)s * m_max * b + e] = acc;
+}
+
+template <typename T, int B, int CPT>
+__global__ void __launch_bounds__(kThreads) gram_seg_dyn_kernel(int64_t n, const int* __restrict__ d_m,
+                                                                const int64_t* __restrict__ chunks,
+                                                                const int* __restrict__ seg_active,
+                                                                const T* __restrict__ Q, const T* __restrict__ W,
+                                                                double* __restrict__ partial) {
+    const int64_t seg = chunks[3 * blockIdx.x];
+    if (seg_active && !seg_active[seg]) return;
+    const int m = *d_m;
+    const int cols = (m + CPT - 1) / CPT;
+    int TC = 1;
+    while (TC < cols && TC < kThreads) TC <<= 1;
+    if ((int)blockIdx.y * TC * CPT >= m) return;
+    gram_body<T, B, CPT>(n, m, OneRange{chunks[3 * blockIdx.x + 1], chunks[3 * blockIdx.x + 2]}, TC, blockIdx.y, Q, W,
+                         partial + (int64_t)blockIdx.x * m * B);
+}
+
+template <typename T, int B, int CPT>
+bbl_status launch_gram_seg(int64_t n, int m_max, const int* d_m, const T* Q, const T* W, const int64_t* chunks,
+                           int nchunks, const int* active, double* partial, cudaStream_t st) {
+    const int cols = (m_max + CPT - 1) / CPT;
+    const int gy = (cols + kThreads - 1) / kThreads;
+    static bool attr_set = false;
+    if (!attr_set) {
+        BBL_CUDA(cudaFuncSetAttribute(gram_seg_dyn_kernel<T, B, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(double) * kThreads * CPT * B)));
+        attr_set = true;
+    }
+    dim3 grid((unsigned)nchunks, (unsigned)gy);
+    gram_seg_dyn_kernel<T, B, CPT><<<grid, kThreads, sizeof(double) * kThreads * CPT * B, st>>>(n, d_m, chunks, active,
+                                                                                                Q, W, partial);
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
+}
+
+template <typename T, bool SUB, typename TA, typename TO, int B>
+bbl_status launch_apply_seg(int64_t n, int kc, const int* ms, int mss, const int64_t* ctas, int nctas,
+                            const int* active, const T* Q, const double* C, int64_t cstride, TO* W, cudaStream_t st) {
+    if (kc == B)
+        apply_seg_kernel<T, B, B, SUB, TA, TO><<<nctas, kThreads, 0, st>>>(n, 0, ms, mss, kc, ctas, active, Q, C,
+                                                                          cstride, W);
+    else
+        apply_seg_kernel<T, B, 0, SUB, TA, TO><<<nctas, kThreads, 0, st>>>(n, 0, ms, mss, kc, ctas, active, Q, C,
+                                                                          cstride, W);
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
+}
+
+template <typename T, bool SUB, typename TA, typename TO>
+bbl_status apply_seg_typed(int64_t n, int b, int kc, const int* ms, int mss, const int64_t* ctas, int nctas,
+                           const int* active, const T* Q, const double* C, int64_t cstride, TO* W, cudaStream_t st) {
+    switch (b) {
+        case 1: return launch_apply_seg<T, SUB, TA, TO, 1>(n, kc, ms, mss, ctas, nctas, active, Q, C, cstride, W, st);
+        case 2: return launch_apply_seg<T, SUB, TA, TO, 2>(n, kc, ms, mss, ctas, nctas, active, Q, C, cstride, W, st);
+        case 4: return launch_apply_seg<T, SUB, TA, TO, 4>(n, kc, ms, mss, ctas, nctas, active, Q, C, cstride, W, st);
+        case 8: return launch_apply_seg<T, SUB, TA, TO, 8>(n, kc, ms, mss, ctas, nctas, active, Q, C, cstride, W, st);
+        case 16: return launch_apply_seg<T, SUB, TA, TO, 16>(n, kc, ms, mss, ctas, nctas, active, Q, C, cstride, W, st);
+        default: return set_error(BBL_ERR_UNSUPPORTED, "batched: b=%d (supported: 1, 2, 4, 8, 16)", b);
+    }
+}
+
+}  // namespace
+
+bbl_status gram_seg(int64_t n, int b, int m_max, const int* d_m, int dtype, const void* Q, const void* W,
+                    const int64_t* chunks, int nchunks, const int* seg_chunk_ptr, int nseg, const int* active,
+                    double* partial, double* C, cudaStream_t st) {
+    constexpr int kC = 4;
+    if (dtype == BBL_FP64) {
+        auto q = static_cast<const double*>(Q);
+        auto w = static_cast<const double*>(W);
+        switch (b) {
+            case 1: BBL_TRY((launch_gram_seg<double, 1, 1>(n, m_max, d_m, q, w, chunks, nchunks, active, partial, st))); break;
+            case 2: BBL_TRY((launch_gram_seg<double, 2, 2>(n, m_max, d_m, q, w, chunks, nchunks, active, partial, st))); break;
+            case 4: BBL_TRY((launch_gram_seg<double, 4, 2>(n, m_max, d_m, q, w, chunks, nchunks, active, partial, st))); break;
+            case 8: BBL_TRY((launch_gram_seg<double, 8, 2>(n, m_max, d_m, q, w, chunks, nchunks, active, partial, st))); break;
+            case 16: BBL_TRY((launch_gram_seg<double, 16, 2>(n, m_max, d_m, q, w, chunks, nchunks, active, partial, st))); break;
+            default: return set_error(BBL_ERR_UNSUPPORTED, "batched: b=%d", b);
+        }
+    } else {
+        auto q = static_cast<const float*>(Q);
+        auto w = static_cast<const float*>(W);
+        switch (b) {
+            case 1: BBL_TRY((launch_gram_seg<float, 1, 1>(n, m_max, d_m, q, w, chunks, nchunks, active, partial, st))); break;
+            case 2: BBL_TRY((launch_gram_seg<float, 2, 2>(n, m_max, d_m, q, w, chunks, nchunks, active, partial, st))); break;
+            case 4: BBL_TRY((launch_gram_seg<float, 4, kC>(n, m_max, d_m, q, w, chunks, nchunks, active, partial, st))); break;
+            case 8: BBL_TRY((launch_gram_seg<float, 8, kC>(n, m_max, d_m, q, w, chunks, nchunks, active, partial, st))); break;
+            case 16: BBL_TRY((launch_gram_seg<float, 16, 2>(n, m_max, d_m, q, w, chunks, nchunks, active, partial, st))); break;
+            default: return set_error(BBL_ERR_UNSUPPORTED, "batched: b=%d", b);
+        }
+    }
+    dim3 g((unsigned)ceil_div((int64_t)m_max * b, 256), (unsigned)nseg);
+    reduce_seg_kernel<<<g, 256, 0, st>>>(m_max, b, d_m, seg_chunk_ptr, active, partial, C);
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
+}
+
+bbl_status apply_seg(int64_t n, int b, int kc, const int* ms, int ms_stride, int dtype, const void* Q, const double* C,
+                     int64_t cstride, void* W, bool sub, bool f64_out, const int64_t* ctas, int nctas, const int* active,
+                     cudaStream_t st) {
+    if (dtype == BBL_FP64) {
+        auto q = static_cast<const double*>(Q);
+        if (sub) return apply_seg_typed<double, true, double, double>(n, b, kc, ms, ms_stride, ctas, nctas, active, q, C, cstride,
+                                                                      static_cast<double*>(W), st);
+        return apply_seg_typed<double, false, double, double>(n, b, kc, ms, ms_stride, ctas, nctas, active, q, C, cstride,
+                                                              static_cast<double*>(W), st);
+    }
+    auto q = static_cast<const float*>(Q);
+    if (f64_out)
+        return apply_seg_typed<float, false, double, double>(n, b, kc, ms, ms_stride, ctas, nctas, active, q, C, cstride,
+                                                             static_cast<double*>(W), st);
+    if (sub) return apply_seg_typed<float, true, float, float>(n, b, kc, ms, ms_stride, ctas, nctas, active, q, C, cstride,
+                                                               static_cast<float*>(W), st);
+    return apply_seg_typed<float, false, float, float>(n, b, kc, ms, ms_stride, ctas, nctas, active, q, C, cstride,
+                                                       static_cast<float*>(W), st);
+}
+
+bbl_status chol_seg(int b, int nseg, const double* G, const double* thresh2, int relative, double* R, double* Rinv,
+                    int* ndefl, int* mask, int* status, const int* active, cudaStream_t st) {
+    chol_seg_kernel<<<(unsigned)ceil_div(nseg, 32), 32, 0, st>>>(b, nseg, G, thresh2, relative, R, Rinv, ndefl, mask,
+                                                                 status, active);
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
+}
+
+bbl_status trmul_seg(int b, int nseg, const double* R2, const double* R1, double* B, const int* active, cudaStream_t st) {
+    trmul_seg_kernel<<<dim3(1, nseg), 256, 0, st>>>(b, nseg, R2, R1, B, active);
+    BBL_LAUNCH_CHECK();
     return BBL_OK;
 }
 
@@ -610,34 +1053,15 @@ bbl_status noalloc_scratch(double** out) {
 
 template <typename T, int B, int CPT>
 bbl_status launch_gram_fixed(int64_t n, int m, const T* Q, const T* W, double* C, double* scratch, cudaStream_t st) {
-    int cols = (m + CPT - 1) / CPT;
-    int TC = 1;
-    while (TC < cols && TC < kThreads) TC <<= 1;
-    const int gy = (cols + TC - 1) / TC;
-    const int RS = kThreads / TC;
+    // the first 64 doubles of the array hold the chunk tickets (zeroed by
+    // every call), the rest the per-worker partial sums
     const int64_t per_chunk = (int64_t)m * B;
-    if (per_chunk > kNoAllocScratchDoubles)
+    if (per_chunk > kNoAllocScratchDoubles - 64)
         return set_error(BBL_ERR_INVALID_ARG,
                          "block_gram_noalloc: nblocks*b*b = %lld exceeds the fixed scratch of %lld doubles",
-                         (long long)per_chunk, (long long)kNoAllocScratchDoubles);
-    const int64_t max_chunks = kNoAllocScratchDoubles / per_chunk;
-    int64_t target = std::max<int64_t>(1, std::min<int64_t>((152 * 4) / gy, max_chunks));
-    int64_t rpc = std::max<int64_t>(kRT * 4, ceil_div(n, target));
-    rpc = ceil_div(rpc, kRT) * kRT;
-    int64_t nch = std::max<int64_t>(1, ceil_div(n, rpc));
-    while (nch > max_chunks) {  // grow the chunks until the partials fit
-        rpc += kRT;
-        nch = ceil_div(n, rpc);
-    }
-    const size_t smem = RS > 1 ? sizeof(double) * kThreads * CPT * B : 0;
-    BBL_CUDA(cudaFuncSetAttribute(gram_kernel<T, B, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(sizeof(double) * kThreads * CPT * B)));
-    dim3 grid((unsigned)nch, (unsigned)gy);
-    gram_kernel<T, B, CPT><<<grid, kThreads, smem, st>>>(n, m, rpc, TC, Q, W, scratch);
-    BBL_LAUNCH_CHECK();
-    reduce_partials_kernel<<<(unsigned)ceil_div(per_chunk, 256), 256, 0, st>>>(per_chunk, (int)nch, scratch, C);
-    BBL_LAUNCH_CHECK();
-    return BBL_OK;
+                         (long long)per_chunk, (long long)(kNoAllocScratchDoubles - 64));
+    return gram_core<T, B, CPT>(n, m, Q, W, C, scratch + 64, kNoAllocScratchDoubles - 64,
+                                reinterpret_cast<int*>(scratch), st);
 }
 
 template <typename T>

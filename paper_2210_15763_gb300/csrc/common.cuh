@@ -126,6 +126,7 @@ struct bbl_matrix {
     bool has_csr = false;
     // SELL-C-sigma
     int sell_sigma = 0;
+    int spmm_lanes = 0;    // CSR lanes per row from the autotuner (0 = built-in rule)
     int64_t nslices = 0, padded_nnz = 0;
     bbl::DevBuf slice_ptr; // int64 [nslices+1], element offsets
     bbl::DevBuf sell_col;  // int32 [padded_nnz]

@@ -401,6 +401,13 @@ bbl_status bbl_matrix_info(const bbl_matrix* A, int64_t* n, int64_t* nnz, double
 }
 
 // diag(H) into a caller device buffer (FP64 [n]).
+bbl_status bbl_matrix_set_spmm_lanes(bbl_matrix* A, int lanes_per_row) {
+    if (!A || lanes_per_row < 0 || lanes_per_row > 32 || (lanes_per_row & (lanes_per_row - 1)))
+        return bbl::set_error(BBL_ERR_INVALID_ARG, "matrix_set_spmm_lanes: 0 or a power of two <= 32");
+    A->spmm_lanes = lanes_per_row;
+    return BBL_OK;
+}
+
 bbl_status bbl_matrix_diagonal(const bbl_matrix* A, double* d, void* stream) {
     if (!A || !d) return bbl::set_error(BBL_ERR_INVALID_ARG, "matrix_diagonal: NULL argument");
     BBL_CUDA(cudaMemcpyAsync(d, A->diag.p, sizeof(double) * A->n, cudaMemcpyDefault, bbl::as_stream(stream)));

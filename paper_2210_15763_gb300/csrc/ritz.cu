@@ -31,8 +31,18 @@ namespace {
 
 constexpr int kMaxP = kMaxB;            // bandwidth limit
 constexpr int kWin = kMaxP + 1;         // LDL^T window edge
-constexpr int kBisectWarps = 4;
+constexpr int kBisectWarps = 8;
+constexpr size_t kBandSmemMax = 160 * 1024;  // band bytes staged in shared memory
 constexpr int kMaxNev = 32;
+
+// Per-segment addressing for a batch of independent T's (blockIdx.y = segment
+// in bisect / invit, blockIdx.x in cluster).  The single-problem path passes
+// d_m = active = nullptr and zero strides.
+struct SegArgs {
+    const int* d_m;       // current order m in device memory (overrides the argument)
+    const int* active;    // per-segment flag; inactive segments are skipped
+    int64_t sT, sTh, sS, sWs, sTmp;
+};
 
 __device__ __forceinline__ double band_get(const double* __restrict__ Tb, int p, int m, int r, int c) {
     // T[r][c] for any r, c (0 outside the band or the matrix)
@@ -95,16 +105,32 @@ struct Bracket {
     double lo, hi;
 };
 
-__global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p, int nev, const double* __restrict__ Tb,
+__global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p, int nev, const double* __restrict__ Tg,
                                                                    double* __restrict__ theta_out,
-                                                                   double* __restrict__ width_out) {
+                                                                   double* __restrict__ width_out, int band_in_smem,
+                                                                   SegArgs sa) {
     __shared__ double win64[kBisectWarps][kWin * kWin];
     __shared__ float win32[kBisectWarps][kWin * kWin];
     __shared__ int counts[kBisectWarps];
     __shared__ double red[2][32 * kBisectWarps];
     __shared__ double s_lo, s_hi;
+    extern __shared__ double tb_sh[];
     const int i = blockIdx.x;
+    const int seg = blockIdx.y;
+    if (sa.active && !sa.active[seg]) return;
+    if (sa.d_m) m = *sa.d_m;
+    if (i >= min(nev, m)) return;
+    Tg += seg * sa.sT;
+    theta_out += seg * sa.sTh;
+    width_out += seg * sa.sTh;
     const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
+    // the elimination walks T row by row: keep its band in shared memory when it fits
+    const double* Tb = Tg;
+    if (band_in_smem) {
+        for (int e = tid; e < m * (p + 1); e += blockDim.x) tb_sh[e] = Tg[e];
+        __syncthreads();
+        Tb = tb_sh;
+    }
     // Gershgorin interval
     double gmin = 1e308, gmax = -1e308;
     for (int r = tid; r < m; r += blockDim.x) {
@@ -136,8 +162,8 @@ __global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p,
     const double pivmin32 = 1e-6 * scale;
     const double glo = s_lo, ghi = s_hi;
     double lo = glo, hi = ghi;
-    // phase 1: FP32 multisection to a 1e-4 * scale bracket
-    for (int round = 0; round < 40 && (hi - lo) > 1e-4 * scale; ++round) {
+    // phase 1: FP32 multisection to a 2e-5 * scale bracket
+    for (int round = 0; round < 40 && (hi - lo) > 2e-5 * scale; ++round) {
         const double sigma = lo + (hi - lo) * (double)(warp + 1) / (double)(kBisectWarps + 1);
         const int cnt = inertia_count<float>(Tb, p, m, sigma, pivmin32, win32[warp]);
         if (lane == 0) counts[warp] = cnt;
@@ -164,9 +190,10 @@ __global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p,
         hi = ghi;
     }
     __syncthreads();
-    // phase 3: FP64 multisection
+    // phase 3: FP64 multisection to 1e-9 * scale; inverse iteration and the
+    // Rayleigh quotient then give the eigenvalue to working precision
     for (int round = 0; round < 200; ++round) {
-        const double tolw = 1e-12 * scale + 1e-300;
+        const double tolw = 1e-9 * scale + 1e-300;
         if (hi - lo <= tolw) break;
         const double sigma = lo + (hi - lo) * (double)(warp + 1) / (double)(kBisectWarps + 1);
         const int cnt = inertia_count<double>(Tb, p, m, sigma, pivmin64, win64[warp]);
@@ -199,16 +226,32 @@ __device__ __forceinline__ double hash_uniform(uint64_t a, uint64_t b) {
 
 // Inverse iteration for eigenvalue i.  ws: per-eigenvalue workspace of
 // m*(3p+1) doubles + m ints (U rows of width 2p+1, L multipliers, pivots).
-__global__ void __launch_bounds__(32) invit_kernel(int m, int p, const double* __restrict__ Tb,
+__global__ void __launch_bounds__(32) invit_kernel(int m, int p, const double* __restrict__ Tg,
                                                     double* __restrict__ theta, double* __restrict__ S, int nev,
-                                                    double* __restrict__ ws, double scale_hint) {
+                                                    double* __restrict__ ws, double scale_hint, int band_in_smem,
+                                                    SegArgs sa) {
     extern __shared__ double sm[];
     const int i = blockIdx.x;
+    const int seg = blockIdx.y;
+    if (sa.active && !sa.active[seg]) return;
+    if (sa.d_m) m = *sa.d_m;
+    if (i >= min(nev, m)) return;
+    Tg += seg * sa.sT;
+    theta += seg * sa.sTh;
+    S += seg * sa.sS;
+    ws += seg * sa.sWs;
     const int lane = threadIdx.x;
     const int P1 = p + 1, UW = 2 * p + 1;
     double* win = sm;              // P1 x UW circular window
     double* x = win + P1 * UW;     // m
     double* lsh = x + m;           // p multipliers
+    const double* Tb = Tg;
+    if (band_in_smem) {            // band copy after the multipliers
+        double* tb = lsh + p + 8;
+        for (int e = lane; e < m * (p + 1); e += 32) tb[e] = Tg[e];
+        __syncwarp();
+        Tb = tb;
+    }
     double* U = ws + (int64_t)i * m * (3 * p + 1);
     double* L = U + (int64_t)m * UW;
     int* piv = reinterpret_cast<int*>(ws + (int64_t)nev * m * (3 * p + 1)) + (int64_t)i * m;
@@ -301,7 +344,7 @@ __global__ void __launch_bounds__(32) invit_kernel(int m, int p, const double* _
     // inverse iteration
     for (int r = lane; r < m; r += 32) x[r] = hash_uniform((uint64_t)i + 1, (uint64_t)r);
     __syncwarp();
-    for (int it = 0; it < 3; ++it) {
+    for (int it = 0; it < 2; ++it) {
         // forward: P and L
         for (int k = 0; k < m; ++k) {
             if (lane == 0) {
@@ -350,9 +393,9 @@ __global__ void __launch_bounds__(32) invit_kernel(int m, int p, const double* _
 
 // Groups close eigenvalues, orthonormalises their vectors, Rayleigh-Ritz in
 // each group (cyclic Jacobi), sorts, applies the sign convention.
-__global__ void __launch_bounds__(256) cluster_kernel(int m, int p, int nev, const double* __restrict__ Tb,
+__global__ void __launch_bounds__(256) cluster_kernel(int m, int p, int ldS, const double* __restrict__ Tb,
                                                       double* __restrict__ theta, double* __restrict__ S,
-                                                      double* __restrict__ tmp /* m x nev */) {
+                                                      double* __restrict__ tmp /* m x ldS */, SegArgs sa) {
     __shared__ double K[kMaxNev * kMaxNev];
     __shared__ double Z[kMaxNev * kMaxNev];
     __shared__ double red[256];
@@ -360,6 +403,14 @@ __global__ void __launch_bounds__(256) cluster_kernel(int m, int p, int nev, con
     __shared__ int start[kMaxNev + 1];
     __shared__ int ngroups;
     __shared__ double s_scale;
+    const int seg = blockIdx.x;
+    if (sa.active && !sa.active[seg]) return;
+    if (sa.d_m) m = *sa.d_m;
+    const int nev = min(ldS, m);  // columns computed; S keeps row stride ldS
+    Tb += seg * sa.sT;
+    theta += seg * sa.sTh;
+    S += seg * sa.sS;
+    tmp += seg * sa.sTmp;
     const int tid = threadIdx.x;
     // scale = max |theta|, at least the largest diagonal magnitude
     double sc = 0.0;
@@ -389,9 +440,9 @@ __global__ void __launch_bounds__(256) cluster_kernel(int m, int p, int nev, con
         __syncthreads();
         if (sel != a) {
             for (int r = tid; r < m; r += 256) {
-                const double t = S[(int64_t)r * nev + a];
-                S[(int64_t)r * nev + a] = S[(int64_t)r * nev + sel];
-                S[(int64_t)r * nev + sel] = t;
+                const double t = S[(int64_t)r * ldS + a];
+                S[(int64_t)r * ldS + a] = S[(int64_t)r * ldS + sel];
+                S[(int64_t)r * ldS + sel] = t;
             }
         }
         __syncthreads();
@@ -413,7 +464,7 @@ __global__ void __launch_bounds__(256) cluster_kernel(int m, int p, int nev, con
             for (int a = a0; a < a1; ++a) {
                 for (int q = a0; q < a; ++q) {
                     double s = 0.0;
-                    for (int r = tid; r < m; r += 256) s += S[(int64_t)r * nev + q] * S[(int64_t)r * nev + a];
+                    for (int r = tid; r < m; r += 256) s += S[(int64_t)r * ldS + q] * S[(int64_t)r * ldS + a];
                     red[tid] = s;
                     __syncthreads();
                     for (int w = 128; w > 0; w >>= 1) {
@@ -422,11 +473,11 @@ __global__ void __launch_bounds__(256) cluster_kernel(int m, int p, int nev, con
                     }
                     const double dot = red[0];
                     __syncthreads();
-                    for (int r = tid; r < m; r += 256) S[(int64_t)r * nev + a] -= dot * S[(int64_t)r * nev + q];
+                    for (int r = tid; r < m; r += 256) S[(int64_t)r * ldS + a] -= dot * S[(int64_t)r * ldS + q];
                     __syncthreads();
                 }
                 double s = 0.0;
-                for (int r = tid; r < m; r += 256) s += S[(int64_t)r * nev + a] * S[(int64_t)r * nev + a];
+                for (int r = tid; r < m; r += 256) s += S[(int64_t)r * ldS + a] * S[(int64_t)r * ldS + a];
                 red[tid] = s;
                 __syncthreads();
                 for (int w = 128; w > 0; w >>= 1) {
@@ -435,7 +486,7 @@ __global__ void __launch_bounds__(256) cluster_kernel(int m, int p, int nev, con
                 }
                 const double inv = 1.0 / sqrt(red[0]);
                 __syncthreads();
-                for (int r = tid; r < m; r += 256) S[(int64_t)r * nev + a] *= inv;
+                for (int r = tid; r < m; r += 256) S[(int64_t)r * ldS + a] *= inv;
                 __syncthreads();
             }
         }
@@ -443,8 +494,8 @@ __global__ void __launch_bounds__(256) cluster_kernel(int m, int p, int nev, con
         for (int r = tid; r < m; r += 256) {
             for (int a = a0; a < a1; ++a) {
                 double t = 0.0;
-                for (int c = max(0, r - p); c <= min(m - 1, r + p); ++c) t += band_get(Tb, p, m, r, c) * S[(int64_t)c * nev + a];
-                tmp[(int64_t)r * nev + a] = t;
+                for (int c = max(0, r - p); c <= min(m - 1, r + p); ++c) t += band_get(Tb, p, m, r, c) * S[(int64_t)c * ldS + a];
+                tmp[(int64_t)r * ldS + a] = t;
             }
         }
         __syncthreads();
@@ -452,7 +503,7 @@ __global__ void __launch_bounds__(256) cluster_kernel(int m, int p, int nev, con
         for (int e = 0; e < k * k; ++e) {
             const int a = a0 + e / k, q = a0 + e % k;
             double s = 0.0;
-            for (int r = tid; r < m; r += 256) s += S[(int64_t)r * nev + a] * tmp[(int64_t)r * nev + q];
+            for (int r = tid; r < m; r += 256) s += S[(int64_t)r * ldS + a] * tmp[(int64_t)r * ldS + q];
             red[tid] = s;
             __syncthreads();
             for (int w = 128; w > 0; w >>= 1) {
@@ -521,11 +572,11 @@ __global__ void __launch_bounds__(256) cluster_kernel(int m, int p, int nev, con
         // S_g <- S_g Z
         for (int r = tid; r < m; r += 256) {
             double row[kMaxNev];
-            for (int a = 0; a < k; ++a) row[a] = S[(int64_t)r * nev + a0 + a];
+            for (int a = 0; a < k; ++a) row[a] = S[(int64_t)r * ldS + a0 + a];
             for (int a = 0; a < k; ++a) {
                 double s = 0.0;
                 for (int q = 0; q < k; ++q) s += row[q] * Z[q * k + a];
-                S[(int64_t)r * nev + a0 + a] = s;
+                S[(int64_t)r * ldS + a0 + a] = s;
             }
         }
         __syncthreads();
@@ -535,7 +586,7 @@ __global__ void __launch_bounds__(256) cluster_kernel(int m, int p, int nev, con
         double best = -1.0;
         int bi = 0;
         for (int r = tid; r < m; r += 256) {
-            const double v = fabs(S[(int64_t)r * nev + a]);
+            const double v = fabs(S[(int64_t)r * ldS + a]);
             if (v > best) {
                 best = v;
                 bi = r;
@@ -555,10 +606,10 @@ __global__ void __launch_bounds__(256) cluster_kernel(int m, int p, int nev, con
             }
             __syncthreads();
         }
-        const bool flip = S[(int64_t)bix[0] * nev + a] < 0.0;
+        const bool flip = S[(int64_t)bix[0] * ldS + a] < 0.0;
         __syncthreads();
         if (flip)
-            for (int r = tid; r < m; r += 256) S[(int64_t)r * nev + a] = -S[(int64_t)r * nev + a];
+            for (int r = tid; r < m; r += 256) S[(int64_t)r * ldS + a] = -S[(int64_t)r * ldS + a];
         __syncthreads();
     }
     for (int k = tid; k < nev; k += 256) theta[k] = th[k];
@@ -571,6 +622,18 @@ size_t ritz_workspace_bytes(int m, int p, int nev) {
            sizeof(int) * (size_t)nev * m + 256;
 }
 
+namespace {
+bbl_status set_ritz_attrs() {
+    static bool attr_set = false;
+    if (!attr_set) {
+        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024)));
+        attr_set = true;
+    }
+    return BBL_OK;
+}
+}  // namespace
+
 bbl_status ritz_dev(int m, int p, int nev, const double* Tb, double* theta, double* S, DevBuf& work, cudaStream_t st) {
     const size_t need = ritz_workspace_bytes(m, p, nev);
     if (work.bytes < need) BBL_TRY(work.alloc(need + need / 2));
@@ -579,15 +642,53 @@ bbl_status ritz_dev(int m, int p, int nev, const double* Tb, double* theta, doub
                                       sizeof(int) * (size_t)nev * m + 64);
     width = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(width) + 15) & ~uintptr_t(15));
     double* tmp = width + nev + 2;
-    bisect_kernel<<<nev, 32 * kBisectWarps, 0, st>>>(m, p, nev, Tb, theta, width);
+    const size_t band_bytes = sizeof(double) * (size_t)m * (p + 1);
+    const int band_smem = band_bytes <= kBandSmemMax ? 1 : 0;
+    BBL_TRY(set_ritz_attrs());
+    const SegArgs one{nullptr, nullptr, 0, 0, 0, 0, 0};
+    bisect_kernel<<<nev, 32 * kBisectWarps, band_smem ? band_bytes : 0, st>>>(m, p, nev, Tb, theta, width, band_smem,
+                                                                              one);
     BBL_LAUNCH_CHECK();
-    const size_t smem = sizeof(double) * ((size_t)(p + 1) * (2 * p + 1) + m + p + 8);
-    if (smem > 48 * 1024) {
-        BBL_CUDA(cudaFuncSetAttribute(invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    }
-    invit_kernel<<<nev, 32, smem, st>>>(m, p, Tb, theta, S, nev, ws, 0.0);
+    const size_t base = sizeof(double) * ((size_t)(p + 1) * (2 * p + 1) + m + p + 8);
+    const int inv_smem = (base + band_bytes <= 200 * 1024) ? 1 : 0;
+    const size_t smem = base + (inv_smem ? band_bytes : 0);
+    if (smem > 200 * 1024) return set_error(BBL_ERR_UNSUPPORTED, "ritz: m=%d too large for the inverse iteration", m);
+    invit_kernel<<<nev, 32, smem, st>>>(m, p, Tb, theta, S, nev, ws, 0.0, inv_smem, one);
     BBL_LAUNCH_CHECK();
-    cluster_kernel<<<1, 256, 0, st>>>(m, p, nev, Tb, theta, S, tmp);
+    cluster_kernel<<<1, 256, 0, st>>>(m, p, nev, Tb, theta, S, tmp, one);
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
+}
+
+// Per-segment workspace (doubles) for orders up to m_max.
+size_t ritz_seg_workspace_doubles(int m_max, int p, int nev) {
+    const size_t d = (size_t)nev * m_max * (3 * p + 1) + (sizeof(int) * (size_t)nev * m_max + 7) / 8 + 16;
+    return (d + 31) & ~size_t(31);
+}
+
+// Batched Ritz solves: nseg independent band matrices Tb + s*sT (order *d_m,
+// at most m_max, bandwidth p), k = min(nev, m) lowest pairs each into
+// theta + s*sTh and S + s*sS (row stride nev); segments with active[s] == 0
+// are skipped.  ws: nseg * ritz_seg_workspace_doubles; tmp: nseg * m_max * nev.
+bbl_status ritz_dev_batched(int m_max, int p, int nev, int nseg, const double* Tb, int64_t sT, double* theta,
+                            int64_t sTh, double* width, double* S, int64_t sS, double* ws, double* tmp, const int* d_m,
+                            const int* active, cudaStream_t st) {
+    BBL_TRY(set_ritz_attrs());
+    const size_t band_bytes = sizeof(double) * (size_t)m_max * (p + 1);
+    const int band_smem = band_bytes <= kBandSmemMax ? 1 : 0;
+    const int64_t sWs = (int64_t)ritz_seg_workspace_doubles(m_max, p, nev);
+    const SegArgs sa{d_m, active, sT, sTh, sS, sWs, (int64_t)m_max * nev};
+    dim3 g(nev, nseg);
+    bisect_kernel<<<g, 32 * kBisectWarps, band_smem ? band_bytes : 0, st>>>(m_max, p, nev, Tb, theta, width, band_smem,
+                                                                            sa);
+    BBL_LAUNCH_CHECK();
+    const size_t base = sizeof(double) * ((size_t)(p + 1) * (2 * p + 1) + m_max + p + 8);
+    const int inv_smem = (base + band_bytes <= 200 * 1024) ? 1 : 0;
+    const size_t smem = base + (inv_smem ? band_bytes : 0);
+    if (smem > 200 * 1024) return set_error(BBL_ERR_UNSUPPORTED, "ritz: m=%d too large for the inverse iteration", m_max);
+    invit_kernel<<<g, 32, smem, st>>>(m_max, p, Tb, theta, S, nev, ws, 0.0, inv_smem, sa);
+    BBL_LAUNCH_CHECK();
+    cluster_kernel<<<nseg, 256, 0, st>>>(m_max, p, nev, Tb, theta, S, tmp, sa);
     BBL_LAUNCH_CHECK();
     return BBL_OK;
 }

@@ -58,15 +58,16 @@ __global__ void fill_B_kernel(int j, int b, int rows_alloc, const double* __rest
     Tb[(int64_t)row * (b + 1) + (b + r - c)] = Bj[r * b + c];
 }
 
-// est_i = || B_j S[m-b .. m-1, i] ||_2, written into the report
-__global__ void estimate_kernel(int m, int b, int k, const double* __restrict__ Bj, const double* __restrict__ S,
+// est_i = || B_j S[m-b .. m-1, i] ||_2 with B_j read from rows m..m+b-1 of
+// the band (upper triangular: B_j[r][c] at d = b + r - c, c >= r)
+__global__ void estimate_kernel(int m, int b, int k, const double* __restrict__ Tb, const double* __restrict__ S,
                                 double* __restrict__ est) {
     const int i = threadIdx.x;
     if (i >= k) return;
     double s2 = 0.0;
     for (int r = 0; r < b; ++r) {
         double t = 0.0;
-        for (int c = 0; c < b; ++c) t += Bj[r * b + c] * S[(int64_t)(m - b + c) * k + i];
+        for (int c = r; c < b; ++c) t += Tb[(int64_t)(m + r) * (b + 1) + (b + r - c)] * S[(int64_t)(m - b + c) * k + i];
         s2 += t * t;
     }
     est[i] = sqrt(s2);
@@ -166,7 +167,7 @@ struct Timer {
 
 struct StageOut {
     std::vector<double> theta, est;
-    int iters = 0, deflations = 0, nev_eff = 0;
+    int iters = 0, deflations = 0, nev_eff = 0, spmm_calls = 0;
     bool converged = false;
     double t_spmm = 0, t_reorth = 0, t_chol = 0, t_ritz = 0, t_other = 0;
     double spmm_bytes = 0, reorth_bytes = 0;
@@ -317,13 +318,96 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     BBL_CUDA(cudaStreamSynchronize(st));
     if (h_ndefl[0] > 0) BBL_TRY(replace_deflated(0, blockp(0), d_mask));
 
+    // The Ritz solve of T_j runs on a side stream while the main stream goes
+    // on with block j+1 (whose SpMM does not need it); the host checks the
+    // result of T_j after enqueuing block j+1.  When T_j has converged, block
+    // j+1 was speculative and is not used.
     Timer tm;
     BBL_TRY(tm.init());
+    cudaStream_t side = nullptr;
+    BBL_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    struct SideGuard {
+        cudaStream_t s;
+        cudaEvent_t e[6];
+        ~SideGuard() {
+            if (s) {
+                cudaStreamSynchronize(s);
+                cudaStreamDestroy(s);
+            }
+            for (auto& x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } guard{side, {}};
+    for (int q = 0; q < 6; ++q) BBL_CUDA(cudaEventCreate(&guard.e[q]));
+    cudaEvent_t* ev_main = guard.e;       // [2] main-stream block done
+    cudaEvent_t* ev_r0 = guard.e + 2;     // [2] Ritz start
+    cudaEvent_t* ev_r1 = guard.e + 4;     // [2] Ritz done (report in host memory)
+    DevBuf theta2, S2, est2;
+    BBL_TRY(theta2.alloc(sizeof(double) * 2 * 64));
+    BBL_TRY(S2.alloc(sizeof(double) * 2 * (size_t)m_max * nev));
+    BBL_TRY(est2.alloc(sizeof(double) * 2 * 64));
+    DevBuf rwork2;
+    BBL_TRY(rwork2.alloc(ritz_workspace_bytes(m_max, b, nev) + 1024));
+    DevBuf* rw[2] = {&rwork, &rwork2};
     std::vector<double> prev_theta;
     int last_defl = 0;
     out.converged = false;
+    int pending = -1;      // block whose Ritz report is in flight
+    int final_j = -1;      // block whose Ritz pairs are returned
+    int final_k = 0;
+    auto launch_ritz = [&](int jj) -> bbl_status {
+        const int m = (jj + 1) * b;
+        const int k = std::min(nev, m);
+        const int slot = jj & 1;
+        BBL_CUDA(cudaStreamWaitEvent(side, ev_main[slot], 0));
+        BBL_CUDA(cudaEventRecord(ev_r0[slot], side));
+        double* th = theta2.as<double>() + 64 * slot;
+        double* Sd = S2.as<double>() + (size_t)slot * m_max * nev;
+        double* es = est2.as<double>() + 64 * slot;
+        BBL_TRY(ritz_dev(m, b, k, Tb.as<double>(), th, Sd, *rw[slot], side));
+        // B_jj sits in rows (jj+1)b.. of the band: the estimate reads it there
+        estimate_kernel<<<1, 64, 0, side>>>(m, b, k, Tb.as<double>(), Sd, es);
+        BBL_LAUNCH_CHECK();
+        BBL_CUDA(cudaMemcpyAsync(h_theta + 32 * slot, th, sizeof(double) * k, cudaMemcpyDeviceToHost, side));
+        BBL_CUDA(cudaMemcpyAsync(h_est + 32 * slot, es, sizeof(double) * k, cudaMemcpyDeviceToHost, side));
+        BBL_CUDA(cudaEventRecord(ev_r1[slot], side));
+        return BBL_OK;
+    };
+    // waits for the report of block jj; returns 1 when converged
+    auto check_ritz = [&](int jj, bool* done) -> bbl_status {
+        const int m = (jj + 1) * b;
+        const int k = std::min(nev, m);
+        const int slot = jj & 1;
+        BBL_CUDA(cudaEventSynchronize(ev_r1[slot]));
+        out.t_ritz += [&] { float t = 0.f; cudaEventElapsedTime(&t, ev_r0[slot], ev_r1[slot]); return (double)t; }();
+        const double* ht = h_theta + 32 * slot;
+        const double* he = h_est + 32 * slot;
+        for (int i = 0; i < k; ++i)
+            if (!std::isfinite(ht[i]) || !std::isfinite(he[i]))
+                return set_error(BBL_ERR_NUMERICAL, "solve: non-finite Ritz value at block %d", jj);
+        out.theta.assign(ht, ht + k);
+        out.est.assign(he, he + k);
+        *done = false;
+        if (k == nev) {
+            if (o.criterion == 1) {
+                if (prev_theta.size() == (size_t)nev) {
+                    double ss = 0.0;
+                    for (int i = 0; i < nev; ++i) ss += (ht[i] - prev_theta[i]) * (ht[i] - prev_theta[i]);
+                    *done = std::sqrt(ss / nev) < o.rms_tol;
+                }
+            } else {
+                *done = true;
+                for (int i = 0; i < nev; ++i) *done = *done && (he[i] <= tol * nrm);
+            }
+        }
+        prev_theta.assign(ht, ht + k);
+        final_j = jj;
+        final_k = k;
+        return BBL_OK;
+    };
     int j = 0;
-    for (j = 0; j < J_max; ++j) {
+    bool stop = false;
+    for (j = 0; j < J_max && !stop; ++j) {
         char* Vj = blockp(j);
         char* Wn = (j + 1 < J_max) ? blockp(j + 1) : Z.as<char>();
         BBL_CUDA(cudaEventRecord(tm.ev[0], st));
@@ -344,69 +428,60 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         fill_B_kernel<<<1, 256, 0, st>>>(j, b, t_rows, bj.as<double>(), Tb.as<double>());
         BBL_LAUNCH_CHECK();
         BBL_CUDA(cudaEventRecord(tm.ev[3], st));
-        const int m = (j + 1) * b;
-        const int k = std::min(nev, m);
-        const bool check = ((j + 1) % std::max(1, o.check_every) == 0) || (j == J_max - 1) || k < nev;
-        if (check) {
-            BBL_TRY(ritz_dev(m, b, k, Tb.as<double>(), theta_dev, S.as<double>(), rwork, st));
-            estimate_kernel<<<1, 64, 0, st>>>(m, b, k, bj.as<double>(), S.as<double>(), d_est);
-            BBL_LAUNCH_CHECK();
-            BBL_CUDA(cudaMemcpyAsync(h_theta, theta_dev, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
-            BBL_CUDA(cudaMemcpyAsync(h_est, d_est, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
-        }
+        BBL_CUDA(cudaEventRecord(ev_main[j & 1], st));
         BBL_CUDA(cudaMemcpyAsync(h_ndefl, d_ndefl, sizeof(int), cudaMemcpyDeviceToHost, st));
-        BBL_CUDA(cudaEventRecord(tm.ev[4], st));
         BBL_CUDA(cudaStreamSynchronize(st));
         out.t_spmm += tm.ms(0, 1);
         out.t_reorth += tm.ms(1, 2);
         out.t_chol += tm.ms(2, 3);
-        out.t_ritz += tm.ms(3, 4);
-        out.iters = j + 1;
-        out.nev_eff = k;
         {
+            const int m = (j + 1) * b;
             const double sx = (double)s;
             const double sv = (A->storage == BBL_FP64 || (f64_spmm && A->val64.p)) ? 8.0 : 4.0;
             out.spmm_bytes += (double)A->nnz * (sv + 4.0) + (double)(n + 1) * 8.0 + 2.0 * (double)n * b * sx;
             out.reorth_bytes += 2.0 * (2.0 * (double)n * m * sx + 3.0 * (double)n * b * sx);
         }
-        bool done = false;
-        if (check) {
-            for (int i = 0; i < k; ++i)
-                if (!std::isfinite(h_theta[i]) || !std::isfinite(h_est[i]))
-                    return set_error(BBL_ERR_NUMERICAL, "solve: non-finite Ritz value at block %d", j);
-            out.theta.assign(h_theta, h_theta + k);
-            out.est.assign(h_est, h_est + k);
-            if (k == nev) {
-                if (o.criterion == 1) {
-                    if (prev_theta.size() == (size_t)nev) {
-                        double ss = 0.0;
-                        for (int i = 0; i < nev; ++i) ss += (h_theta[i] - prev_theta[i]) * (h_theta[i] - prev_theta[i]);
-                        done = std::sqrt(ss / nev) < o.rms_tol;
-                    }
-                } else {
-                    done = true;
-                    for (int i = 0; i < nev; ++i) done = done && (h_est[i] <= tol * nrm);
-                }
+        out.spmm_calls = j + 1;
+        const bool last = (j == J_max - 1);
+        const bool want = ((j + 1) % std::max(1, o.check_every) == 0) || last || (j + 1) * b < nev;
+        if (want) {
+            // a new Ritz solve may reuse the buffers of block j-2 only: the one of block j-1 is pending
+            BBL_TRY(launch_ritz(j));
+        }
+        if (pending >= 0) {
+            bool done = false;
+            BBL_TRY(check_ritz(pending, &done));
+            pending = -1;
+            if (done) {
+                out.converged = true;
+                stop = true;
+                break;
             }
-            prev_theta.assign(h_theta, h_theta + k);
         }
-        if (done) {
-            out.converged = true;
-            break;
-        }
-        if (j == J_max - 1) break;
+        if (want) pending = j;
+        if (last) break;
         if (h_ndefl[0] > last_defl) {
             BBL_TRY(replace_deflated(j + 1, Wn, d_mask));
             last_defl = h_ndefl[0];
             if (exhausted) break;  // no direction left to extend the basis with
         }
     }
+    if (pending >= 0 && !stop) {
+        bool done = false;
+        BBL_TRY(check_ritz(pending, &done));
+        out.converged = done;
+    }
+    BBL_CUDA(cudaStreamSynchronize(side));
     out.deflations = last_defl;
-    // Ritz vectors X = Q S (k columns)
-    const int nb = out.iters;
-    const int k = out.nev_eff;
+    if (final_j < 0) return set_error(BBL_ERR_NUMERICAL, "solve: no Ritz solve completed");
+    out.iters = final_j + 1;
+    out.nev_eff = final_k;
+    const int slot = final_j & 1;
+    BBL_CUDA(cudaMemcpyAsync(theta_dev, theta2.as<double>() + 64 * slot, sizeof(double) * final_k,
+                             cudaMemcpyDeviceToDevice, st));
+    // Ritz vectors X = Q S (k columns) from the blocks of the returned T
     BBL_CUDA(cudaEventRecord(tm.ev[0], st));
-    BBL_TRY(ritz_vectors(n, b, nb, dtype, basis.p, k, S.as<double>(), X, st));
+    BBL_TRY(ritz_vectors(n, b, out.iters, dtype, basis.p, final_k, S2.as<double>() + (size_t)slot * m_max * nev, X, st));
     BBL_CUDA(cudaEventRecord(tm.ev[1], st));
     BBL_CUDA(cudaStreamSynchronize(st));
     out.t_other += tm.ms(0, 1);
@@ -501,8 +576,8 @@ bbl_status solve_impl(const bbl_matrix* A, int nev, int b, const double* pivot, 
         stats->t_total_ms = tt;
         const double sv = mixed ? 4.0 : 8.0;
         stats->spmm_bytes = (double)A->nnz * (sv + 4.0) + (double)(n + 1) * 8.0 + 2.0 * (double)n * b * sv;
-        stats->spmm_gbs = s1.t_spmm > 0 ? stats->spmm_bytes * s1.iters / (s1.t_spmm * 1e-3) / 1e9 : 0.0;
-        stats->ns_per_op = s1.t_spmm > 0 ? s1.t_spmm * 1e6 / ((double)A->nnz * b * s1.iters) : 0.0;
+        stats->spmm_gbs = s1.t_spmm > 0 ? s1.spmm_bytes / (s1.t_spmm * 1e-3) / 1e9 : 0.0;
+        stats->ns_per_op = s1.t_spmm > 0 ? s1.t_spmm * 1e6 / ((double)A->nnz * b * s1.spmm_calls) : 0.0;
         stats->spmm_bytes_total = s1.spmm_bytes + s2.spmm_bytes;
         stats->reorth_bytes_total = s1.reorth_bytes + s2.reorth_bytes;
     }

@@ -158,8 +158,37 @@ __global__ void __launch_bounds__(256) spmm_sell_kernel(int64_t nslices, const i
     TX acc[B];
 #pragma unroll
     for (int q = 0; q < B; ++q) acc[q] = TX(0);
-#pragma unroll 2
-    for (int k = 0; k < len; ++k) {
+    // Each nonzero is a dependent pair of loads (column index, then the
+    // gathered row of V); batches of U nonzeros issue all index loads, then
+    // all gathers, so that U gathers per lane are in flight at once.
+    constexpr int U = (B * sizeof(TX) <= 32) ? 8 : 4;
+    int k = 0;
+    for (; k + U <= len; k += U) {
+        int c[U];
+        TX h[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            c[u] = __ldg(sc + base + (int64_t)(k + u) * kSellC);
+            h[u] = (TX)__ldg(sv + base + (int64_t)(k + u) * kSellC);
+        }
+        TX v[U][B];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const TX* vp = V + (int64_t)c[u] * B;
+#pragma unroll
+            for (int ch = 0; ch < NCH; ++ch) {
+                TX t[CH];
+                load_pack<TX, CH>(vp + ch * CH, t);
+#pragma unroll
+                for (int q = 0; q < CH; ++q) v[u][ch * CH + q] = t[q];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int q = 0; q < B; ++q) acc[q] = fma(h[u], v[u][q], acc[q]);
+    }
+    for (; k < len; ++k) {
         const int c = __ldg(sc + base + (int64_t)k * kSellC);
         const TX h = (TX)__ldg(sv + base + (int64_t)k * kSellC);
         const TX* vp = V + (int64_t)c * B;
@@ -249,7 +278,7 @@ int default_group(const bbl_matrix* A) {
 template <typename TM, typename TX>
 bbl_status spmm_typed(const bbl_matrix* A, int b, const TM* csr_val, const TM* sell_val, const TX* V, TX* W,
                       cudaStream_t st, int G) {
-    if (G <= 0) G = default_group(A);
+    if (G <= 0) G = A->spmm_lanes > 0 ? A->spmm_lanes : default_group(A);
     const bool pow2 = (b == 1 || b == 2 || b == 4 || b == 8 || b == 16);
     if (A->fmt == BBL_SELL && sell_val) {
         const int64_t blocks = ceil_div(A->nslices * 32, 256);
