@@ -441,9 +441,70 @@ def run_batched(args):
     print(json.dumps(out))
 
 
+def run_learned(args):
+    """The learned-pivot form on H(g) = H0 + g V (H0: the n = 1e6 Kronecker
+    matrix, V: six more coupling terms), 64 values g ~ U(0,1): 48 training
+    solves (bootstrapped pivot, FP32 stage + FP64 polish) build the stored
+    basis U (64 eigenvectors at 8 training g) and the targets; the MLP
+    (1 -> 128 -> 128 -> 64*8, GELU) is trained on the GPU; on the 16 held-out
+    g the iterations and times to residual 1e-8 are compared for the learned
+    (gated) pivot, the bootstrapped pivot and a random pivot."""
+    import torch
+    import synth
+    import paper_2210_15763_gb300 as bbl
+    from paper_2210_15763_gb300 import learned
+    b = nev = 8
+    trunc = max(64, int(round(20000 * args.family_scale ** 2)))
+    h0, v = synth.learned_family(scale=args.family_scale)
+    gs = synth.family_g()
+    make = lambda g: synth.family_matrix(h0, v, g, fp32_values=True)
+    t0 = time.time()
+    lp = learned.fit(make, gs[:48], nev=nev, b=b, trunc_dim=trunc, n_basis_g=8, hidden=128, epochs=args.epochs,
+                     lr=1e-3, seed=0, tol=TOL, storage="fp32", fmt="csr")
+    t_fit = time.time() - t0
+    rows = []
+    for g in gs[48:]:
+        A = bbl.Matrix(make(g), storage="fp32", fmt="csr")
+        ev = torch.cuda.Event(enable_timing=True)
+        ee = torch.cuda.Event(enable_timing=True)
+        out = {"g": float(g)}
+        ev.record()
+        r_l, info = learned.solve_with_learned_pivot(A, lp, g, b, trunc, tol=TOL)
+        ee.record()
+        torch.cuda.synchronize()
+        out.update(learned_iters=r_l.stats["iters"] + r_l.stats["polish_iters"], learned_s=ev.elapsed_time(ee) / 1e3,
+                   **info)
+        ev.record()
+        P = bbl.pivot_bootstrap(A, trunc, b, sub_tol=1e-10)
+        r_b = bbl.solve(A, nev, b, pivot=P, tol=TOL)
+        ee.record()
+        torch.cuda.synchronize()
+        out.update(boot_iters=r_b.stats["iters"] + r_b.stats["polish_iters"], boot_s=ev.elapsed_time(ee) / 1e3)
+        ev.record()
+        r_r = bbl.solve(A, nev, b, pivot=None, seed=7, tol=TOL)
+        ee.record()
+        torch.cuda.synchronize()
+        out.update(random_iters=r_r.stats["iters"] + r_r.stats["polish_iters"], random_s=ev.elapsed_time(ee) / 1e3,
+                   max_eval_diff=float(np.max(np.abs(r_l.evals - r_r.evals))),
+                   converged=bool(r_l.converged and r_b.converged and r_r.converged))
+        rows.append(out)
+        A.close()
+    mean = lambda k: float(np.mean([r[k] for r in rows]))
+    res = {"mode": "learned", "n": int(h0.n), "held_out": len(rows), "fit_s": t_fit,
+           "train_loss_first_last": [float(lp.loss[0]), float(lp.loss[-1])], "epochs": args.epochs,
+           "mean_iters": {"learned": mean("learned_iters"), "bootstrap": mean("boot_iters"),
+                          "random": mean("random_iters")},
+           "mean_time_s": {"learned": mean("learned_s"), "bootstrap": mean("boot_s"), "random": mean("random_s")},
+           "learned_used_fraction": mean("learned_used"), "all_converged": all(r["converged"] for r in rows),
+           "max_eval_diff_learned_vs_random": max(r["max_eval_diff"] for r in rows), "per_g": rows}
+    print(json.dumps(res))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--mode", default="solve", choices=["solve", "kernels", "batched"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "kernels", "batched", "learned"])
+    ap.add_argument("--epochs", type=int, default=3000)
+    ap.add_argument("--family-scale", type=float, default=1.0)
     ap.add_argument("--count", type=int, default=256)
     ap.add_argument("--batch-max-vectors", type=int, default=400)
     ap.add_argument("--scale", type=float, default=0.5)
@@ -461,6 +522,8 @@ def main():
         run_kernels(args)
     elif args.mode == "batched":
         run_batched(args)
+    elif args.mode == "learned":
+        run_learned(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -157,7 +157,7 @@ bbl_status cholqr2_dev(int64_t n, int b, int dtype, void* W, double* B, double d
                        int* d_deflmask, DevBuf& partials, DevBuf& small, cudaStream_t st);
 // ritz.cu
 bbl_status ritz_dev(int m, int p, int nev, const double* Tband, double* theta, double* S, DevBuf& work,
-                    cudaStream_t st);
+                    cudaStream_t st, const double* warm = nullptr, int warm_count = 0);
 // rng.cu
 bbl_status fill_normal(int64_t n, int b, uint64_t seed, uint64_t offset, double* P, cudaStream_t st);
 bbl_status fill_uniform_cols(int64_t n, int b, int dtype, uint64_t seed, uint64_t offset, const int* mask,

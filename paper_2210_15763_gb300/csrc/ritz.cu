@@ -108,7 +108,8 @@ struct Bracket {
 __global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p, int nev, const double* __restrict__ Tg,
                                                                    double* __restrict__ theta_out,
                                                                    double* __restrict__ width_out, int band_in_smem,
-                                                                   SegArgs sa) {
+                                                                   SegArgs sa, const double* __restrict__ warm,
+                                                                   int warm_count) {
     __shared__ double win64[kBisectWarps][kWin * kWin];
     __shared__ float win32[kBisectWarps][kWin * kWin];
     __shared__ int counts[kBisectWarps];
@@ -159,11 +160,23 @@ __global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p,
     // pivots smaller than these are replaced by -pivmin (a perturbation of T
     // far below the bracket widths used): keeps the elimination finite
     const double pivmin64 = 1e-14 * scale;
-    const double pivmin32 = 1e-6 * scale;
+    const double pivmin32 = 1e-7 * scale;
     const double glo = s_lo, ghi = s_hi;
     double lo = glo, hi = ghi;
-    // phase 1: FP32 multisection to a 2e-5 * scale bracket
-    for (int round = 0; round < 40 && (hi - lo) > 2e-5 * scale; ++round) {
+    if (warm && i < warm_count) {
+        // T of an earlier block is a leading principal submatrix of this T, so
+        // its i-th Ritz value bounds this one from above (Cauchy interlacing);
+        // a guessed lower end is checked with the final FP64 counts below
+        const double w = warm[i];
+        hi = fmin(ghi, w + 1e-9 * scale);
+        lo = fmax(glo, w - 1e-3 * scale);
+        if (!(lo < hi)) {
+            lo = glo;
+            hi = ghi;
+        }
+    }
+    // phase 1: FP32 multisection to a 1e-6 * scale bracket
+    for (int round = 0; round < 40 && (hi - lo) > 1e-6 * scale; ++round) {
         const double sigma = lo + (hi - lo) * (double)(warp + 1) / (double)(kBisectWarps + 1);
         const int cnt = inertia_count<float>(Tb, p, m, sigma, pivmin32, win32[warp]);
         if (lane == 0) counts[warp] = cnt;
@@ -185,14 +198,17 @@ __global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p,
         if (lane == 0) counts[warp] = cnt;
     }
     __syncthreads();
-    if (!(counts[0] <= i && counts[1] > i)) {
+    const bool verified = counts[0] <= i && counts[1] > i;
+    __syncthreads();
+    // phase 3 (only when the FP32 bracket failed the FP64 check): FP64
+    // multisection from the Gershgorin interval to 1e-9 * scale.  Otherwise
+    // the 1e-6 * scale bracket goes straight to inverse iteration, whose
+    // Rayleigh quotient gives the eigenvalue to working precision.
+    if (!verified) {
         lo = glo;
         hi = ghi;
     }
-    __syncthreads();
-    // phase 3: FP64 multisection to 1e-9 * scale; inverse iteration and the
-    // Rayleigh quotient then give the eigenvalue to working precision
-    for (int round = 0; round < 200; ++round) {
+    for (int round = 0; round < 200 && !verified; ++round) {
         const double tolw = 1e-9 * scale + 1e-300;
         if (hi - lo <= tolw) break;
         const double sigma = lo + (hi - lo) * (double)(warp + 1) / (double)(kBisectWarps + 1);
@@ -344,7 +360,7 @@ __global__ void __launch_bounds__(32) invit_kernel(int m, int p, const double* _
     // inverse iteration
     for (int r = lane; r < m; r += 32) x[r] = hash_uniform((uint64_t)i + 1, (uint64_t)r);
     __syncwarp();
-    for (int it = 0; it < 2; ++it) {
+    for (int it = 0; it < 3; ++it) {
         // forward: P and L
         for (int k = 0; k < m; ++k) {
             if (lane == 0) {
@@ -634,7 +650,8 @@ bbl_status set_ritz_attrs() {
 }
 }  // namespace
 
-bbl_status ritz_dev(int m, int p, int nev, const double* Tb, double* theta, double* S, DevBuf& work, cudaStream_t st) {
+bbl_status ritz_dev(int m, int p, int nev, const double* Tb, double* theta, double* S, DevBuf& work, cudaStream_t st,
+                    const double* warm, int warm_count) {
     const size_t need = ritz_workspace_bytes(m, p, nev);
     if (work.bytes < need) BBL_TRY(work.alloc(need + need / 2));
     double* ws = work.as<double>();
@@ -647,7 +664,7 @@ bbl_status ritz_dev(int m, int p, int nev, const double* Tb, double* theta, doub
     BBL_TRY(set_ritz_attrs());
     const SegArgs one{nullptr, nullptr, 0, 0, 0, 0, 0};
     bisect_kernel<<<nev, 32 * kBisectWarps, band_smem ? band_bytes : 0, st>>>(m, p, nev, Tb, theta, width, band_smem,
-                                                                              one);
+                                                                              one, warm, warm_count);
     BBL_LAUNCH_CHECK();
     const size_t base = sizeof(double) * ((size_t)(p + 1) * (2 * p + 1) + m + p + 8);
     const int inv_smem = (base + band_bytes <= 200 * 1024) ? 1 : 0;
@@ -680,7 +697,7 @@ bbl_status ritz_dev_batched(int m_max, int p, int nev, int nseg, const double* T
     const SegArgs sa{d_m, active, sT, sTh, sS, sWs, (int64_t)m_max * nev};
     dim3 g(nev, nseg);
     bisect_kernel<<<g, 32 * kBisectWarps, band_smem ? band_bytes : 0, st>>>(m_max, p, nev, Tb, theta, width, band_smem,
-                                                                            sa);
+                                                                            sa, nullptr, 0);
     BBL_LAUNCH_CHECK();
     const size_t base = sizeof(double) * ((size_t)(p + 1) * (2 * p + 1) + m_max + p + 8);
     const int inv_smem = (base + band_bytes <= 200 * 1024) ? 1 : 0;

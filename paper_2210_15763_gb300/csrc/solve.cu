@@ -353,6 +353,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     int last_defl = 0;
     out.converged = false;
     int pending = -1;      // block whose Ritz report is in flight
+    int warm_k = 0;        // Ritz values available from the previous solve
     int final_j = -1;      // block whose Ritz pairs are returned
     int final_k = 0;
     auto launch_ritz = [&](int jj) -> bbl_status {
@@ -364,7 +365,10 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         double* th = theta2.as<double>() + 64 * slot;
         double* Sd = S2.as<double>() + (size_t)slot * m_max * nev;
         double* es = est2.as<double>() + 64 * slot;
-        BBL_TRY(ritz_dev(m, b, k, Tb.as<double>(), th, Sd, *rw[slot], side));
+        // warm start from the previous Ritz solve on this stream (other slot)
+        const double* warm = warm_k > 0 ? theta2.as<double>() + 64 * (slot ^ 1) : nullptr;
+        BBL_TRY(ritz_dev(m, b, k, Tb.as<double>(), th, Sd, *rw[slot], side, warm, warm_k));
+        warm_k = k;
         // B_jj sits in rows (jj+1)b.. of the band: the estimate reads it there
         estimate_kernel<<<1, 64, 0, side>>>(m, b, k, Tb.as<double>(), Sd, es);
         BBL_LAUNCH_CHECK();

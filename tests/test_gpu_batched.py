@@ -14,8 +14,8 @@ def _family(count=7, seed=3):
     mats = []
     rng = np.random.default_rng(seed)
     for s in range(count):
-        nP = int(rng.integers(12, 40))
-        nN = int(rng.integers(10, 30))
+        nP = int(rng.integers(24, 48))
+        nN = int(rng.integers(20, 36))
         f = synth.kron_factors(nP, nN, K=4, c=3.0, seed=100 + s)
         mats.append(synth.assemble(f))
     return mats
@@ -27,7 +27,7 @@ def test_batched_solve_matches_dense_eigensolves(storage):
     mats = _family()
     B = bbl.Batch(mats, storage=storage)
     tol = 1e-10 if storage == "fp64" else 1e-6
-    ev, rs, it, st, stats = B.solve(4, 4, use_graph=True, tol=tol, max_vectors=160, seed=11)
+    ev, rs, it, st, stats = B.solve(4, 4, use_graph=True, tol=tol, max_vectors=400, seed=11)
     assert np.all(st == 0), st
     for s, A in enumerate(mats):
         want = np.linalg.eigvalsh(A.to_dense())[:4]
