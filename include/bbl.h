@@ -79,7 +79,14 @@ typedef struct {
                                    reach `tol`; needs an FP64 copy of the values
                                    (bbl_matrix_create keeps one when asked)       */
     double stage1_tol;          /* FP32 stage tolerance when polishing (default 2e-6) */
-    int check_every;            /* Ritz solve every k-th block (default 1)         */
+    int check_every;            /* k > 0: Ritz solve (convergence test) after every
+                                   k-th block; 0 (default): adaptive, from the decay
+                                   rate of the last two residual estimates the next
+                                   test is placed at half the predicted distance to
+                                   convergence (at most 8 blocks ahead), so that the
+                                   run stops at most a few blocks after the first
+                                   block that passes.  The rms-change criterion
+                                   always tests every block.                       */
     void* stream;               /* cudaStream_t                                    */
 } bbl_options;
 
@@ -97,6 +104,7 @@ typedef struct {
     double spmm_bytes_total;    /* algorithmic bytes of every SpMM of the call     */
     double reorth_bytes_total;  /* algorithmic bytes of every Gram-Schmidt pass:
                                    per pass 2*n*m*s + 3*n*b*s (m basis columns)    */
+    int ritz_solves;            /* Ritz solves (convergence tests) of all stages   */
 } bbl_stats;
 
 void bbl_options_default(bbl_options* opt);

@@ -71,7 +71,7 @@ void bbl_options_default(bbl_options* o) {
     o->storage = BBL_FP64;
     o->polish = 1;
     o->stage1_tol = 2e-6;
-    o->check_every = 1;
+    o->check_every = 0;
     o->stream = nullptr;
 }
 

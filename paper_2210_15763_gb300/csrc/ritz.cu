@@ -175,31 +175,41 @@ __global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p,
             hi = ghi;
         }
     }
-    // phase 1: FP32 multisection to a 1e-6 * scale bracket
-    for (int round = 0; round < 40 && (hi - lo) > 1e-6 * scale; ++round) {
-        const double sigma = lo + (hi - lo) * (double)(warp + 1) / (double)(kBisectWarps + 1);
-        const int cnt = inertia_count<float>(Tb, p, m, sigma, pivmin32, win32[warp]);
-        if (lane == 0) counts[warp] = cnt;
-        __syncthreads();
-        double nlo = lo, nhi = hi;
-        for (int w = 0; w < kBisectWarps; ++w) {
-            const double s = lo + (hi - lo) * (double)(w + 1) / (double)(kBisectWarps + 1);
-            if (counts[w] <= i) nlo = fmax(nlo, s);
-            else nhi = fmin(nhi, s);
+    // phase 1: FP32 multisection to a 1e-6 * scale bracket, checked with FP64
+    // counts at its ends (warp 0 at lo, warp 1 at hi).  A warm bracket that
+    // fails the check (the value moved further down than guessed) is retried
+    // once from the Gershgorin interval.
+    const bool warm_used = warm && i < warm_count && !(lo == glo && hi == ghi);
+    bool verified = false;
+    for (int attempt = 0; attempt < (warm_used ? 2 : 1) && !verified; ++attempt) {
+        if (attempt == 1) {
+            lo = glo;
+            hi = ghi;
+        }
+        for (int round = 0; round < 40 && (hi - lo) > 1e-6 * scale; ++round) {
+            const double sigma = lo + (hi - lo) * (double)(warp + 1) / (double)(kBisectWarps + 1);
+            const int cnt = inertia_count<float>(Tb, p, m, sigma, pivmin32, win32[warp]);
+            if (lane == 0) counts[warp] = cnt;
+            __syncthreads();
+            double nlo = lo, nhi = hi;
+            for (int w = 0; w < kBisectWarps; ++w) {
+                const double s = lo + (hi - lo) * (double)(w + 1) / (double)(kBisectWarps + 1);
+                if (counts[w] <= i) nlo = fmax(nlo, s);
+                else nhi = fmin(nhi, s);
+            }
+            __syncthreads();
+            if (nlo >= nhi) break;  // inconsistent FP32 counts: stop, the FP64 check decides
+            lo = nlo;
+            hi = nhi;
+        }
+        if (warp < 2) {
+            const int cnt = inertia_count<double>(Tb, p, m, warp == 0 ? lo : hi, pivmin64, win64[warp]);
+            if (lane == 0) counts[warp] = cnt;
         }
         __syncthreads();
-        if (nlo >= nhi) break;  // inconsistent FP32 counts: stop, the FP64 check below decides
-        lo = nlo;
-        hi = nhi;
+        verified = counts[0] <= i && counts[1] > i;
+        __syncthreads();
     }
-    // phase 2: check the bracket in FP64 (warp 0 at lo, warp 1 at hi)
-    if (warp < 2) {
-        const int cnt = inertia_count<double>(Tb, p, m, warp == 0 ? lo : hi, pivmin64, win64[warp]);
-        if (lane == 0) counts[warp] = cnt;
-    }
-    __syncthreads();
-    const bool verified = counts[0] <= i && counts[1] > i;
-    __syncthreads();
     // phase 3 (only when the FP32 bracket failed the FP64 check): FP64
     // multisection from the Gershgorin interval to 1e-9 * scale.  Otherwise
     // the 1e-6 * scale bracket goes straight to inverse iteration, whose
@@ -360,7 +370,10 @@ __global__ void __launch_bounds__(32) invit_kernel(int m, int p, const double* _
     // inverse iteration
     for (int r = lane; r < m; r += 32) x[r] = hash_uniform((uint64_t)i + 1, (uint64_t)r);
     __syncwarp();
-    for (int it = 0; it < 3; ++it) {
+    // the shift is within 1e-6 * scale of the eigenvalue and other eigenvalues
+    // closer than 1e-3 * scale are handled as a cluster, so each iteration
+    // shrinks the other components by 5e-4 or more: five give working precision
+    for (int it = 0; it < 5; ++it) {
         // forward: P and L
         for (int k = 0; k < m; ++k) {
             if (lane == 0) {

@@ -167,7 +167,7 @@ struct Timer {
 
 struct StageOut {
     std::vector<double> theta, est;
-    int iters = 0, deflations = 0, nev_eff = 0, spmm_calls = 0;
+    int iters = 0, deflations = 0, nev_eff = 0, spmm_calls = 0, ritz_solves = 0;
     bool converged = false;
     double t_spmm = 0, t_reorth = 0, t_chol = 0, t_ritz = 0, t_other = 0;
     double spmm_bytes = 0, reorth_bytes = 0;
@@ -225,6 +225,37 @@ bbl_status finish_vectors(const bbl_matrix* A, int k, double* X, const double* t
     }
     return BBL_OK;
 }
+
+// When to run the Ritz solve (the convergence test of Sec. II.B).  every > 0:
+// after every `every`-th block.  every == 0: adaptive.  The residual
+// estimates of block Lanczos fall roughly geometrically; from the last two
+// tests, rho = max_i est_i / (tol ||H||) and its per-block decay give a
+// predicted number of blocks to convergence, and the next test is placed at
+// half of it (1..8 blocks ahead), so a run stops at most a few blocks after
+// the first block that passes.  Until two decreasing tests exist, every
+// block is tested.
+struct CheckPlan {
+    int every = 1;
+    int next = 0;
+    int n_pts = 0;
+    int j_prev = -1;
+    double l_prev = 0.0;
+    bool want(int j) const { return every > 0 ? ((j + 1) % every == 0) : (j >= next); }
+    void report(int jj, double rho) {
+        if (every > 0) return;
+        const double l = std::log(std::max(rho, 1e-300));
+        int step = 1;
+        if (n_pts > 0 && jj > j_prev && l < l_prev && l > 0.0) {
+            const double rate = (l_prev - l) / (double)(jj - j_prev);
+            const double blocks = l / rate;
+            step = (int)std::min(8.0, std::max(1.0, std::floor(0.5 * blocks)));
+        }
+        j_prev = jj;
+        l_prev = l;
+        ++n_pts;
+        next = jj + step;
+    }
+};
 
 // One block Lanczos run from an FP64 device pivot (n x b).  dtype: storage of
 // the blocks; f64_spmm: FP64 arithmetic in the SpMM.  On return X (device
@@ -356,6 +387,8 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     int warm_k = 0;        // Ritz values available from the previous solve
     int final_j = -1;      // block whose Ritz pairs are returned
     int final_k = 0;
+    CheckPlan plan;
+    plan.every = (o.check_every > 0 || o.criterion == 1) ? std::max(1, o.check_every) : 0;
     auto launch_ritz = [&](int jj) -> bbl_status {
         const int m = (jj + 1) * b;
         const int k = std::min(nev, m);
@@ -392,7 +425,11 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         out.theta.assign(ht, ht + k);
         out.est.assign(he, he + k);
         *done = false;
+        ++out.ritz_solves;
         if (k == nev) {
+            double rho = 0.0;
+            for (int i = 0; i < nev; ++i) rho = std::max(rho, he[i] / (tol * nrm));
+            plan.report(jj, rho);
             if (o.criterion == 1) {
                 if (prev_theta.size() == (size_t)nev) {
                     double ss = 0.0;
@@ -447,7 +484,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         }
         out.spmm_calls = j + 1;
         const bool last = (j == J_max - 1);
-        const bool want = ((j + 1) % std::max(1, o.check_every) == 0) || last || (j + 1) * b < nev;
+        const bool want = plan.want(j) || last || (j + 1) * b < nev;
         if (want) {
             // a new Ritz solve may reuse the buffers of block j-2 only: the one of block j-1 is pending
             BBL_TRY(launch_ritz(j));
@@ -584,6 +621,7 @@ bbl_status solve_impl(const bbl_matrix* A, int nev, int b, const double* pivot, 
         stats->ns_per_op = s1.t_spmm > 0 ? s1.t_spmm * 1e6 / ((double)A->nnz * b * s1.spmm_calls) : 0.0;
         stats->spmm_bytes_total = s1.spmm_bytes + s2.spmm_bytes;
         stats->reorth_bytes_total = s1.reorth_bytes + s2.reorth_bytes;
+        stats->ritz_solves = s1.ritz_solves + s2.ritz_solves;
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);

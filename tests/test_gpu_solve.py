@@ -38,7 +38,7 @@ def test_solve_fp64_kron_small_vs_oracle(b):
     piv = OR.normal_block(5, H.n, b)
     ref = OL.block_lanczos(H, nev, b, piv, tol=1e-8)
     M = bbl.Matrix(H)
-    res = bbl.solve(M, nev, b, pivot=piv, tol=1e-8)
+    res = bbl.solve(M, nev, b, pivot=piv, tol=1e-8, check_every=1)
     assert res.converged and ref.converged
     _check_eigs(res, ref.evals, H, 1e-8)
     assert abs(res.stats["iters"] - ref.iters) <= 1
@@ -53,17 +53,33 @@ def test_solve_fp64_full_size_config_n2e4_vs_oracle():
     H = synth.kron_matrix("kron_n2e4")
     piv = OR.normal_block(20221028, H.n, 4)
     ref = OL.block_lanczos(H, 4, 4, piv, tol=1e-8)
-    res = bbl.solve(bbl.Matrix(H), 4, 4, pivot=piv, tol=1e-8)
+    res = bbl.solve(bbl.Matrix(H), 4, 4, pivot=piv, tol=1e-8, check_every=1)
     assert res.converged
     _check_eigs(res, ref.evals, H, 1e-8)
     assert abs(res.stats["iters"] - ref.iters) <= 1
+    assert res.stats["ritz_solves"] >= res.stats["iters"]
+
+
+def test_adaptive_convergence_tests_stop_within_a_few_blocks_of_the_oracle():
+    """check_every=0 (the default) tests convergence at predicted blocks only:
+    far fewer Ritz solves, the same eigenpairs, and a stop at most a few
+    blocks after the first block that passes (the oracle tests every block)."""
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4")
+    piv = OR.normal_block(20221028, H.n, 4)
+    ref = OL.block_lanczos(H, 4, 4, piv, tol=1e-8)
+    res = bbl.solve(bbl.Matrix(H), 4, 4, pivot=piv, tol=1e-8)
+    assert res.converged
+    _check_eigs(res, ref.evals, H, 1e-8)
+    assert ref.iters - 1 <= res.stats["iters"] <= ref.iters + 4
+    assert res.stats["ritz_solves"] < 0.6 * res.stats["iters"]
 
 
 def test_solve_random_pivot_null_uses_the_published_generator():
     torch, bbl = need_gpu()
     H = synth.kron_matrix("kron_n2e4", scale=0.3)
     ref = OL.block_lanczos(H, 4, 4, OP.random_pivot(H.n, 4, 99), tol=1e-8)
-    res = bbl.solve(bbl.Matrix(H), 4, 4, pivot=None, seed=99, tol=1e-8)
+    res = bbl.solve(bbl.Matrix(H), 4, 4, pivot=None, seed=99, tol=1e-8, check_every=1)
     _check_eigs(res, ref.evals, H, 1e-8)
     assert abs(res.stats["iters"] - ref.iters) <= 1
 
