@@ -74,10 +74,15 @@ typedef struct {
                                    BBL_FP32 (mixed precision: FP32 blocks and SpMM,
                                    FP64 coefficients, Gram, T, residual).  Must
                                    match the matrix storage.                       */
-    int polish;                 /* FP32 storage only: 1 (default) restarts FP64
-                                   block Lanczos from the FP32 Ritz vectors to
-                                   reach `tol`; needs an FP64 copy of the values
-                                   (bbl_matrix_create keeps one when asked)       */
+    int polish;                 /* FP32 storage only: 1 (default) restarts block
+                                   Lanczos from the FP32 Ritz vectors to reach
+                                   `tol`, with float-float blocks (pairs of FP32
+                                   numbers, ~48-bit significands, products on the
+                                   FP32 pipes) and FP64 coefficients, Gram and T;
+                                   2: the same restart with FP64 blocks and FP64
+                                   arithmetic (on an FP64 copy of the values when
+                                   bbl_matrix_create kept one); 0: no polish.
+                                   The reported residuals are FP64 products.      */
     double stage1_tol;          /* FP32 stage tolerance when polishing (default 2e-6) */
     int check_every;            /* k > 0: Ritz solve (convergence test) after every
                                    k-th block; 0 (default): adaptive, from the decay

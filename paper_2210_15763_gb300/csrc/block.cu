@@ -19,13 +19,29 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "df32.cuh"
 
 namespace bbl {
 namespace {
 
 template <typename T, int N>
 __device__ __forceinline__ void ldvec(const T* p, T (&out)[N]) {
-    if constexpr (N * sizeof(T) == 16) {
+    if constexpr (is_df32<T>::value) {
+        if constexpr (N % 2 == 0) {
+#pragma unroll
+            for (int q = 0; q < N; q += 2) {
+                const float4 x = __ldg(reinterpret_cast<const float4*>(p + q));
+                out[q] = df32(x.x, x.y);
+                out[q + 1] = df32(x.z, x.w);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < N; ++q) {
+                const float2 x = __ldg(reinterpret_cast<const float2*>(p + q));
+                out[q] = df32(x.x, x.y);
+            }
+        }
+    } else if constexpr (N * sizeof(T) == 16) {
         if constexpr (sizeof(T) == 8) {
             double2 x = __ldg(reinterpret_cast<const double2*>(p));
             out[0] = x.x;
@@ -711,6 +727,8 @@ bbl_status gram(int64_t n, int b, int nblocks, int dtype, const void* Q, const v
     const int m = nblocks * b;
     if (dtype == BBL_FP64)
         return gram_typed<double>(n, b, m, static_cast<const double*>(Q), static_cast<const double*>(W), C, partials, st);
+    if (dtype == kDF32)
+        return gram_typed<df32>(n, b, m, static_cast<const df32*>(Q), static_cast<const df32*>(W), C, partials, st);
     return gram_typed<float>(n, b, m, static_cast<const float*>(Q), static_cast<const float*>(W), C, partials, st);
 }
 
@@ -719,6 +737,9 @@ bbl_status update(int64_t n, int b, int nblocks, int dtype, const void* Q, const
     if (dtype == BBL_FP64)
         return apply_typed<double, true, double, double>(n, b, m, b, static_cast<const double*>(Q), C,
                                                          static_cast<double*>(W), st);
+    if (dtype == kDF32)
+        return apply_typed<df32, true, df32, df32>(n, b, m, b, static_cast<const df32*>(Q), C, static_cast<df32*>(W),
+                                                   st);
     return apply_typed<float, true, float, float>(n, b, m, b, static_cast<const float*>(Q), C, static_cast<float*>(W),
                                                   st);
 }
@@ -728,6 +749,8 @@ bbl_status ritz_vectors(int64_t n, int b, int nblocks, int dtype, const void* Q,
     const int m = nblocks * b;
     if (dtype == BBL_FP64)
         return apply_typed<double, false, double, double>(n, b, m, k, static_cast<const double*>(Q), S, X, st);
+    if (dtype == kDF32)
+        return apply_typed<df32, false, df32, double>(n, b, m, k, static_cast<const df32*>(Q), S, X, st);
     return apply_typed<float, false, double, double>(n, b, m, k, static_cast<const float*>(Q), S, X, st);
 }
 
@@ -741,6 +764,15 @@ bbl_status self_gram(int64_t n, int b, int dtype, const void* W, double* G, DevB
             case 2: return launch_syrk<double, 2>(n, w, G, partials, st);
             case 4: return launch_syrk<double, 4>(n, w, G, partials, st);
             case 8: return launch_syrk<double, 8>(n, w, G, partials, st);
+            default: break;
+        }
+    } else if (dtype == kDF32) {
+        auto w = static_cast<const df32*>(W);
+        switch (b) {
+            case 1: return launch_syrk<df32, 1>(n, w, G, partials, st);
+            case 2: return launch_syrk<df32, 2>(n, w, G, partials, st);
+            case 4: return launch_syrk<df32, 4>(n, w, G, partials, st);
+            case 8: return launch_syrk<df32, 8>(n, w, G, partials, st);
             default: break;
         }
     } else {
@@ -774,6 +806,9 @@ bbl_status cholqr2_dev(int64_t n, int b, int dtype, void* W, double* B, double d
     if (dtype == BBL_FP64)
         BBL_TRY((apply_typed<double, false, double, double>(n, b, b, b, static_cast<double*>(W), R1i,
                                                              static_cast<double*>(W), st)));
+    else if (dtype == kDF32)
+        BBL_TRY((apply_typed<df32, false, df32, df32>(n, b, b, b, static_cast<df32*>(W), R1i, static_cast<df32*>(W),
+                                                       st)));
     else
         BBL_TRY((apply_typed<float, false, float, float>(n, b, b, b, static_cast<float*>(W), R1i,
                                                           static_cast<float*>(W), st)));
@@ -785,6 +820,9 @@ bbl_status cholqr2_dev(int64_t n, int b, int dtype, void* W, double* B, double d
     if (dtype == BBL_FP64)
         BBL_TRY((apply_typed<double, false, double, double>(n, b, b, b, static_cast<double*>(W), R2i,
                                                              static_cast<double*>(W), st)));
+    else if (dtype == kDF32)
+        BBL_TRY((apply_typed<df32, false, df32, df32>(n, b, b, b, static_cast<df32*>(W), R2i, static_cast<df32*>(W),
+                                                       st)));
     else
         BBL_TRY((apply_typed<float, false, float, float>(n, b, b, b, static_cast<float*>(W), R2i,
                                                           static_cast<float*>(W), st)));

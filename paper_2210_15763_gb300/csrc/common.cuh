@@ -49,7 +49,10 @@ void count_launch();
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-inline size_t dtype_size(int dt) { return dt == BBL_FP64 ? 8 : 4; }
+// Internal block type of the polish stage: float-float pairs (df32.cuh), 8 bytes.
+constexpr int kDF32 = 2;
+
+inline size_t dtype_size(int dt) { return (dt == BBL_FP64 || dt == kDF32) ? 8 : 4; }
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -145,6 +148,8 @@ namespace bbl {
 // spmm.cu
 bbl_status spmm_dispatch(const bbl_matrix* A, int b, const void* V, void* W, bool f64_arith, cudaStream_t st,
                          int rows_per_warp_hint = 0);
+// W = H V with float-float blocks V, W (n x b pairs) and FP32 matrix values
+bbl_status spmm_df32(const bbl_matrix* A, int b, const void* V, void* W, cudaStream_t st);
 // block.cu
 struct BlockWork;  // scratch for Gram/reorth/CholQR2
 bbl_status gram(int64_t n, int b, int nblocks, int dtype, const void* Q, const void* W, double* C,

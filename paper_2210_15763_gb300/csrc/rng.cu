@@ -5,6 +5,7 @@
 // Used for random pivots (Sec. III "randomly constructed pivot") and for the
 // replacement directions of deflated columns.
 #include "common.cuh"
+#include "df32.cuh"
 
 namespace bbl {
 namespace {
@@ -56,6 +57,8 @@ bbl_status fill_uniform_cols(int64_t n, int b, int dtype, uint64_t seed, uint64_
                              cudaStream_t st) {
     if (dtype == BBL_FP64)
         uniform_cols_kernel<double><<<152 * 8, 256, 0, st>>>(n, b, seed, offset, mask, static_cast<double*>(Z));
+    else if (dtype == kDF32)
+        uniform_cols_kernel<df32><<<152 * 8, 256, 0, st>>>(n, b, seed, offset, mask, static_cast<df32*>(Z));
     else
         uniform_cols_kernel<float><<<152 * 8, 256, 0, st>>>(n, b, seed, offset, mask, static_cast<float*>(Z));
     BBL_LAUNCH_CHECK();

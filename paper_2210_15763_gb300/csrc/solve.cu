@@ -15,14 +15,18 @@
 //
 // Mixed precision (FP32 storage): stage 1 runs the same loop on FP32
 // blocks with FP32 SpMM and FP64 coefficients / Gram / T / residual, to
-// stage1_tol; stage 2 ("polish") restarts FP64 block Lanczos from the stage-1
+// stage1_tol; stage 2 ("polish") restarts block Lanczos from the stage-1
 // Ritz vectors -- the bootstrapping idea of Sec. II.B applied across
-// precisions -- until the FP64 residuals meet tol.
+// precisions -- until the FP64 residuals meet tol.  The polish keeps its
+// blocks as float-float pairs (about 48 bits, products on the FP32 pipes;
+// df32.cuh) with FP64 coefficients, Gram and T, or in plain FP64 (polish = 2).
+// The residuals that decide convergence are always FP64 SpMM products.
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "common.cuh"
+#include "df32.cuh"
 
 namespace bbl {
 
@@ -308,10 +312,12 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     // pivot -> block 0 in storage precision, orthonormalised (relative deflation)
     if (dtype == BBL_FP64)
         BBL_CUDA(cudaMemcpyAsync(blockp(0), pivot_dev, sizeof(double) * n * b, cudaMemcpyDeviceToDevice, st));
+    else if (dtype == kDF32)
+        convert_kernel<double, df32><<<cg, 256, 0, st>>>(n * b, pivot_dev, reinterpret_cast<df32*>(blockp(0)));
     else
         convert_kernel<double, float><<<cg, 256, 0, st>>>(n * b, pivot_dev, reinterpret_cast<float*>(blockp(0)));
     BBL_LAUNCH_CHECK();
-    const double defl_tol = o.defl_tol > 0 ? o.defl_tol : (dtype == BBL_FP64 ? 1e-10 : 1e-6);
+    const double defl_tol = o.defl_tol > 0 ? o.defl_tol : (dtype == BBL_FP32 ? 1e-6 : 1e-10);
     const double thresh2 = (defl_tol * nrm) * (defl_tol * nrm);
     uint64_t defl_counter = 0;
     bool exhausted = false;
@@ -339,6 +345,8 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             if (hm[c] && hm[kMaxB + c]) exhausted = true;
         if (dtype == BBL_FP64)
             merge_cols_kernel<double><<<cg, 256, 0, st>>>(n, b, mask_dev, Z.as<double>(), reinterpret_cast<double*>(Wn));
+        else if (dtype == kDF32)
+            merge_cols_kernel<df32><<<cg, 256, 0, st>>>(n, b, mask_dev, Z.as<df32>(), reinterpret_cast<df32*>(Wn));
         else
             merge_cols_kernel<float><<<cg, 256, 0, st>>>(n, b, mask_dev, Z.as<float>(), reinterpret_cast<float*>(Wn));
         BBL_LAUNCH_CHECK();
@@ -454,7 +462,8 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         BBL_CUDA(cudaEventRecord(tm.ev[0], st));
         // W = H V_j is formed directly in the next basis slot and turned into
         // V_{j+1} there (Gram-Schmidt only reads blocks 0..j)
-        BBL_TRY(spmm_dispatch(A, b, Vj, Wn, f64_spmm, st));
+        if (dtype == kDF32) BBL_TRY(spmm_df32(A, b, Vj, Wn, st));
+        else BBL_TRY(spmm_dispatch(A, b, Vj, Wn, f64_spmm, st));
         BBL_CUDA(cudaEventRecord(tm.ev[1], st));
         double* C1 = coeff.as<double>();
         double* C2 = C1 + (size_t)m_max * b;
@@ -478,7 +487,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         {
             const int m = (j + 1) * b;
             const double sx = (double)s;
-            const double sv = (A->storage == BBL_FP64 || (f64_spmm && A->val64.p)) ? 8.0 : 4.0;
+            const double sv = (A->storage == BBL_FP64 || (dtype != kDF32 && f64_spmm && A->val64.p)) ? 8.0 : 4.0;
             out.spmm_bytes += (double)A->nnz * (sv + 4.0) + (double)(n + 1) * 8.0 + 2.0 * (double)n * b * sx;
             out.reorth_bytes += 2.0 * (2.0 * (double)n * m * sx + 3.0 * (double)n * b * sx);
         }
@@ -583,7 +592,10 @@ bbl_status solve_impl(const bbl_matrix* A, int nev, int b, const double* pivot, 
             BBL_CUDA(cudaMemcpyAsync(piv.p, X.p, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, st));
             bbl_options o2 = o;
             o2.criterion = 0;
-            BBL_TRY(lanczos_stage(A, nev, k, piv.as<double>(), BBL_FP64, true, o.tol, o2, st, X.as<double>(),
+            // polish 1: float-float blocks and products (FP32 pipes, ~48-bit);
+            // polish 2: FP64 blocks and FP64 arithmetic
+            const int pdt = o.polish == 2 ? BBL_FP64 : kDF32;
+            BBL_TRY(lanczos_stage(A, nev, k, piv.as<double>(), pdt, true, o.tol, o2, st, X.as<double>(),
                                   theta.as<double>(), s2));
             k = s2.nev_eff;
             BBL_TRY(finish_vectors(A, k, X.as<double>(), theta.as<double>(), res.data(), scratch, st));

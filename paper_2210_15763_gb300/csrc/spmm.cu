@@ -16,7 +16,10 @@
 // accumulation type).  FP64 storage uses <double, double>; the
 // mixed-precision form uses <float, float>; its FP64 residual product uses
 // <float, double>.
+#include <type_traits>
+
 #include "common.cuh"
+#include "df32.cuh"
 
 namespace bbl {
 namespace {
@@ -33,9 +36,29 @@ struct alignas(N * sizeof(T) >= 16 ? 16 : N * sizeof(T)) Pack {
     T v[N];
 };
 
+// type of the matrix value in the product: float-float blocks multiply by the
+// FP32 value itself
+template <typename TM, typename TX>
+using HType = std::conditional_t<is_df32<TX>::value, float, TX>;
+
 template <typename T, int N>
 __device__ __forceinline__ void load_pack(const T* __restrict__ p, T (&out)[N]) {
-    if constexpr (N * sizeof(T) == 16) {
+    if constexpr (is_df32<T>::value) {
+        if constexpr (N % 2 == 0) {
+#pragma unroll
+            for (int q = 0; q < N; q += 2) {
+                const float4 x = __ldg(reinterpret_cast<const float4*>(p + q));
+                out[q] = df32(x.x, x.y);
+                out[q + 1] = df32(x.z, x.w);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < N; ++q) {
+                const float2 x = __ldg(reinterpret_cast<const float2*>(p + q));
+                out[q] = df32(x.x, x.y);
+            }
+        }
+    } else if constexpr (N * sizeof(T) == 16) {
         if constexpr (sizeof(T) == 8) {
             double2 x = __ldg(reinterpret_cast<const double2*>(p));
             out[0] = x.x;
@@ -59,7 +82,13 @@ __device__ __forceinline__ void load_pack(const T* __restrict__ p, T (&out)[N]) 
 
 template <typename T, int N>
 __device__ __forceinline__ void store_pack(T* p, const T (&v)[N]) {
-    if constexpr (N * sizeof(T) == 16) {
+    if constexpr (is_df32<T>::value) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            const df32 r = dfm::renorm(v[q].hi, v[q].lo);
+            *reinterpret_cast<float2*>(p + q) = make_float2(r.hi, r.lo);
+        }
+    } else if constexpr (N * sizeof(T) == 16) {
         if constexpr (sizeof(T) == 8) {
             *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
         } else {
@@ -93,7 +122,7 @@ __global__ void __launch_bounds__(256) spmm_csr_kernel(int64_t n, const int64_t*
 #pragma unroll 4
     for (int64_t k = s + slot; k < e; k += NPS) {
         const int c = __ldg(ci + k);
-        const TX h = (TX)__ldg(va + k);
+        const HType<TM, TX> h = (HType<TM, TX>)__ldg(va + k);
         TX v[VEC];
         load_pack<TX, VEC>(V + (int64_t)c * B + sub * VEC, v);
 #pragma unroll
@@ -102,7 +131,7 @@ __global__ void __launch_bounds__(256) spmm_csr_kernel(int64_t n, const int64_t*
 #pragma unroll
     for (int off = LPN; off < G; off <<= 1) {
 #pragma unroll
-        for (int q = 0; q < VEC; ++q) acc[q] += __shfl_xor_sync(gmask, acc[q], off);
+        for (int q = 0; q < VEC; ++q) acc[q] += shfl_xor_any(gmask, acc[q], off);
     }
     if (slot == 0) store_pack<TX, VEC>(W + row * B + sub * VEC, acc);
 }
@@ -120,7 +149,7 @@ __global__ void __launch_bounds__(256) spmm_csr_generic(int64_t n, int b, const 
     for (int q = 0; q < kMaxB; ++q) acc[q] = TX(0);
     for (int64_t k = rp[row] + lane; k < rp[row + 1]; k += 32) {
         const int c = ci[k];
-        const TX h = (TX)va[k];
+        const HType<TM, TX> h = (HType<TM, TX>)va[k];
 #pragma unroll
         for (int q = 0; q < kMaxB; ++q)
             if (q < b) acc[q] = fma(h, V[(int64_t)c * b + q], acc[q]);
@@ -129,7 +158,7 @@ __global__ void __launch_bounds__(256) spmm_csr_generic(int64_t n, int b, const 
     for (int q = 0; q < kMaxB; ++q) {
         TX x = acc[q];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        for (int off = 16; off > 0; off >>= 1) x += shfl_xor_any(0xffffffffu, x, off);
         acc[q] = x;
     }
     if (lane < b) {
@@ -137,7 +166,8 @@ __global__ void __launch_bounds__(256) spmm_csr_generic(int64_t n, int b, const 
 #pragma unroll
         for (int q = 1; q < kMaxB; ++q)
             if (q == lane) out = acc[q];
-        W[row * b + lane] = out;
+        if constexpr (is_df32<TX>::value) W[row * b + lane] = dfm::renorm(out.hi, out.lo);
+        else W[row * b + lane] = out;
     }
 }
 
@@ -165,11 +195,11 @@ __global__ void __launch_bounds__(256) spmm_sell_kernel(int64_t nslices, const i
     int k = 0;
     for (; k + U <= len; k += U) {
         int c[U];
-        TX h[U];
+        HType<TM, TX> h[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             c[u] = __ldg(sc + base + (int64_t)(k + u) * kSellC);
-            h[u] = (TX)__ldg(sv + base + (int64_t)(k + u) * kSellC);
+            h[u] = (HType<TM, TX>)__ldg(sv + base + (int64_t)(k + u) * kSellC);
         }
         TX v[U][B];
 #pragma unroll
@@ -190,7 +220,7 @@ __global__ void __launch_bounds__(256) spmm_sell_kernel(int64_t nslices, const i
     }
     for (; k < len; ++k) {
         const int c = __ldg(sc + base + (int64_t)k * kSellC);
-        const TX h = (TX)__ldg(sv + base + (int64_t)k * kSellC);
+        const HType<TM, TX> h = (HType<TM, TX>)__ldg(sv + base + (int64_t)k * kSellC);
         const TX* vp = V + (int64_t)c * B;
 #pragma unroll
         for (int ch = 0; ch < NCH; ++ch) {
@@ -229,7 +259,7 @@ __global__ void __launch_bounds__(256) spmm_sell_generic(int64_t nslices, int b,
     for (int q = 0; q < kMaxB; ++q) acc[q] = TX(0);
     for (int k = 0; k < len; ++k) {
         const int c = sc[base + (int64_t)k * kSellC];
-        const TX h = (TX)sv[base + (int64_t)k * kSellC];
+        const HType<TM, TX> h = (HType<TM, TX>)sv[base + (int64_t)k * kSellC];
 #pragma unroll
         for (int q = 0; q < kMaxB; ++q)
             if (q < b) acc[q] = fma(h, V[(int64_t)c * b + q], acc[q]);
@@ -238,7 +268,10 @@ __global__ void __launch_bounds__(256) spmm_sell_generic(int64_t nslices, int b,
     if (row >= 0) {
 #pragma unroll
         for (int q = 0; q < kMaxB; ++q)
-            if (q < b) W[(int64_t)row * b + q] = acc[q];
+            if (q < b) {
+                if constexpr (is_df32<TX>::value) W[(int64_t)row * b + q] = dfm::renorm(acc[q].hi, acc[q].lo);
+                else W[(int64_t)row * b + q] = acc[q];
+            }
     }
 }
 
@@ -338,6 +371,14 @@ bbl_status spmm_dispatch(const bbl_matrix* A, int b, const void* V, void* W, boo
     return spmm_typed<float, double>(A, b, A->has_csr ? A->val.as<float>() : nullptr,
                                      A->fmt == BBL_SELL ? A->sell_val.as<float>() : nullptr,
                                      static_cast<const double*>(V), static_cast<double*>(W), st, G);
+}
+
+bbl_status spmm_df32(const bbl_matrix* A, int b, const void* V, void* W, cudaStream_t st) {
+    if (A->storage != BBL_FP32)
+        return set_error(BBL_ERR_UNSUPPORTED, "spmm: float-float blocks need FP32 matrix values");
+    return spmm_typed<float, df32>(A, b, A->has_csr ? A->val.as<float>() : nullptr,
+                                   A->fmt == BBL_SELL ? A->sell_val.as<float>() : nullptr, static_cast<const df32*>(V),
+                                   static_cast<df32*>(W), st, 0);
 }
 
 }  // namespace bbl

@@ -143,6 +143,26 @@ def test_solve_mixed_precision_with_polish_matches_fp64_oracle(fmt):
     assert res.stats["polish_iters"] >= 1
 
 
+@pytest.mark.parametrize("fmt", ["csr", "sell"])
+def test_float_float_polish_agrees_with_fp64_polish(fmt):
+    """polish=1 keeps the restart's blocks as float-float pairs (~48 bits);
+    polish=2 runs it in FP64.  Both reach the FP64 residual bar, give the
+    oracle's eigenvalues to 1e-10 and take nearly the same number of blocks."""
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4", scale=0.5)
+    piv = OR.normal_block(9, H.n, 8)
+    ref = OL.block_lanczos(H, 8, 8, piv, tol=1e-9)
+    M = bbl.Matrix(H, storage="fp32", fmt=fmt, sell_sigma=256, keep_fp64=True)
+    r1 = bbl.solve(M, 8, 8, pivot=piv, tol=1e-9, polish=1, check_every=1)
+    r2 = bbl.solve(M, 8, 8, pivot=piv, tol=1e-9, polish=2, check_every=1)
+    assert r1.converged and r2.converged
+    _check_eigs(r1, ref.evals, H, 1e-9)
+    _check_eigs(r2, ref.evals, H, 1e-9)
+    np.testing.assert_allclose(r1.evals, r2.evals, rtol=1e-12)
+    assert r1.stats["iters"] == r2.stats["iters"]
+    assert abs(r1.stats["polish_iters"] - r2.stats["polish_iters"]) <= 1
+
+
 def test_solve_mixed_precision_stage1_error_below_1e6():
     torch, bbl = need_gpu()
     H = synth.kron_matrix("kron_n2e4", scale=0.5)
