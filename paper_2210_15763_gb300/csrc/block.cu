@@ -227,6 +227,173 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(int64_t n, int m, int64_
     gram_body<T, B, CPT>(n, m, next, TC, blockIdx.y, Q, W, partial + (int64_t)blockIdx.x * m * B);
 }
 
+// Row-contiguous split-K Gram (b = 4, 8).  A CTA takes a chunk of R rows from
+// the ticket counter, stages W's rows of the chunk in shared memory and its
+// warps walk the basis blocks: a warp reads a block's rows of the chunk as
+// whole consecutive rows (LPR lanes x 16 bytes per row, RL = 32 / LPR rows
+// per warp load, so every warp load is one contiguous stretch); each lane
+// multiplies its CPL columns of Q by the row's B values of W and keeps
+// CPL x B sums.  At the end of the chunk the RL row lanes are combined by a
+// butterfly that halves the values each lane carries per round, and each
+// lane adds its share of the block's B x B partial to the CTA's FP64 slot.
+// Blocks are dealt to warps round-robin; with fewer than 8 blocks the rows
+// of a chunk are split among wpb warps per block (one slot per row share).
+// FP32 data: products are summed in FP32 per batch of U rows, then over the
+// batches of the chunk and the lane tree, and in FP64 across chunks.
+template <typename T, int B>
+struct GramRowsShape {
+    static constexpr int CPL = 16 / (int)sizeof(T);         // Q columns per lane
+    static constexpr int LPR = B / CPL;                     // lanes per row
+    static constexpr int RL = 32 / LPR;                     // rows per warp step
+    static constexpr int R = 32768 / (B * (int)sizeof(T));  // rows per chunk (32 KB of W)
+    static constexpr int U = 8;                             // rows per lane per batch
+    static constexpr int NV = CPL * B;                      // sums per lane
+    static constexpr int LOGRL = RL >= 32 ? 5 : RL >= 16 ? 4 : RL >= 8 ? 3 : RL >= 4 ? 2 : RL >= 2 ? 1 : 0;
+};
+
+template <typename T>
+__device__ __forceinline__ T add_any(T a, T b) {
+    return a + b;
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads) gram_rows_kernel(int64_t n, int m, int wpb, int rc, int nchunks,
+                                                             const T* __restrict__ Q, const T* __restrict__ W,
+                                                             double* __restrict__ partial, int* __restrict__ ticket) {
+    using S = GramRowsShape<T, B>;
+    constexpr int CPL = S::CPL, LPR = S::LPR, RL = S::RL, R = S::R, U = S::U, NV = S::NV, LOGRL = S::LOGRL;
+    static_assert(LPR >= 1 && LPR <= 32 && 32 % LPR == 0 && B % CPL == 0 && (1 << LOGRL) == RL, "gram_rows shape");
+    // W tile, layout [h][row][CPL]: the 16-byte reads of one part h of RL
+    // consecutive rows are contiguous (no bank conflicts)
+    __shared__ __align__(16) T ws[R * B];
+    __shared__ int s_chunk;
+    const int nblocks = m / B;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane % LPR, t = lane / LPR;
+    const int ngrp = (kThreads / 32) / wpb;
+    const int grp = warp / wpb, sub = warp % wpb;
+    const int rsub = rc / wpb;  // rc <= R rows per chunk (fewer for small n)
+    double* part = partial + ((int64_t)blockIdx.x * wpb + sub) * m * B;
+    for (int64_t e = threadIdx.x; e < (int64_t)wpb * m * B; e += kThreads)
+        partial[(int64_t)blockIdx.x * wpb * m * B + e] = 0.0;
+    // after the butterfly lane t holds sums vbase .. vbase + NK - 1; when
+    // NV < RL the last rounds are plain all-reduces and only t < NV write
+    constexpr int NK = NV >= RL ? NV / RL : 1;
+    int vbase = 0;
+#pragma unroll
+    for (int k = 0; k < LOGRL; ++k)
+        if ((NV >> k) > 1 && (t & (1 << k))) vbase += NV >> (k + 1);
+    const bool writer = (NV >= RL) || (t < NV);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int c = s_chunk;
+        if (c >= nchunks) break;
+        const int64_t r0 = (int64_t)c * rc;
+        const int rows = (int)min((int64_t)rc, n - r0);
+        for (int e = threadIdx.x; e < R * LPR; e += kThreads) {
+            const int r = e / LPR, h = e % LPR;
+            T v[CPL];
+            if (r < rows) {
+                ldvec<T, CPL>(W + (r0 + r) * B + h * CPL, v);
+            } else {
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) v[q] = T(0);
+            }
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) ws[(h * R + r) * CPL + q] = v[q];
+        }
+        __syncthreads();
+        const int rb = sub * rsub;
+        const int re = min(rows, rb + rsub);
+        for (int j = grp; j < nblocks; j += ngrp) {
+            T acc[CPL][B];
+#pragma unroll
+            for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                for (int cc = 0; cc < B; ++cc) acc[i][cc] = T(0);
+            const T* qb = Q + ((int64_t)j * n + r0) * B + g * CPL;
+            for (int rr = rb + t; rr < re; rr += RL * U) {
+                T q[U][CPL];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int row = rr + u * RL;
+                    if (row < re) {
+                        ldvec<T, CPL>(qb + (int64_t)row * B, q[u]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < CPL; ++i) q[u][i] = T(0);
+                    }
+                }
+                T bat[CPL][B];
+#pragma unroll
+                for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                    for (int cc = 0; cc < B; ++cc) bat[i][cc] = T(0);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    // q is zero past the share; the tile row read there is in range
+                    const int row = min(rr + u * RL, R - 1);
+                    T w[B];
+#pragma unroll
+                    for (int h = 0; h < LPR; ++h) {
+                        const T* src = ws + (h * R + row) * CPL;
+                        if constexpr (sizeof(T) == 4) {
+                            const float4 x = *reinterpret_cast<const float4*>(src);
+                            w[h * CPL + 0] = x.x;
+                            w[h * CPL + 1] = x.y;
+                            w[h * CPL + 2] = x.z;
+                            w[h * CPL + 3] = x.w;
+                        } else {
+#pragma unroll
+                            for (int q2 = 0; q2 < CPL; ++q2) w[h * CPL + q2] = src[q2];
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                        for (int cc = 0; cc < B; ++cc) bat[i][cc] = fma(q[u][i], w[cc], bat[i][cc]);
+                }
+#pragma unroll
+                for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                    for (int cc = 0; cc < B; ++cc) acc[i][cc] = add_any(acc[i][cc], bat[i][cc]);
+            }
+            // butterfly over the RL row lanes (lane bits above the LPR group)
+            T v[NV];
+#pragma unroll
+            for (int e = 0; e < NV; ++e) v[e] = acc[e / B][e % B];
+#pragma unroll
+            for (int k = 0; k < LOGRL; ++k) {
+                const int o = (1 << k) * LPR;
+                const bool up = (t & (1 << k)) != 0;
+                if ((NV >> k) > 1) {
+                    const int hv = NV >> (k + 1);
+#pragma unroll
+                    for (int x = 0; x < NV / 2; ++x) {
+                        if (x < hv) {
+                            const T send = up ? v[x] : v[x + hv];
+                            const T keep = up ? v[x + hv] : v[x];
+                            v[x] = add_any(keep, shfl_xor_any(0xffffffffu, send, o));
+                        }
+                    }
+                } else {
+                    v[0] = add_any(v[0], shfl_xor_any(0xffffffffu, v[0], o));
+                }
+            }
+            if (writer) {
+#pragma unroll
+                for (int x = 0; x < NK; ++x) {
+                    const int e = vbase + x;
+                    const int i = e / B, cc = e % B;
+                    part[(int64_t)(j * B + g * CPL + i) * B + cc] += (double)v[x];
+                }
+            }
+        }
+    }
+}
+
 // Segmented Gram for a batch of independent problems stacked row-wise:
 // chunk x covers rows [chunks[3x+1], chunks[3x+2]) of segment chunks[3x];
 // chunks of inactive segments do nothing.
@@ -427,6 +594,40 @@ bbl_status gram_core(int64_t n, int m, const T* Q, const T* W, double* C, double
     return BBL_OK;
 }
 
+template <typename T, int B>
+bbl_status launch_gram_rows(int64_t n, int m, const T* Q, const T* W, double* C, DevBuf& partials, cudaStream_t st) {
+    using S = GramRowsShape<T, B>;
+    static int occ = 0;
+    if (occ == 0) {
+        BBL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gram_rows_kernel<T, B>, kThreads, 0));
+        if (occ < 1) occ = 1;
+    }
+    const int nblocks = m / B;
+    int wpb = 1;  // warps per block when there are fewer blocks than warps
+    while (wpb < kThreads / 32 && nblocks * wpb * 2 <= kThreads / 32) wpb <<= 1;
+    const int64_t slots_max = (int64_t)sm_count() * occ;
+    // rows per chunk: the full tile, or fewer so that small n still spreads
+    // over the GPU (a multiple of RL * wpb)
+    const int unit = S::RL * wpb;
+    int64_t rc = ceil_div(n, slots_max);
+    rc = std::max<int64_t>(unit * S::U, ceil_div(rc, unit) * unit);
+    rc = std::min<int64_t>(rc, S::R);
+    const int nch = (int)std::max<int64_t>(1, ceil_div(n, rc));
+    const int64_t workers = std::min<int64_t>(slots_max, nch);
+    const int64_t per = (int64_t)m * B;
+    const int64_t slots = workers * wpb;
+    const size_t need = sizeof(double) * (size_t)(slots * per) + 256;
+    if (partials.bytes < need) BBL_TRY(partials.alloc(need));
+    int* ticket = reinterpret_cast<int*>(partials.as<char>() + sizeof(double) * (size_t)(slots * per));
+    BBL_CUDA(cudaMemsetAsync(ticket, 0, sizeof(int), st));
+    gram_rows_kernel<T, B><<<(unsigned)workers, kThreads, 0, st>>>(n, m, wpb, (int)rc, nch, Q, W, partials.as<double>(),
+                                                                   ticket);
+    BBL_LAUNCH_CHECK();
+    reduce_partials_kernel<<<(unsigned)ceil_div(per, 256), 256, 0, st>>>(per, (int)slots, partials.as<double>(), C);
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
+}
+
 template <typename T, int B, int CPT>
 bbl_status launch_gram(int64_t n, int m, const T* Q, const T* W, double* C, DevBuf& partials, cudaStream_t st) {
     const int64_t per = (int64_t)m * B;
@@ -470,8 +671,8 @@ bbl_status gram_typed(int64_t n, int b, int m, const T* Q, const T* W, double* C
     switch (b) {
         case 1: return launch_gram<T, 1, 1>(n, m, Q, W, C, partials, st);
         case 2: return launch_gram<T, 2, 2>(n, m, Q, W, C, partials, st);
-        case 4: return launch_gram<T, 4, F ? 4 : 2>(n, m, Q, W, C, partials, st);
-        case 8: return launch_gram<T, 8, F ? 4 : 2>(n, m, Q, W, C, partials, st);
+        case 4: return launch_gram_rows<T, 4>(n, m, Q, W, C, partials, st);
+        case 8: return launch_gram_rows<T, 8>(n, m, Q, W, C, partials, st);
         case 16: return launch_gram<T, 16, 2>(n, m, Q, W, C, partials, st);
         default: return launch_gram_generic<T>(n, m, b, Q, W, C, partials, st);
     }
