@@ -227,33 +227,50 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(int64_t n, int m, int64_
     gram_body<T, B, CPT>(n, m, next, TC, blockIdx.y, Q, W, partial + (int64_t)blockIdx.x * m * B);
 }
 
-// Row-contiguous split-K Gram (b = 4, 8).  A CTA takes a chunk of R rows from
-// the ticket counter, stages W's rows of the chunk in shared memory and its
-// warps walk the basis blocks: a warp reads a block's rows of the chunk as
-// whole consecutive rows (LPR lanes x 16 bytes per row, RL = 32 / LPR rows
-// per warp load, so every warp load is one contiguous stretch); each lane
-// multiplies its CPL columns of Q by the row's B values of W and keeps
-// CPL x B sums.  At the end of the chunk the RL row lanes are combined by a
-// butterfly that halves the values each lane carries per round, and each
-// lane adds its share of the block's B x B partial to the CTA's FP64 slot.
-// Blocks are dealt to warps round-robin; with fewer than 8 blocks the rows
-// of a chunk are split among wpb warps per block (one slot per row share).
-// FP32 data: products are summed in FP32 per batch of U rows, then over the
-// batches of the chunk and the lane tree, and in FP64 across chunks.
+// Row-contiguous split-K Gram (b = 4, 8).  A CTA takes a chunk of rows from
+// the ticket counter and stages W's rows of the chunk in shared memory; its
+// warps walk the basis blocks.  A warp streams a block's rows of the chunk
+// into its own shared-memory ring with asynchronous 16-byte copies
+// (cp.async), NS stages of RL * U whole consecutive rows, so that NS - 1
+// stages are in flight while it computes on the oldest: no registers hold
+// data in flight.  Lane (g, t) multiplies its CPL columns of a row (LPR
+// lanes per row, RL = 32 / LPR rows per step) by the row's B values of W and
+// keeps CPL x B sums; at the end of the block's rows the RL row lanes are
+// combined by a butterfly that halves the values each lane carries per
+// round, and each lane adds its share of the B x B partial to the CTA's
+// FP64 slot.  Blocks are dealt to warps round-robin; with fewer than 8
+// blocks the rows of a chunk are split among wpb warps per block (one slot
+// per row share).  FP32 data: products are summed in FP32 per stage, then
+// over the stages of the chunk and the lane tree, and in FP64 across chunks.
 template <typename T, int B>
 struct GramRowsShape {
     static constexpr int CPL = 16 / (int)sizeof(T);         // Q columns per lane
     static constexpr int LPR = B / CPL;                     // lanes per row
     static constexpr int RL = 32 / LPR;                     // rows per warp step
     static constexpr int R = 32768 / (B * (int)sizeof(T));  // rows per chunk (32 KB of W)
-    static constexpr int U = 8;                             // rows per lane per batch
+    static constexpr int U = 4;                             // rows per lane per stage
+    static constexpr int NS = 4;                            // ring stages per warp
+    static constexpr int SROWS = RL * U;                    // rows per stage (2 KB)
     static constexpr int NV = CPL * B;                      // sums per lane
     static constexpr int LOGRL = RL >= 32 ? 5 : RL >= 16 ? 4 : RL >= 8 ? 3 : RL >= 4 ? 2 : RL >= 2 ? 1 : 0;
+    static constexpr int kWarps = kThreads / 32;
+    static constexpr size_t smem_bytes = (size_t)R * B * sizeof(T) + (size_t)kWarps * NS * SROWS * B * sizeof(T);
 };
 
 template <typename T>
 __device__ __forceinline__ T add_any(T a, T b) {
     return a + b;
+}
+
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 template <typename T, int B>
@@ -262,15 +279,19 @@ __global__ void __launch_bounds__(kThreads) gram_rows_kernel(int64_t n, int m, i
                                                              double* __restrict__ partial, int* __restrict__ ticket) {
     using S = GramRowsShape<T, B>;
     constexpr int CPL = S::CPL, LPR = S::LPR, RL = S::RL, R = S::R, U = S::U, NV = S::NV, LOGRL = S::LOGRL;
+    constexpr int NS = S::NS, SROWS = S::SROWS;
+    constexpr int PIECES = SROWS * LPR / 32;  // 16-byte copies per lane per stage
     static_assert(LPR >= 1 && LPR <= 32 && 32 % LPR == 0 && B % CPL == 0 && (1 << LOGRL) == RL, "gram_rows shape");
-    // W tile, layout [h][row][CPL]: the 16-byte reads of one part h of RL
-    // consecutive rows are contiguous (no bank conflicts)
-    __shared__ __align__(16) T ws[R * B];
+    static_assert((SROWS * LPR) % 32 == 0, "stage pieces");
+    // [ W tile: layout [h][row][CPL] | per-warp rings: NS stages of SROWS rows ]
+    extern __shared__ __align__(16) unsigned char gram_rows_smem[];
+    T* ws = reinterpret_cast<T*>(gram_rows_smem);
     __shared__ int s_chunk;
     const int nblocks = m / B;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane % LPR, t = lane / LPR;
-    const int ngrp = (kThreads / 32) / wpb;
+    T* ring = ws + (size_t)R * B + (size_t)warp * NS * SROWS * B;
+    const int ngrp = S::kWarps / wpb;
     const int grp = warp / wpb, sub = warp % wpb;
     const int rsub = rc / wpb;  // rc <= R rows per chunk (fewer for small n)
     double* part = partial + ((int64_t)blockIdx.x * wpb + sub) * m * B;
@@ -307,90 +328,126 @@ __global__ void __launch_bounds__(kThreads) gram_rows_kernel(int64_t n, int m, i
         __syncthreads();
         const int rb = sub * rsub;
         const int re = min(rows, rb + rsub);
-        for (int j = grp; j < nblocks; j += ngrp) {
-            T acc[CPL][B];
+        if (re <= rb) continue;
+        const int nst = (re - rb + SROWS - 1) / SROWS;       // stages per block
+        const int nblk = (nblocks - grp + ngrp - 1) / ngrp;  // blocks of this warp
+        const int total = nblk * nst;
+        // stage k: block grp + (k / nst) * ngrp, rows rb + (k % nst) * SROWS ..
+        auto issue = [&](int k) {
+            T* buf = ring + (size_t)(k % NS) * SROWS * B;
+            if (k < total) {
+                const int j = grp + (k / nst) * ngrp;
+                const int s0 = rb + (k % nst) * SROWS;
+                const T* src = Q + ((int64_t)j * n + r0 + s0) * B;
+#pragma unroll
+                for (int i = 0; i < PIECES; ++i) {
+                    const int pc = lane + 32 * i;
+                    const int row = pc / LPR, h = pc % LPR;
+                    const bool ok = s0 + row < re;
+                    cp_async16(buf + (size_t)pc * CPL, ok ? (const void*)(src + (size_t)row * B + h * CPL) : (const void*)Q,
+                               ok ? 16 : 0);
+                }
+            }
+            cp_async_commit();  // an empty group past the end keeps the count uniform
+        };
+#pragma unroll
+        for (int k = 0; k < NS - 1; ++k) issue(k);
+        T acc[CPL][B];
+#pragma unroll
+        for (int i = 0; i < CPL; ++i)
+#pragma unroll
+            for (int cc = 0; cc < B; ++cc) acc[i][cc] = T(0);
+        for (int k = 0; k < total; ++k) {
+            cp_async_wait<NS - 2>();
+            __syncwarp();
+            issue(k + NS - 1);  // into the buffer consumed at k - 1
+            const T* buf = ring + (size_t)(k % NS) * SROWS * B;
+            const int s0 = rb + (k % nst) * SROWS;
+            T bat[CPL][B];
 #pragma unroll
             for (int i = 0; i < CPL; ++i)
 #pragma unroll
-                for (int cc = 0; cc < B; ++cc) acc[i][cc] = T(0);
-            const T* qb = Q + ((int64_t)j * n + r0) * B + g * CPL;
-            for (int rr = rb + t; rr < re; rr += RL * U) {
-                T q[U][CPL];
+                for (int cc = 0; cc < B; ++cc) bat[i][cc] = T(0);
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int row = rr + u * RL;
-                    if (row < re) {
-                        ldvec<T, CPL>(qb + (int64_t)row * B, q[u]);
+            for (int u = 0; u < U; ++u) {
+                const int rr = t + u * RL;              // row within the stage (zero past the share)
+                const int row = min(s0 + rr, R - 1);    // row within the W tile
+                T q[CPL];
+                T w[B];
+                const T* qs = buf + (size_t)rr * B + g * CPL;
+                if constexpr (sizeof(T) == 4) {
+                    const float4 x = *reinterpret_cast<const float4*>(qs);
+                    q[0] = x.x;
+                    q[1] = x.y;
+                    q[2] = x.z;
+                    q[3] = x.w;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < CPL; ++i) q[i] = qs[i];
+                }
+#pragma unroll
+                for (int h = 0; h < LPR; ++h) {
+                    const T* src = ws + (h * R + row) * CPL;
+                    if constexpr (sizeof(T) == 4) {
+                        const float4 x = *reinterpret_cast<const float4*>(src);
+                        w[h * CPL + 0] = x.x;
+                        w[h * CPL + 1] = x.y;
+                        w[h * CPL + 2] = x.z;
+                        w[h * CPL + 3] = x.w;
                     } else {
 #pragma unroll
-                        for (int i = 0; i < CPL; ++i) q[u][i] = T(0);
+                        for (int q2 = 0; q2 < CPL; ++q2) w[h * CPL + q2] = src[q2];
                     }
-                }
-                T bat[CPL][B];
-#pragma unroll
-                for (int i = 0; i < CPL; ++i)
-#pragma unroll
-                    for (int cc = 0; cc < B; ++cc) bat[i][cc] = T(0);
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    // q is zero past the share; the tile row read there is in range
-                    const int row = min(rr + u * RL, R - 1);
-                    T w[B];
-#pragma unroll
-                    for (int h = 0; h < LPR; ++h) {
-                        const T* src = ws + (h * R + row) * CPL;
-                        if constexpr (sizeof(T) == 4) {
-                            const float4 x = *reinterpret_cast<const float4*>(src);
-                            w[h * CPL + 0] = x.x;
-                            w[h * CPL + 1] = x.y;
-                            w[h * CPL + 2] = x.z;
-                            w[h * CPL + 3] = x.w;
-                        } else {
-#pragma unroll
-                            for (int q2 = 0; q2 < CPL; ++q2) w[h * CPL + q2] = src[q2];
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < CPL; ++i)
-#pragma unroll
-                        for (int cc = 0; cc < B; ++cc) bat[i][cc] = fma(q[u][i], w[cc], bat[i][cc]);
                 }
 #pragma unroll
                 for (int i = 0; i < CPL; ++i)
 #pragma unroll
-                    for (int cc = 0; cc < B; ++cc) acc[i][cc] = add_any(acc[i][cc], bat[i][cc]);
+                    for (int cc = 0; cc < B; ++cc) bat[i][cc] = fma(q[i], w[cc], bat[i][cc]);
             }
-            // butterfly over the RL row lanes (lane bits above the LPR group)
-            T v[NV];
 #pragma unroll
-            for (int e = 0; e < NV; ++e) v[e] = acc[e / B][e % B];
+            for (int i = 0; i < CPL; ++i)
 #pragma unroll
-            for (int k = 0; k < LOGRL; ++k) {
-                const int o = (1 << k) * LPR;
-                const bool up = (t & (1 << k)) != 0;
-                if ((NV >> k) > 1) {
-                    const int hv = NV >> (k + 1);
+                for (int cc = 0; cc < B; ++cc) acc[i][cc] = add_any(acc[i][cc], bat[i][cc]);
+            if ((k % nst) == nst - 1) {
+                // last stage of block j: butterfly over the RL row lanes
+                const int j = grp + (k / nst) * ngrp;
+                T v[NV];
 #pragma unroll
-                    for (int x = 0; x < NV / 2; ++x) {
-                        if (x < hv) {
-                            const T send = up ? v[x] : v[x + hv];
-                            const T keep = up ? v[x + hv] : v[x];
-                            v[x] = add_any(keep, shfl_xor_any(0xffffffffu, send, o));
+                for (int e = 0; e < NV; ++e) v[e] = acc[e / B][e % B];
+#pragma unroll
+                for (int kk = 0; kk < LOGRL; ++kk) {
+                    const int o = (1 << kk) * LPR;
+                    const bool up = (t & (1 << kk)) != 0;
+                    if ((NV >> kk) > 1) {
+                        const int hv = NV >> (kk + 1);
+#pragma unroll
+                        for (int x = 0; x < NV / 2; ++x) {
+                            if (x < hv) {
+                                const T send = up ? v[x] : v[x + hv];
+                                const T keep = up ? v[x + hv] : v[x];
+                                v[x] = add_any(keep, shfl_xor_any(0xffffffffu, send, o));
+                            }
                         }
+                    } else {
+                        v[0] = add_any(v[0], shfl_xor_any(0xffffffffu, v[0], o));
                     }
-                } else {
-                    v[0] = add_any(v[0], shfl_xor_any(0xffffffffu, v[0], o));
                 }
-            }
-            if (writer) {
+                if (writer) {
 #pragma unroll
-                for (int x = 0; x < NK; ++x) {
-                    const int e = vbase + x;
-                    const int i = e / B, cc = e % B;
-                    part[(int64_t)(j * B + g * CPL + i) * B + cc] += (double)v[x];
+                    for (int x = 0; x < NK; ++x) {
+                        const int e = vbase + x;
+                        const int i = e / B, cc = e % B;
+                        part[(int64_t)(j * B + g * CPL + i) * B + cc] += (double)v[x];
+                    }
                 }
+#pragma unroll
+                for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                    for (int cc = 0; cc < B; ++cc) acc[i][cc] = T(0);
             }
         }
+        cp_async_wait<0>();
+        __syncwarp();
     }
 }
 
@@ -457,13 +514,40 @@ __global__ void __launch_bounds__(kThreads) gram_generic_kernel(int64_t n, int m
     }
 }
 
-__global__ void reduce_partials_kernel(int64_t count, int nparts, const double* __restrict__ partial,
-                                       double* __restrict__ out) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= count) return;
+// out[e] = sum_p partial[p * count + e]: 32 entries per CTA, the parts split
+// over 8 warps (coalesced 256-byte rows), combined in a fixed order.
+__global__ void __launch_bounds__(256) reduce_partials_kernel(int64_t count, int nparts,
+                                                              const double* __restrict__ partial,
+                                                              double* __restrict__ out) {
+    __shared__ double red[8][33];
+    const int tx = threadIdx.x & 31, pg = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * 32 + tx;
     double s = 0.0;
-    for (int p = 0; p < nparts; ++p) s += partial[(int64_t)p * count + e];
-    out[e] = s;
+    if (e < count) {
+        int p = pg;
+        for (; p + 24 < nparts; p += 32) {
+            const double a0 = partial[(int64_t)p * count + e];
+            const double a1 = partial[(int64_t)(p + 8) * count + e];
+            const double a2 = partial[(int64_t)(p + 16) * count + e];
+            const double a3 = partial[(int64_t)(p + 24) * count + e];
+            s += a0;
+            s += a1;
+            s += a2;
+            s += a3;
+        }
+        for (; p < nparts; p += 8) s += partial[(int64_t)p * count + e];
+    }
+    red[pg][tx] = s;
+    __syncthreads();
+    if (pg == 0 && e < count) {
+        double t = red[0][tx];
+        for (int q = 1; q < 8; ++q) t += red[q][tx];
+        out[e] = t;
+    }
+}
+
+void launch_reduce(int64_t count, int nparts, const double* partial, double* out, cudaStream_t st) {
+    reduce_partials_kernel<<<(unsigned)ceil_div(count, 32), 256, 0, st>>>(count, nparts, partial, out);
 }
 
 // Self Gram G = W^T W for b <= 8 (CholQR2): a thread per row (grid-strided),
@@ -511,11 +595,21 @@ __global__ void __launch_bounds__(kThreads) syrk_kernel(int64_t n, const T* __re
             cnt = 0;
         }
     }
+    // warp tree in the data type (FP32 sums of at most 64 rows per lane,
+    // then 32 lanes); the FP64 flushes only exist when a lane saw more rows
+    const bool flushed = n > (int64_t)64 * gridDim.x * kThreads;
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-        double v = acc64[q] + (double)acc[q];
+        T vt = acc[q];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        for (int off = 16; off > 0; off >>= 1) vt = add_any(vt, shfl_xor_any(0xffffffffu, vt, off));
+        double v = (double)vt;
+        if (flushed) {
+            double v64 = acc64[q];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v64 += __shfl_xor_sync(0xffffffffu, v64, off);
+            v += v64;
+        }
         if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32][q] = v;
     }
     __syncthreads();
@@ -541,7 +635,7 @@ bbl_status launch_syrk(int64_t n, const T* W, double* G, DevBuf& partials, cudaS
     if (partials.bytes < need) BBL_TRY(partials.alloc(need));
     syrk_kernel<T, B><<<grid, kThreads, 0, st>>>(n, W, partials.as<double>());
     BBL_LAUNCH_CHECK();
-    reduce_partials_kernel<<<1, 256, 0, st>>>((int64_t)B * B, grid, partials.as<double>(), G);
+    launch_reduce((int64_t)B * B, grid, partials.as<double>(), G, st);
     BBL_LAUNCH_CHECK();
     return BBL_OK;
 }
@@ -589,7 +683,7 @@ bbl_status gram_core(int64_t n, int m, const T* Q, const T* W, double* C, double
     dim3 grid((unsigned)workers, (unsigned)gy);
     gram_kernel<T, B, CPT><<<grid, kThreads, smem, st>>>(n, m, rpc, nch, TC, Q, W, partial, tickets);
     BBL_LAUNCH_CHECK();
-    reduce_partials_kernel<<<(unsigned)ceil_div(per, 256), 256, 0, st>>>(per, (int)workers, partial, C);
+    launch_reduce(per, (int)workers, partial, C, st);
     BBL_LAUNCH_CHECK();
     return BBL_OK;
 }
@@ -599,7 +693,9 @@ bbl_status launch_gram_rows(int64_t n, int m, const T* Q, const T* W, double* C,
     using S = GramRowsShape<T, B>;
     static int occ = 0;
     if (occ == 0) {
-        BBL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gram_rows_kernel<T, B>, kThreads, 0));
+        BBL_CUDA(cudaFuncSetAttribute(gram_rows_kernel<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)S::smem_bytes));
+        BBL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gram_rows_kernel<T, B>, kThreads, S::smem_bytes));
         if (occ < 1) occ = 1;
     }
     const int nblocks = m / B;
@@ -620,10 +716,10 @@ bbl_status launch_gram_rows(int64_t n, int m, const T* Q, const T* W, double* C,
     if (partials.bytes < need) BBL_TRY(partials.alloc(need));
     int* ticket = reinterpret_cast<int*>(partials.as<char>() + sizeof(double) * (size_t)(slots * per));
     BBL_CUDA(cudaMemsetAsync(ticket, 0, sizeof(int), st));
-    gram_rows_kernel<T, B><<<(unsigned)workers, kThreads, 0, st>>>(n, m, wpb, (int)rc, nch, Q, W, partials.as<double>(),
-                                                                   ticket);
+    gram_rows_kernel<T, B><<<(unsigned)workers, kThreads, S::smem_bytes, st>>>(n, m, wpb, (int)rc, nch, Q, W,
+                                                                              partials.as<double>(), ticket);
     BBL_LAUNCH_CHECK();
-    reduce_partials_kernel<<<(unsigned)ceil_div(per, 256), 256, 0, st>>>(per, (int)slots, partials.as<double>(), C);
+    launch_reduce(per, (int)slots, partials.as<double>(), C, st);
     BBL_LAUNCH_CHECK();
     return BBL_OK;
 }
@@ -660,14 +756,13 @@ bbl_status launch_gram_generic(int64_t n, int m, int b, const T* Q, const T* W, 
     gram_generic_kernel<T><<<grid, kThreads, smem, st>>>(n, m, b, rpc, TC, Q, W, partials.as<double>());
     BBL_LAUNCH_CHECK();
     const int64_t count = (int64_t)m * b;
-    reduce_partials_kernel<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(count, (int)nch, partials.as<double>(), C);
+    launch_reduce(count, (int)nch, partials.as<double>(), C, st);
     BBL_LAUNCH_CHECK();
     return BBL_OK;
 }
 
 template <typename T>
 bbl_status gram_typed(int64_t n, int b, int m, const T* Q, const T* W, double* C, DevBuf& partials, cudaStream_t st) {
-    constexpr bool F = sizeof(T) == 4;
     switch (b) {
         case 1: return launch_gram<T, 1, 1>(n, m, Q, W, C, partials, st);
         case 2: return launch_gram<T, 2, 2>(n, m, Q, W, C, partials, st);
