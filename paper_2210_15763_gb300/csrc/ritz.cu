@@ -34,6 +34,7 @@ constexpr int kWin = kMaxP + 1;         // LDL^T window edge
 constexpr int kBisectWarps = 8;
 constexpr size_t kBandSmemMax = 160 * 1024;  // band bytes staged in shared memory
 constexpr int kMaxNev = 32;
+constexpr size_t kInvitSmemMax = 220 * 1024;  // inverse iteration: window, vector and LU factors
 
 // Per-segment addressing for a batch of independent T's (blockIdx.y = segment
 // in bisect / invit, blockIdx.x in cluster).  The single-problem path passes
@@ -101,18 +102,109 @@ __device__ int inertia_count(const double* __restrict__ Tb, int p, int m, double
     return neg;
 }
 
+// The same count with the active window in registers, for bandwidths
+// P in {1, 2, 4, 8, 16}.  A group of P+1 lanes evaluates one shift (a warp
+// holds 32 / (P+1) groups, each with its own sigma).  Lane r of a group holds
+// one row of the window: at step k the rows k..k+P sit in lanes k mod (P+1),
+// ..., and a lane keeps its row's entries in the not yet eliminated columns
+// k..(its row) as f[0..delta], delta = its distance from the pivot row.  A
+// step gathers column k (every lane's f[0]) with P+1 shuffles, each lane
+// applies its multiplier f[0] / d_k to its row, shifts its entries by one
+// column, and the pivot lane takes the next row of T (loaded one cycle of
+// P+1 steps ahead).  All lanes of a group see the same pivots d_k.
+template <typename F, int P>
+__device__ int inertia_count_reg(const double* __restrict__ Tb, int m, double sigma, double pivmin) {
+    constexpr int P1 = P + 1;
+    const int lane = threadIdx.x & 31;
+    const int base = (lane / P1) * P1;  // spare lanes past the last group run along harmlessly
+    const int r = lane - base;
+    const F big = (F)1e30;
+    // entries of row R of T - sigma I in columns k1 .. k1 + P (lower triangle)
+    auto load = [&](int R, int k1, F(&dst)[P1]) {
+#pragma unroll
+        for (int j = 0; j < P1; ++j) {
+            const int C = k1 + j;
+            const int d = R - C;
+            F v = F(0);
+            if (R >= m) {
+                v = (d == 0) ? big : F(0);
+            } else if (d >= 0 && d <= P && C >= 0) {
+                double t = Tb[(int64_t)R * P1 + d];
+                if (d == 0) t -= sigma;
+                v = (F)t;
+            }
+            dst[j] = v;
+        }
+    };
+    F f[P1], nf[P1];
+    load(r, 0, f);            // row r, columns 0..P
+    load(r + P1, r + 1, nf);  // the row this lane takes after pivoting at step r
+    int delta = r < P ? r : P;
+    int piv = 0;
+    int neg = 0;
+    const F fpivmin = (F)pivmin;
+    for (int k = 0; k < m; ++k) {
+        F g[P1];
+#pragma unroll
+        for (int j = 0; j < P1; ++j) {
+            int src = piv + j;
+            if (src >= P1) src -= P1;
+            g[j] = __shfl_sync(0xffffffffu, f[0], base + src);
+        }
+        F d = g[0];
+        if (fabs(d) < fpivmin) d = -fpivmin;
+        neg += (d < F(0)) ? 1 : 0;
+        if (delta == 0) {
+#pragma unroll
+            for (int j = 0; j < P1; ++j) f[j] = nf[j];
+            load(k + 2 * P1, k + P1 + 1, nf);
+            delta = P;
+        } else {
+            F mlt;
+            if constexpr (sizeof(F) == 4) mlt = __fdividef(f[0], d);
+            else mlt = f[0] / d;
+#pragma unroll
+            for (int j = 1; j < P1; ++j)
+                if (j <= delta) f[j] = fma(-mlt, g[j], f[j]);
+#pragma unroll
+            for (int j = 0; j < P; ++j) f[j] = f[j + 1];
+            f[P] = F(0);
+            delta -= 1;
+        }
+        piv = (piv + 1 == P1) ? 0 : piv + 1;
+    }
+    return neg;
+}
+
+// Shifts evaluated at once per CTA: one per warp (window in shared memory,
+// any p) or one per lane group (register window, P > 0).
+template <int P>
+struct BisectShape {
+    static constexpr int G = P > 0 ? 32 / (P + 1) : 1;
+    static constexpr int NSH = kBisectWarps * G;
+};
+
+template <typename F, int P>
+__device__ __forceinline__ int count_below(const double* Tb, int p, int m, double sigma, double pivmin, F* win) {
+    if constexpr (P > 0) return inertia_count_reg<F, P>(Tb, m, sigma, pivmin);
+    else return inertia_count<F>(Tb, p, m, sigma, pivmin, win);
+}
+
 struct Bracket {
     double lo, hi;
 };
 
+template <int P>
 __global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p, int nev, const double* __restrict__ Tg,
                                                                    double* __restrict__ theta_out,
                                                                    double* __restrict__ width_out, int band_in_smem,
                                                                    SegArgs sa, const double* __restrict__ warm,
                                                                    int warm_count) {
-    __shared__ double win64[kBisectWarps][kWin * kWin];
-    __shared__ float win32[kBisectWarps][kWin * kWin];
-    __shared__ int counts[kBisectWarps];
+    constexpr int G = BisectShape<P>::G, NSH = BisectShape<P>::NSH;
+    constexpr int WIN = P > 0 ? 1 : kWin * kWin;  // shared-memory windows only for the generic form
+    __shared__ double win64[kBisectWarps][WIN];
+    __shared__ float win32[kBisectWarps][WIN];
+    __shared__ int counts[NSH];
     __shared__ double red[2][32 * kBisectWarps];
     __shared__ double s_lo, s_hi;
     extern __shared__ double tb_sh[];
@@ -125,6 +217,10 @@ __global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p,
     theta_out += seg * sa.sTh;
     width_out += seg * sa.sTh;
     const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
+    // shift slot of this lane: warp * G + its lane group; reporter: the group's first lane
+    const int lgrp = P > 0 ? min(lane / (P + 1), G - 1) : 0;
+    const int sidx = warp * G + lgrp;
+    const bool reporter = P > 0 ? (lane % (P + 1) == 0 && lane / (P + 1) < G) : (lane == 0);
     // the elimination walks T row by row: keep its band in shared memory when it fits
     const double* Tb = Tg;
     if (band_in_smem) {
@@ -187,13 +283,13 @@ __global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p,
             hi = ghi;
         }
         for (int round = 0; round < 40 && (hi - lo) > 1e-6 * scale; ++round) {
-            const double sigma = lo + (hi - lo) * (double)(warp + 1) / (double)(kBisectWarps + 1);
-            const int cnt = inertia_count<float>(Tb, p, m, sigma, pivmin32, win32[warp]);
-            if (lane == 0) counts[warp] = cnt;
+            const double sigma = lo + (hi - lo) * (double)(sidx + 1) / (double)(NSH + 1);
+            const int cnt = count_below<float, P>(Tb, p, m, sigma, pivmin32, win32[warp]);
+            if (reporter) counts[sidx] = cnt;
             __syncthreads();
             double nlo = lo, nhi = hi;
-            for (int w = 0; w < kBisectWarps; ++w) {
-                const double s = lo + (hi - lo) * (double)(w + 1) / (double)(kBisectWarps + 1);
+            for (int w = 0; w < NSH; ++w) {
+                const double s = lo + (hi - lo) * (double)(w + 1) / (double)(NSH + 1);
                 if (counts[w] <= i) nlo = fmax(nlo, s);
                 else nhi = fmin(nhi, s);
             }
@@ -203,7 +299,7 @@ __global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p,
             hi = nhi;
         }
         if (warp < 2) {
-            const int cnt = inertia_count<double>(Tb, p, m, warp == 0 ? lo : hi, pivmin64, win64[warp]);
+            const int cnt = count_below<double, P>(Tb, p, m, warp == 0 ? lo : hi, pivmin64, win64[warp]);
             if (lane == 0) counts[warp] = cnt;
         }
         __syncthreads();
@@ -221,13 +317,13 @@ __global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p,
     for (int round = 0; round < 200 && !verified; ++round) {
         const double tolw = 1e-9 * scale + 1e-300;
         if (hi - lo <= tolw) break;
-        const double sigma = lo + (hi - lo) * (double)(warp + 1) / (double)(kBisectWarps + 1);
-        const int cnt = inertia_count<double>(Tb, p, m, sigma, pivmin64, win64[warp]);
-        if (lane == 0) counts[warp] = cnt;
+        const double sigma = lo + (hi - lo) * (double)(sidx + 1) / (double)(NSH + 1);
+        const int cnt = count_below<double, P>(Tb, p, m, sigma, pivmin64, win64[warp]);
+        if (reporter) counts[sidx] = cnt;
         __syncthreads();
         double nlo = lo, nhi = hi;
-        for (int w = 0; w < kBisectWarps; ++w) {
-            const double s = lo + (hi - lo) * (double)(w + 1) / (double)(kBisectWarps + 1);
+        for (int w = 0; w < NSH; ++w) {
+            const double s = lo + (hi - lo) * (double)(w + 1) / (double)(NSH + 1);
             if (counts[w] <= i) nlo = fmax(nlo, s);
             else nhi = fmin(nhi, s);
         }
@@ -408,6 +504,203 @@ __global__ void __launch_bounds__(32) invit_kernel(int m, int p, const double* _
         __syncwarp();
     }
     // Rayleigh quotient
+    double rq = 0.0;
+    for (int r = lane; r < m; r += 32) {
+        double tx = 0.0;
+        for (int c = max(0, r - p); c <= min(m - 1, r + p); ++c) tx += band_get(Tb, p, m, r, c) * x[c];
+        rq += x[r] * tx;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) rq += __shfl_xor_sync(0xffffffffu, rq, off);
+    if (lane == 0) theta[i] = rq;
+    for (int r = lane; r < m; r += 32) S[(int64_t)r * nev + i] = x[r];
+}
+
+// Inverse iteration for bandwidths P in {1, 2, 4, 8}: the same banded LU
+// with partial pivoting as invit_kernel, with its factors kept in shared
+// memory when they fit (lu_in_smem), and column-oriented triangular solves
+// whose active rows live in registers: the forward solve keeps rows
+// k..k+P in lanes (row r in lane r mod (P+1)), applies the row interchange
+// of step k with two shuffles and updates the rows below with the
+// multipliers of column k; the backward solve keeps rows k-2P..k in lanes
+// (row r in lane r mod (2P+1)), forms x_k = y_k / U_kk and updates the rows
+// above.  One shuffle latency per row instead of a reduction per row.
+template <int P>
+__global__ void __launch_bounds__(32) invit_reg_kernel(int m, const double* __restrict__ Tg, double* __restrict__ theta,
+                                                        double* __restrict__ S, int nev, double* __restrict__ ws,
+                                                        int lu_in_smem, SegArgs sa) {
+    constexpr int p = P, P1 = P + 1, UW = 2 * P + 1;
+    static_assert(UW <= 32, "backward window exceeds a warp");
+    extern __shared__ double sm[];
+    const int i = blockIdx.x;
+    const int seg = blockIdx.y;
+    if (sa.active && !sa.active[seg]) return;
+    if (sa.d_m) m = *sa.d_m;
+    if (i >= min(nev, m)) return;
+    Tg += seg * sa.sT;
+    theta += seg * sa.sTh;
+    S += seg * sa.sS;
+    ws += seg * sa.sWs;
+    const int lane = threadIdx.x;
+    double* win = sm;             // P1 x UW circular window
+    double* x = win + P1 * UW;    // m
+    double* lsh = x + m;          // p multipliers (+ pad)
+    double* U;
+    double* L;
+    int* piv;
+    if (lu_in_smem) {
+        U = lsh + p + 8;
+        L = U + (int64_t)m * UW;
+        piv = reinterpret_cast<int*>(L + (int64_t)m * p);
+    } else {
+        U = ws + (int64_t)i * m * (3 * p + 1);
+        L = U + (int64_t)m * UW;
+        piv = reinterpret_cast<int*>(ws + (int64_t)nev * m * (3 * p + 1)) + (int64_t)i * m;
+    }
+    const double* Tb = Tg;
+    const double sigma = theta[i];
+    double scale = 0.0;
+    for (int r = lane; r < m; r += 32) {
+        double s = 0.0;
+        for (int c = max(0, r - p); c <= min(m - 1, r + p); ++c) s += fabs(band_get(Tb, p, m, r, c));
+        scale = fmax(scale, s);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) scale = fmax(scale, __shfl_xor_sync(0xffffffffu, scale, off));
+    const double tiny = 1e-14 * fmax(scale, 1e-300);
+    // ---- banded LU with partial pivoting of T - sigma I (rows k..k+p, columns k..k+2p in the window)
+    for (int e = lane; e < P1 * UW; e += 32) {
+        const int r = e / UW, c = e % UW;
+        double v = (r < m && c < m) ? band_get(Tb, p, m, r, c) : 0.0;
+        if (r == c && r < m) v -= sigma;
+        win[(r % P1) * UW + (c % UW)] = v;
+    }
+    __syncwarp();
+    for (int k = 0; k < m; ++k) {
+        const int ks = k % P1;
+        const int kc = k % UW;
+        double best = -1.0;
+        int bi = 0;
+        if (lane <= p && k + lane < m) {
+            best = fabs(win[((k + lane) % P1) * UW + kc]);
+            bi = lane;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        const int ps = (k + bi) % P1;
+        if (bi != 0) {
+            for (int c = lane; c < UW; c += 32) {
+                const int cs = (k + c) % UW;
+                const double a = win[ks * UW + cs], b2 = win[ps * UW + cs];
+                win[ks * UW + cs] = b2;
+                win[ps * UW + cs] = a;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            piv[k] = k + bi;
+            double u = win[ks * UW + kc];
+            if (fabs(u) < tiny) u = (u < 0.0) ? -tiny : tiny;
+            win[ks * UW + kc] = u;
+        }
+        __syncwarp();
+        for (int c = lane; c < UW; c += 32) U[(int64_t)k * UW + c] = win[ks * UW + (k + c) % UW];
+        const double u0 = win[ks * UW + kc];
+        if (lane >= 1 && lane <= p) {
+            const double l = (k + lane < m) ? win[((k + lane) % P1) * UW + kc] / u0 : 0.0;
+            lsh[lane - 1] = l;
+            L[(int64_t)k * p + lane - 1] = l;
+        }
+        __syncwarp();
+        for (int c = lane; c < UW; c += 32) {
+            if (c == 0) continue;
+            const int cs = (k + c) % UW;
+            const double top = win[ks * UW + cs];
+#pragma unroll
+            for (int r = 1; r <= p; ++r) {
+                const int rs = (k + r) % P1;
+                win[rs * UW + cs] -= lsh[r - 1] * top;
+            }
+        }
+        __syncwarp();
+        const int R = k + p + 1;
+        for (int c = lane; c < UW; c += 32) {
+            const int C = k + 1 + c;
+            double v = 0.0;
+            if (R < m && C < m) v = band_get(Tb, p, m, R, C) - (R == C ? sigma : 0.0);
+            win[ks * UW + (C % UW)] = v;
+        }
+        if (lane >= 1 && lane <= p) win[((k + lane) % P1) * UW + kc] = 0.0;
+        __syncwarp();
+    }
+    // ---- inverse iteration
+    for (int r = lane; r < m; r += 32) x[r] = hash_uniform((uint64_t)i + 1, (uint64_t)r);
+    __syncwarp();
+    for (int it = 0; it < 5; ++it) {
+        // forward: row interchanges and L (rows k..k+P in lanes)
+        {
+            double xv = (lane < P1 && lane < m) ? x[lane] : 0.0;
+            for (int k = 0; k < m; ++k) {
+                const int sk = k % P1;
+                const int pk = piv[k];
+                const int sp = pk % P1;
+                const double xk_new = __shfl_sync(0xffffffffu, xv, sp);
+                const double xk_old = __shfl_sync(0xffffffffu, xv, sk);
+                if (lane == sp) xv = xk_old;
+                if (lane == sk) xv = xk_new;
+                if (lane < P1 && lane != sk) {
+                    const int d = lane - sk + (lane < sk ? P1 : 0);  // row k + d
+                    if (k + d < m) xv = fma(-L[(int64_t)k * p + d - 1], xk_new, xv);
+                }
+                if (lane == sk) {
+                    x[k] = xk_new;
+                    xv = (k + P1 < m) ? x[k + P1] : 0.0;
+                }
+            }
+        }
+        __syncwarp();
+        // backward: U x = y (rows k-2P..k in lanes)
+        {
+            double yv = 0.0, rd = 0.0;
+            {
+                // lane l holds the row r <= m-1 with r % UW == l among the last UW rows
+                const int r = (m - 1) - (((m - 1) % UW - lane + UW) % UW);
+                if (lane < UW && r >= 0) {
+                    yv = x[r];
+                    rd = 1.0 / U[(int64_t)r * UW];
+                }
+            }
+            for (int k = m - 1; k >= 0; --k) {
+                const int sk = k % UW;
+                const double xk = __shfl_sync(0xffffffffu, yv * rd, sk);
+                if (lane < UW && lane != sk) {
+                    const int c = sk - lane + (lane > sk ? UW : 0);  // row k - c
+                    if (k - c >= 0) yv = fma(-U[(int64_t)(k - c) * UW + c], xk, yv);
+                }
+                if (lane == sk) {
+                    x[k] = xk;
+                    const int r = k - UW;
+                    yv = (r >= 0) ? x[r] : 0.0;
+                    rd = (r >= 0) ? 1.0 / U[(int64_t)r * UW] : 0.0;
+                }
+            }
+        }
+        __syncwarp();
+        double nn = 0.0;
+        for (int r = lane; r < m; r += 32) nn += x[r] * x[r];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, off);
+        const double inv = 1.0 / sqrt(nn);
+        for (int r = lane; r < m; r += 32) x[r] *= inv;
+        __syncwarp();
+    }
     double rq = 0.0;
     for (int r = lane; r < m; r += 32) {
         double tx = 0.0;
@@ -655,10 +948,67 @@ namespace {
 bbl_status set_ritz_attrs() {
     static bool attr_set = false;
     if (!attr_set) {
-        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
         BBL_CUDA(cudaFuncSetAttribute(invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024)));
+        BBL_CUDA(cudaFuncSetAttribute(invit_reg_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvitSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(invit_reg_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvitSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(invit_reg_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvitSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(invit_reg_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvitSmemMax));
         attr_set = true;
     }
+    return BBL_OK;
+}
+
+// the register-window bisection for p in {1, 2, 4, 8, 16}, else the generic one
+bbl_status launch_bisect(dim3 grid, int m, int p, int nev, const double* Tb, double* theta, double* width,
+                         int band_smem, size_t band_bytes, SegArgs sa, const double* warm, int warm_count,
+                         cudaStream_t st) {
+    const size_t sm = band_smem ? band_bytes : 0;
+    const unsigned th = 32 * kBisectWarps;
+    switch (p) {
+        case 1: bisect_kernel<1><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
+        case 2: bisect_kernel<2><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
+        case 4: bisect_kernel<4><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
+        case 8: bisect_kernel<8><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
+        case 16: bisect_kernel<16><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
+        default: bisect_kernel<0><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count);
+    }
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
+}
+
+// inverse iteration: the register-window solves for p in {1, 2, 4, 8} (LU
+// factors in shared memory when they fit), else the generic kernel
+bbl_status launch_invit(dim3 grid, int m, int p, int nev, const double* Tb, double* theta, double* S, double* ws,
+                        SegArgs sa, cudaStream_t st) {
+    if (p == 1 || p == 2 || p == 4 || p == 8) {
+        const int UW = 2 * p + 1, P1 = p + 1;
+        const size_t base = sizeof(double) * ((size_t)P1 * UW + m + p + 8);
+        const size_t lu = sizeof(double) * (size_t)m * (UW + p) + sizeof(int) * (size_t)m;
+        const int lu_smem = (base + lu <= kInvitSmemMax) ? 1 : 0;
+        const size_t smem = base + (lu_smem ? lu : 0);
+        if (smem > kInvitSmemMax) return set_error(BBL_ERR_UNSUPPORTED, "ritz: m=%d too large for the inverse iteration", m);
+        switch (p) {
+            case 1: invit_reg_kernel<1><<<grid, 32, smem, st>>>(m, Tb, theta, S, nev, ws, lu_smem, sa); break;
+            case 2: invit_reg_kernel<2><<<grid, 32, smem, st>>>(m, Tb, theta, S, nev, ws, lu_smem, sa); break;
+            case 4: invit_reg_kernel<4><<<grid, 32, smem, st>>>(m, Tb, theta, S, nev, ws, lu_smem, sa); break;
+            default: invit_reg_kernel<8><<<grid, 32, smem, st>>>(m, Tb, theta, S, nev, ws, lu_smem, sa); break;
+        }
+        BBL_LAUNCH_CHECK();
+        return BBL_OK;
+    }
+    const size_t band_bytes = sizeof(double) * (size_t)m * (p + 1);
+    const size_t base = sizeof(double) * ((size_t)(p + 1) * (2 * p + 1) + m + p + 8);
+    const int inv_smem = (base + band_bytes <= 200 * 1024) ? 1 : 0;
+    const size_t smem = base + (inv_smem ? band_bytes : 0);
+    if (smem > 200 * 1024) return set_error(BBL_ERR_UNSUPPORTED, "ritz: m=%d too large for the inverse iteration", m);
+    invit_kernel<<<grid, 32, smem, st>>>(m, p, Tb, theta, S, nev, ws, 0.0, inv_smem, sa);
+    BBL_LAUNCH_CHECK();
     return BBL_OK;
 }
 }  // namespace
@@ -676,15 +1026,8 @@ bbl_status ritz_dev(int m, int p, int nev, const double* Tb, double* theta, doub
     const int band_smem = band_bytes <= kBandSmemMax ? 1 : 0;
     BBL_TRY(set_ritz_attrs());
     const SegArgs one{nullptr, nullptr, 0, 0, 0, 0, 0};
-    bisect_kernel<<<nev, 32 * kBisectWarps, band_smem ? band_bytes : 0, st>>>(m, p, nev, Tb, theta, width, band_smem,
-                                                                              one, warm, warm_count);
-    BBL_LAUNCH_CHECK();
-    const size_t base = sizeof(double) * ((size_t)(p + 1) * (2 * p + 1) + m + p + 8);
-    const int inv_smem = (base + band_bytes <= 200 * 1024) ? 1 : 0;
-    const size_t smem = base + (inv_smem ? band_bytes : 0);
-    if (smem > 200 * 1024) return set_error(BBL_ERR_UNSUPPORTED, "ritz: m=%d too large for the inverse iteration", m);
-    invit_kernel<<<nev, 32, smem, st>>>(m, p, Tb, theta, S, nev, ws, 0.0, inv_smem, one);
-    BBL_LAUNCH_CHECK();
+    BBL_TRY(launch_bisect(dim3(nev), m, p, nev, Tb, theta, width, band_smem, band_bytes, one, warm, warm_count, st));
+    BBL_TRY(launch_invit(dim3(nev), m, p, nev, Tb, theta, S, ws, one, st));
     cluster_kernel<<<1, 256, 0, st>>>(m, p, nev, Tb, theta, S, tmp, one);
     BBL_LAUNCH_CHECK();
     return BBL_OK;
@@ -709,15 +1052,8 @@ bbl_status ritz_dev_batched(int m_max, int p, int nev, int nseg, const double* T
     const int64_t sWs = (int64_t)ritz_seg_workspace_doubles(m_max, p, nev);
     const SegArgs sa{d_m, active, sT, sTh, sS, sWs, (int64_t)m_max * nev};
     dim3 g(nev, nseg);
-    bisect_kernel<<<g, 32 * kBisectWarps, band_smem ? band_bytes : 0, st>>>(m_max, p, nev, Tb, theta, width, band_smem,
-                                                                            sa, nullptr, 0);
-    BBL_LAUNCH_CHECK();
-    const size_t base = sizeof(double) * ((size_t)(p + 1) * (2 * p + 1) + m_max + p + 8);
-    const int inv_smem = (base + band_bytes <= 200 * 1024) ? 1 : 0;
-    const size_t smem = base + (inv_smem ? band_bytes : 0);
-    if (smem > 200 * 1024) return set_error(BBL_ERR_UNSUPPORTED, "ritz: m=%d too large for the inverse iteration", m_max);
-    invit_kernel<<<g, 32, smem, st>>>(m_max, p, Tb, theta, S, nev, ws, 0.0, inv_smem, sa);
-    BBL_LAUNCH_CHECK();
+    BBL_TRY(launch_bisect(g, m_max, p, nev, Tb, theta, width, band_smem, band_bytes, sa, nullptr, 0, st));
+    BBL_TRY(launch_invit(g, m_max, p, nev, Tb, theta, S, ws, sa, st));
     cluster_kernel<<<nseg, 256, 0, st>>>(m_max, p, nev, Tb, theta, S, tmp, sa);
     BBL_LAUNCH_CHECK();
     return BBL_OK;
