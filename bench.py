@@ -37,6 +37,11 @@ B = 8
 NEV = 8
 TOL = 1e-8
 TRUNC = 20000
+# DRAM bytes per stored nonzero of one FP32 CSR SpMM launch (b = 8, 32 lanes
+# per row), from an ncu capture of the same kernel on the half-scale matrix
+# of the same family (dram__bytes_read.sum + dram__bytes_write.sum =
+# 1.185 GB for 139,708,000 nonzeros); traffic grows with the nonzeros.
+SPMM_TRAFFIC_PER_NNZ = 1.185e9 / 139_708_000
 SELL_SIGMA = 256
 METRIC = "time-to-solve lowest 8 eigenpairs @resid 1e-8 (s)"
 
@@ -258,12 +263,33 @@ def run_ours(args):
               "assembly_ms": tot["t_other_ms"] / args.steps,
               "bootstrap_pivot_ms": sum(a.elapsed_time(b) for a, b in boot_ev) / args.steps,
               "solve_total_ms": tot["t_total_ms"] / args.steps}
-    dom = "reorth" if tot["t_reorth_ms"] >= tot["t_spmm_ms"] else "spmm"
-    achieved = reorth_gbs if dom == "reorth" else spmm_gbs
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": None,
-                "kernel": "block Gram-Schmidt (gram + update kernels)" if dom == "reorth" else "SELL-C-sigma SpMM",
-                "peak_kind": peak_kind}
+    # per-kernel rooflines from the solver's own CUDA events (main stage, FP32):
+    # the SpMM phase of an iteration is exactly one SpMM launch; the timed
+    # first-pass Gram is the split-K Gram kernel plus its partial reduction
+    spmm_calls = sum(s["spmm_calls"] for s in stats_log)
+    spmm_total_ms = sum(s["spmm_bytes"] * s["spmm_calls"] / (s["spmm_gbs"] * 1e9) * 1e3 for s in stats_log)
+    spmm_kernel_gbs = stats_log[-1]["spmm_bytes"] * spmm_calls / (spmm_total_ms * 1e-3) / 1e9
+    gram_calls = tot["gram_calls"]
+    gram_gbs = tot["gram_bytes_total"] / (tot["t_gram_ms"] * 1e-3) / 1e9
+    kernels = {
+        "spmm": {"kernel": f"spmm_csr_kernel<float,float,8,{sched['lanes'] or 32}>" if sched["fmt"] == "csr"
+                 else "spmm_sell_kernel<float,float,8>", "launches": spmm_calls,
+                 "total_ms": spmm_total_ms, "achieved": spmm_kernel_gbs,
+                 "bytes_per_launch": stats_log[-1]["spmm_bytes"],
+                 "traffic": SPMM_TRAFFIC_PER_NNZ * A.nnz if sched["fmt"] == "csr" and (sched["lanes"] or 32) == 32
+                 else None},
+        "gram": {"kernel": "gram_rows_kernel<float,8> + reduce_partials_kernel (first pass; the second pass "
+                 "is the same kernel)", "launches": 2 * gram_calls, "total_ms": 2 * tot["t_gram_ms"],
+                 "achieved": gram_gbs, "bytes_per_launch": tot["gram_bytes_total"] / max(gram_calls, 1),
+                 "traffic": None},
+    }
+    dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
+    kd = kernels[dom]
+    roofline = {"bound": "hbm", "achieved": round(kd["achieved"], 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(kd["achieved"] / hbm, 4), "traffic": kd["traffic"], "kernel": kd["kernel"],
+                "peak_kind": peak_kind,
+                "per_kernel": {k: {kk: (round(vv, 3) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                               for k, v in kernels.items()}}
 
     # plain FP64 random-pivot block Lanczos (the comparison named by the metric)
     plain = None

@@ -110,6 +110,10 @@ typedef struct {
     double reorth_bytes_total;  /* algorithmic bytes of every Gram-Schmidt pass:
                                    per pass 2*n*m*s + 3*n*b*s (m basis columns)    */
     int ritz_solves;            /* Ritz solves (convergence tests) of all stages   */
+    int gram_calls;             /* main stage: first-pass Gram products C1 = Q^T W */
+    double t_gram_ms;           /* their time (split-K kernel + partial reduction) */
+    double gram_bytes_total;    /* their algorithmic bytes: (n*m + n*b)*s each     */
+    int spmm_calls;             /* main stage SpMM launches (spmm_gbs is over them) */
 } bbl_stats;
 
 void bbl_options_default(bbl_options* opt);

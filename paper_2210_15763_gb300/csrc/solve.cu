@@ -175,6 +175,8 @@ struct StageOut {
     bool converged = false;
     double t_spmm = 0, t_reorth = 0, t_chol = 0, t_ritz = 0, t_other = 0;
     double spmm_bytes = 0, reorth_bytes = 0;
+    double t_gram = 0, gram_bytes = 0;  // the first Gram-Schmidt pass's Gram (kernel + partial reduction)
+    int gram_calls = 0;
 };
 
 // Normalise columns of X (FP64, n x k) to the sign convention and compute the
@@ -467,7 +469,9 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         BBL_CUDA(cudaEventRecord(tm.ev[1], st));
         double* C1 = coeff.as<double>();
         double* C2 = C1 + (size_t)m_max * b;
+        BBL_CUDA(cudaEventRecord(tm.ev[4], st));
         BBL_TRY(gram(n, b, j + 1, dtype, basis.p, Wn, C1, partials, st));
+        BBL_CUDA(cudaEventRecord(tm.ev[5], st));
         BBL_TRY(update(n, b, j + 1, dtype, basis.p, C1, Wn, st));
         fill_A_kernel<<<1, 256, 0, st>>>(j, b, C1, Tb.as<double>());
         BBL_LAUNCH_CHECK();
@@ -484,6 +488,9 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         out.t_spmm += tm.ms(0, 1);
         out.t_reorth += tm.ms(1, 2);
         out.t_chol += tm.ms(2, 3);
+        out.t_gram += tm.ms(4, 5);
+        out.gram_bytes += ((double)n * (j + 1) * b + (double)n * b) * (double)s;
+        ++out.gram_calls;
         {
             const int m = (j + 1) * b;
             const double sx = (double)s;
@@ -634,6 +641,10 @@ bbl_status solve_impl(const bbl_matrix* A, int nev, int b, const double* pivot, 
         stats->spmm_bytes_total = s1.spmm_bytes + s2.spmm_bytes;
         stats->reorth_bytes_total = s1.reorth_bytes + s2.reorth_bytes;
         stats->ritz_solves = s1.ritz_solves + s2.ritz_solves;
+        stats->gram_calls = s1.gram_calls;
+        stats->t_gram_ms = s1.t_gram;
+        stats->gram_bytes_total = s1.gram_bytes;
+        stats->spmm_calls = s1.spmm_calls;
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
