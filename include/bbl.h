@@ -225,7 +225,10 @@ bbl_status bbl_ritz_banded(int m, int p, int nev, const double* Tband, double* t
 
 /* ---------------------------------------------------------------- S5: Ritz vectors
  * X = Q S: basis as in bbl_block_reorth (m = nblocks*b columns), S device
- * FP64 m x k row-major, X device FP64 n x k row-major.  k in 1..16.     */
+ * FP64 m x k row-major, X device FP64 n x k row-major.  k in 1..16.
+ * FP64 basis: FP64 arithmetic.  FP32 basis: S rounded to FP32, products
+ * summed in FP32 within tiles of 256 basis columns and in FP64 across tiles
+ * (error below 256 * 2^-24 * sum_a |Q_ia S_ac| per entry).              */
 bbl_status bbl_ritz_vectors(int64_t n, int b, int nblocks, bbl_dtype dtype, const void* basis, int k,
                             const double* S, double* X, void* stream);
 

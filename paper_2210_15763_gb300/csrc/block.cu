@@ -64,6 +64,7 @@ __device__ __forceinline__ void ldvec(const T* p, T (&out)[N]) {
 }
 
 constexpr int kRT = 256;   // rows per shared-memory tile in gram
+constexpr int kRitzReserveSMs = 8;
 constexpr int kThreads = 256;
 
 // -------------------------------------------------------------------- gram
@@ -701,7 +702,10 @@ bbl_status launch_gram_rows(int64_t n, int m, const T* Q, const T* W, double* C,
     const int nblocks = m / B;
     int wpb = 1;  // warps per block when there are fewer blocks than warps
     while (wpb < kThreads / 32 && nblocks * wpb * 2 <= kThreads / 32) wpb <<= 1;
-    const int64_t slots_max = (int64_t)sm_count() * occ;
+    // leave a few SMs to the Ritz solve that runs beside the main stream: a
+    // persistent CTA that cannot start until such a kernel ends would hold the
+    // whole Gram back
+    const int64_t slots_max = (int64_t)std::max(1, sm_count() - kRitzReserveSMs) * occ;
     // rows per chunk: the full tile, or fewer so that small n still spreads
     // over the GPU (a multiple of RL * wpb)
     const int unit = S::RL * wpb;
@@ -782,13 +786,21 @@ template <typename T, int B, int KCT, bool SUB, typename TA, typename TO>
 __device__ __forceinline__ void apply_body(int64_t n, int m, int kc, int64_t row0, int64_t row_end, const T* Q,
                                            const double* __restrict__ C, TO* W) {
     constexpr int KM = KCT > 0 ? KCT : kMaxB;
+    // FP32 sums into an FP64 result: FP32 within a tile of kKT columns, FP64
+    // across tiles
+    constexpr bool kTiled = sizeof(TA) == 4 && !is_df32<TA>::value && sizeof(TO) == 8;
     __shared__ TA cs[kKT * KM];
     const int tid = threadIdx.x;
     const int64_t r = row0 + tid;
     const int64_t rlim = row_end;
     TA acc[KM];
+    double acc64[kTiled ? KM : 1];
 #pragma unroll
     for (int c = 0; c < KM; ++c) acc[c] = TA(0);
+    if constexpr (kTiled) {
+#pragma unroll
+        for (int c = 0; c < KM; ++c) acc64[c] = 0.0;
+    }
     for (int a0 = 0; a0 < m; a0 += kKT) {
         const int rows = min(kKT, m - a0);
         __syncthreads();
@@ -823,14 +835,26 @@ __device__ __forceinline__ void apply_body(int64_t n, int m, int kc, int64_t row
                 }
             }
         }
+        if constexpr (kTiled) {
+#pragma unroll
+            for (int c = 0; c < KM; ++c) {
+                acc64[c] += (double)acc[c];
+                acc[c] = TA(0);
+            }
+        }
     }
     if (r < rlim) {
 #pragma unroll
         for (int c = 0; c < KM; ++c) {
             if (c < kc) {
                 TO* w = W + r * kc + c;
-                if (SUB) *w = (TO)((TA)(*w) - acc[c]);
-                else *w = (TO)acc[c];
+                if constexpr (kTiled) {
+                    if (SUB) *w = (TO)((double)(*w) - acc64[c]);
+                    else *w = (TO)acc64[c];
+                } else {
+                    if (SUB) *w = (TO)((TA)(*w) - acc[c]);
+                    else *w = (TO)acc[c];
+                }
             }
         }
     }
@@ -924,13 +948,6 @@ __device__ void chol_body(int b, const double* __restrict__ G, double thresh2, i
                           double* __restrict__ Rinv, int* __restrict__ ndefl, int* __restrict__ mask,
                           int* __restrict__ status);
 
-__global__ void chol_kernel(int b, const double* __restrict__ G, double thresh2, int relative, double* __restrict__ R,
-                            double* __restrict__ Rinv, int* __restrict__ ndefl, int* __restrict__ mask,
-                            int* __restrict__ status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    chol_body(b, G, thresh2, relative, R, Rinv, ndefl, mask, status);
-}
-
 // One thread per segment: Cholesky of G + s*b*b with threshold thresh2[s].
 __global__ void chol_seg_kernel(int b, int nseg, const double* __restrict__ G, const double* __restrict__ thresh2,
                                 int relative, double* __restrict__ R, double* __restrict__ Rinv, int* __restrict__ ndefl,
@@ -1005,6 +1022,72 @@ __device__ void chol_body(int b, const double* __restrict__ G, double thresh2, i
     if (bad && status) atomicOr(status, 1);
 }
 
+// The same Cholesky with deflation by one warp: rows of R are formed one
+// after the other (lane k computes R[i][k]), then lane c forms column c of
+// R^{-1}.  Deflated columns get zero rows in R and zero columns in R^{-1}.
+__global__ void __launch_bounds__(32) chol_warp_kernel(int b, const double* __restrict__ G, double thresh2, int relative,
+                                                      double* __restrict__ R, double* __restrict__ Rinv,
+                                                      int* __restrict__ ndefl, int* __restrict__ mask,
+                                                      int* __restrict__ status) {
+    __shared__ double Gs[kMaxB * kMaxB];
+    __shared__ double Rs[kMaxB * kMaxB];
+    __shared__ int dm[kMaxB];
+    const int lane = threadIdx.x;
+    int bad = 0;
+    double gmax = 0.0;
+    for (int e = lane; e < b * b; e += 32) {
+        const double g = G[e];
+        Gs[e] = g;
+        Rs[e] = 0.0;
+        if (!isfinite(g)) bad = 1;
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    __syncwarp();
+    for (int q = 0; q < b; ++q) gmax = fmax(gmax, Gs[q * b + q]);
+    if (relative) thresh2 *= gmax;
+    int cnt = 0;
+    for (int i = 0; i < b; ++i) {
+        double d = Gs[i * b + i];
+        for (int l = 0; l < i; ++l) d -= Rs[l * b + i] * Rs[l * b + i];
+        const int defl = !(d > thresh2) || bad;
+        cnt += defl;
+        if (lane == 0) dm[i] = defl;
+        if (!defl) {
+            const double rii = sqrt(d);
+            if (lane == i) Rs[i * b + i] = rii;
+            if (lane > i && lane < b) {
+                double t = Gs[i * b + lane];
+                for (int l = 0; l < i; ++l) t -= Rs[l * b + i] * Rs[l * b + lane];
+                Rs[i * b + lane] = t / rii;
+            }
+        }
+        __syncwarp();
+    }
+    for (int e = lane; e < b * b; e += 32) R[e] = Rs[e];
+    if (lane < b) {
+        const int c = lane;
+        double col[kMaxB];
+#pragma unroll
+        for (int q = 0; q < kMaxB; ++q) col[q] = 0.0;
+        if (!dm[c]) {
+            col[c] = 1.0 / Rs[c * b + c];
+            for (int i = c - 1; i >= 0; --i) {
+                if (dm[i]) continue;
+                double t = 0.0;
+                for (int k = i + 1; k <= c; ++k)
+                    if (!dm[k]) t += Rs[i * b + k] * col[k];
+                col[i] = -t / Rs[i * b + i];
+            }
+        }
+        for (int q = 0; q < b; ++q) Rinv[q * b + c] = col[q];
+        if (mask) mask[c] = dm[c];
+    }
+    if (lane == 0) {
+        if (ndefl) *ndefl += cnt;
+        if (bad && status) atomicOr(status, 1);
+    }
+}
+
 // B = R2 R1 (upper triangular product)
 __global__ void trmul_kernel(int b, const double* __restrict__ R2, const double* __restrict__ R1, double* __restrict__ B) {
     const int e = threadIdx.x;
@@ -1047,7 +1130,9 @@ bbl_status ritz_vectors(int64_t n, int b, int nblocks, int dtype, const void* Q,
         return apply_typed<double, false, double, double>(n, b, m, k, static_cast<const double*>(Q), S, X, st);
     if (dtype == kDF32)
         return apply_typed<df32, false, df32, double>(n, b, m, k, static_cast<const df32*>(Q), S, X, st);
-    return apply_typed<float, false, double, double>(n, b, m, k, static_cast<const float*>(Q), S, X, st);
+    // FP32 blocks: FP32 products and sums (the vectors carry FP32 accuracy
+    // anyway), FP64 output
+    return apply_typed<float, false, float, double>(n, b, m, k, static_cast<const float*>(Q), S, X, st);
 }
 
 // small: >= 8*b*b doubles + 4*b ints.  B (device, b x b) receives R2 R1.
@@ -1097,7 +1182,7 @@ bbl_status cholqr2_dev(int64_t n, int b, int dtype, void* W, double* B, double d
     const int relative = defl_abs2 < 0 ? 1 : 0;
     const double t1 = relative ? -defl_abs2 : defl_abs2;
     BBL_TRY(self_gram(n, b, dtype, W, G, partials, st));
-    chol_kernel<<<1, 32, 0, st>>>(b, G, t1, relative, R1, R1i, d_ndefl, d_mask, status);
+    chol_warp_kernel<<<1, 32, 0, st>>>(b, G, t1, relative, R1, R1i, d_ndefl, d_mask, status);
     BBL_LAUNCH_CHECK();
     if (dtype == BBL_FP64)
         BBL_TRY((apply_typed<double, false, double, double>(n, b, b, b, static_cast<double*>(W), R1i,
@@ -1111,7 +1196,7 @@ bbl_status cholqr2_dev(int64_t n, int b, int dtype, void* W, double* B, double d
     BBL_TRY(self_gram(n, b, dtype, W, G, partials, st));
     // second pass: columns of Q1 have norm ~1; a pivot below 1e-6 means the
     // first pass produced no usable direction (it was deflated or lost).
-    chol_kernel<<<1, 32, 0, st>>>(b, G, 1e-6, 0, R2, R2i, nullptr, nullptr, status);
+    chol_warp_kernel<<<1, 32, 0, st>>>(b, G, 1e-6, 0, R2, R2i, nullptr, nullptr, status);
     BBL_LAUNCH_CHECK();
     if (dtype == BBL_FP64)
         BBL_TRY((apply_typed<double, false, double, double>(n, b, b, b, static_cast<double*>(W), R2i,

@@ -7,16 +7,19 @@
 //  1. bisect  - one CTA per wanted eigenvalue index i.  Sylvester's law of
 //               inertia: the number of negative pivots of the LDL^T
 //               factorisation of T - sigma I is the number of eigenvalues below
-//               sigma.  Each warp evaluates one shift (multisection), the
-//               (p+1)x(p+1) active window of the elimination lives in shared
-//               memory with circular row/column indices, one lane per window
-//               column.  Rounds run first in FP32 (64x the FP64 rate on this
-//               GPU) down to a bracket of 1e-4 * scale, the bracket is then
-//               checked with two FP64 counts and refined in FP64.
+//               sigma.  For p in {1, 2, 4, 8, 16} a group of p+1 lanes holds
+//               the elimination window in registers and evaluates one shift
+//               (32/(p+1) shifts per warp, 24 per CTA for p = 8); otherwise a
+//               warp per shift with the window in shared memory.  Multisection
+//               runs in FP32 (58x the FP64 rate on this GPU) to a bracket of
+//               1e-5 * scale, starting from the previous Ritz value when one is
+//               given (Cauchy interlacing makes it an upper bound); FP64 counts
+//               check the bracket and FP64 multisection narrows it to
+//               1e-8 * scale.
 //  2. invit   - one warp per eigenvalue: banded LU with partial pivoting of
-//               T - theta I (U has bandwidth 2p), two steps of inverse
-//               iteration from a per-index pseudo-random start, Rayleigh
-//               quotient.
+//               T - theta I (U has bandwidth 2p), three steps of inverse
+//               iteration from a per-index pseudo-random start (register-window
+//               triangular solves for p <= 8), Rayleigh quotient.
 //  3. cluster - one CTA: eigenvalues closer than 1e-3 * scale are grouped;
 //               their vectors are orthonormalised twice (modified
 //               Gram-Schmidt) and rotated by a small Jacobi Rayleigh-Ritz;
@@ -161,8 +164,21 @@ __device__ int inertia_count_reg(const double* __restrict__ Tb, int m, double si
             delta = P;
         } else {
             F mlt;
-            if constexpr (sizeof(F) == 4) mlt = __fdividef(f[0], d);
-            else mlt = f[0] / d;
+            if constexpr (sizeof(F) == 4) {
+                mlt = __fdividef(f[0], d);
+            } else {
+                // reciprocal from an FP32 seed and one Newton step (relative
+                // error ~2^-46, ample for the signs of the pivots)
+                const double ad = fabs(d);
+                double rd;
+                if (ad > 1e-30 && ad < 1e30) {
+                    const double r0 = (double)__frcp_rn((float)d);
+                    rd = r0 * fma(-d, r0, 2.0);
+                } else {
+                    rd = 1.0 / d;
+                }
+                mlt = f[0] * rd;
+            }
 #pragma unroll
             for (int j = 1; j < P1; ++j)
                 if (j <= delta) f[j] = fma(-mlt, g[j], f[j]);
@@ -271,7 +287,9 @@ __global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p,
             hi = ghi;
         }
     }
-    // phase 1: FP32 multisection to a 1e-6 * scale bracket, checked with FP64
+    // phase 1: FP32 multisection to a 1e-5 * scale bracket (FP32 counts are
+    // exact for a matrix within a few p * 2^-24 * scale of T, so narrower FP32
+    // brackets are not trustworthy), checked with FP64
     // counts at its ends (warp 0 at lo, warp 1 at hi).  A warm bracket that
     // fails the check (the value moved further down than guessed) is retried
     // once from the Gershgorin interval.
@@ -282,7 +300,7 @@ __global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p,
             lo = glo;
             hi = ghi;
         }
-        for (int round = 0; round < 40 && (hi - lo) > 1e-6 * scale; ++round) {
+        for (int round = 0; round < 40 && (hi - lo) > 1e-5 * scale; ++round) {
             const double sigma = lo + (hi - lo) * (double)(sidx + 1) / (double)(NSH + 1);
             const int cnt = count_below<float, P>(Tb, p, m, sigma, pivmin32, win32[warp]);
             if (reporter) counts[sidx] = cnt;
@@ -306,16 +324,16 @@ __global__ void __launch_bounds__(32 * kBisectWarps) bisect_kernel(int m, int p,
         verified = counts[0] <= i && counts[1] > i;
         __syncthreads();
     }
-    // phase 3 (only when the FP32 bracket failed the FP64 check): FP64
-    // multisection from the Gershgorin interval to 1e-9 * scale.  Otherwise
-    // the 1e-6 * scale bracket goes straight to inverse iteration, whose
-    // Rayleigh quotient gives the eigenvalue to working precision.
+    // phase 2: FP64 multisection from the verified bracket (or, when the FP32
+    // bracket failed the check, from the Gershgorin interval) to 1e-8 * scale;
+    // inverse iteration then starts within 1e-8 * scale of the eigenvalue and
+    // its Rayleigh quotient gives the value to working precision.
     if (!verified) {
         lo = glo;
         hi = ghi;
     }
-    for (int round = 0; round < 200 && !verified; ++round) {
-        const double tolw = 1e-9 * scale + 1e-300;
+    for (int round = 0; round < 200; ++round) {
+        const double tolw = 1e-8 * scale + 1e-300;
         if (hi - lo <= tolw) break;
         const double sigma = lo + (hi - lo) * (double)(sidx + 1) / (double)(NSH + 1);
         const int cnt = count_below<double, P>(Tb, p, m, sigma, pivmin64, win64[warp]);
@@ -640,10 +658,14 @@ __global__ void __launch_bounds__(32) invit_reg_kernel(int m, const double* __re
         if (lane >= 1 && lane <= p) win[((k + lane) % P1) * UW + kc] = 0.0;
         __syncwarp();
     }
-    // ---- inverse iteration
+    // ---- inverse iteration: the shift is within 1e-8 * scale of the
+    // eigenvalue and eigenvalues closer than 1e-3 * scale form a cluster, so
+    // each step shrinks the other components by 1e-5 or more: three suffice
+    // the divisions of the backward solve use the reciprocals of U's diagonal
+    for (int r = lane; r < m; r += 32) U[(int64_t)r * UW] = 1.0 / U[(int64_t)r * UW];
     for (int r = lane; r < m; r += 32) x[r] = hash_uniform((uint64_t)i + 1, (uint64_t)r);
     __syncwarp();
-    for (int it = 0; it < 5; ++it) {
+    for (int it = 0; it < 3; ++it) {
         // forward: row interchanges and L (rows k..k+P in lanes)
         {
             double xv = (lane < P1 && lane < m) ? x[lane] : 0.0;
@@ -674,7 +696,7 @@ __global__ void __launch_bounds__(32) invit_reg_kernel(int m, const double* __re
                 const int r = (m - 1) - (((m - 1) % UW - lane + UW) % UW);
                 if (lane < UW && r >= 0) {
                     yv = x[r];
-                    rd = 1.0 / U[(int64_t)r * UW];
+                    rd = U[(int64_t)r * UW];
                 }
             }
             for (int k = m - 1; k >= 0; --k) {
@@ -688,7 +710,7 @@ __global__ void __launch_bounds__(32) invit_reg_kernel(int m, const double* __re
                     x[k] = xk;
                     const int r = k - UW;
                     yv = (r >= 0) ? x[r] : 0.0;
-                    rd = (r >= 0) ? 1.0 / U[(int64_t)r * UW] : 0.0;
+                    rd = (r >= 0) ? U[(int64_t)r * UW] : 0.0;
                 }
             }
         }

@@ -234,7 +234,11 @@ def test_ritz_vectors_match_basis_times_S(dtype, b, nb, k):
     Qf = np.concatenate([Q[j].astype(np.float64) for j in range(nb)], axis=1)
     ref = Qf @ S
     bound = np.abs(Qf) @ np.abs(S)
-    assert np.all(np.abs(X - ref) <= 64 * EPS64 * bound + 1e-300)
+    if dtype == "fp64":
+        assert np.all(np.abs(X - ref) <= 64 * EPS64 * bound + 1e-300)
+    else:
+        # FP32 products summed in FP32 within 256-column tiles, FP64 across
+        assert np.all(np.abs(X - ref) <= 258 * 2.0 ** -24 * bound + 1e-300)
 
 
 def test_pivot_random_is_the_published_generator():
