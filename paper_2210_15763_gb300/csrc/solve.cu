@@ -180,14 +180,19 @@ struct StageOut {
 };
 
 // Normalise columns of X (FP64, n x k) to the sign convention and compute the
-// true residuals ||H x_i - theta_i x_i||_2 (FP64 SpMM).
+// true residuals ||H x_i - theta_i x_i||_2 (FP64 SpMM).  quick (FP32 matrix
+// values only): the product H X in float-float arithmetic instead, for the
+// residuals that only decide whether the polish runs.
 bbl_status finish_vectors(const bbl_matrix* A, int k, double* X, const double* theta_dev, double* resid_host,
-                          DevBuf& scratch, cudaStream_t st) {
+                          DevBuf& scratch, cudaStream_t st, bool quick = false) {
     const int64_t n = A->n;
-    const size_t need = sizeof(double) * (size_t)n * k + (sizeof(double) * 2 + sizeof(int64_t)) * kRedBlocks * k + 256;
+    quick = quick && A->storage == BBL_FP32;
+    const size_t nk2 = ((size_t)n * k + 1) & ~size_t(1);  // 16-byte aligned sub-buffers
+    const size_t need = sizeof(double) * nk2 * (quick ? 3 : 1) +
+                        (sizeof(double) * 2 + sizeof(int64_t)) * kRedBlocks * k + 256;
     if (scratch.bytes < need) BBL_TRY(scratch.alloc(need));
     double* Y = scratch.as<double>();
-    double* pv = Y + (size_t)n * k;
+    double* pv = Y + nk2 * (quick ? 3 : 1);
     int64_t* pi = reinterpret_cast<int64_t*>(pv + (size_t)kRedBlocks * k);
     double* pr = reinterpret_cast<double*>(pi + (size_t)kRedBlocks * k);
     colmax_partial_kernel<<<kRedBlocks, 256, 0, st>>>(n, k, X, pv, pi);
@@ -217,7 +222,17 @@ bbl_status finish_vectors(const bbl_matrix* A, int k, double* X, const double* t
     scale_cols_kernel<<<kRedBlocks, 256, 0, st>>>(n, k, pv, X);
     BBL_LAUNCH_CHECK();
     if (resid_host) {
-        BBL_TRY(spmm_dispatch(A, k, X, Y, true, st));
+        if (quick) {
+            df32* Xd = reinterpret_cast<df32*>(Y + nk2);
+            df32* Yd = reinterpret_cast<df32*>(Y + 2 * nk2);
+            convert_kernel<double, df32><<<152 * 8, 256, 0, st>>>(n * k, X, Xd);
+            BBL_LAUNCH_CHECK();
+            BBL_TRY(spmm_df32(A, k, Xd, Yd, st));
+            convert_kernel<df32, double><<<152 * 8, 256, 0, st>>>(n * k, Yd, Y);
+            BBL_LAUNCH_CHECK();
+        } else {
+            BBL_TRY(spmm_dispatch(A, k, X, Y, true, st));
+        }
         resid_partial_kernel<<<kRedBlocks, 256, 0, st>>>(n, k, Y, X, theta_dev, pr);
         BBL_LAUNCH_CHECK();
         std::vector<double> hp((size_t)kRedBlocks * k);
@@ -588,7 +603,8 @@ bbl_status solve_impl(const bbl_matrix* A, int nev, int b, const double* pivot, 
                               theta.as<double>(), s1));
     }
     int k = s1.nev_eff;
-    BBL_TRY(finish_vectors(A, k, X.as<double>(), theta.as<double>(), res.data(), scratch, st));
+    // before a polish the stage-1 residuals only decide whether it runs
+    BBL_TRY(finish_vectors(A, k, X.as<double>(), theta.as<double>(), res.data(), scratch, st, mixed && o.polish));
     const double nrm = A->norm_inf > 0 ? A->norm_inf : 1.0;
     bool ok = s1.converged && k == nev;
     if (mixed && o.polish) {
@@ -608,6 +624,8 @@ bbl_status solve_impl(const bbl_matrix* A, int nev, int b, const double* pivot, 
             BBL_TRY(finish_vectors(A, k, X.as<double>(), theta.as<double>(), res.data(), scratch, st));
             ok = s2.converged && k == nev;
         } else {
+            // no polish needed: report FP64 residuals
+            BBL_TRY(finish_vectors(A, k, X.as<double>(), theta.as<double>(), res.data(), scratch, st));
             ok = true;
         }
     }
