@@ -212,6 +212,7 @@ def run_ours(args):
 
     stats_log = []
     boot_ev = []
+    solve_opts = {} if args.ritz_overlap is None else {"ritz_overlap": args.ritz_overlap}
 
     def step():
         b0 = torch.cuda.Event(enable_timing=True)
@@ -220,7 +221,7 @@ def run_ours(args):
         P = bbl.pivot_bootstrap(M32, TRUNC, B, sub_tol=1e-10, seed=20221028)
         b1.record(st)
         boot_ev.append((b0, b1))
-        r = bbl.solve(M32, NEV, B, pivot=P, tol=TOL, evecs="device", max_vectors=2000)
+        r = bbl.solve(M32, NEV, B, pivot=P, tol=TOL, evecs="device", max_vectors=2000, **solve_opts)
         stats_log.append(r.stats)
         return r
 
@@ -597,6 +598,7 @@ def main():
     ap.add_argument("--mode", default="solve", choices=["solve", "kernels", "batched", "learned", "c3"])
     ap.add_argument("--c3-vectors", type=int, default=300)
     ap.add_argument("--c3-fp64", action="store_true")
+    ap.add_argument("--ritz-overlap", type=int, default=None)
     ap.add_argument("--epochs", type=int, default=3000)
     ap.add_argument("--family-scale", type=float, default=1.0)
     ap.add_argument("--count", type=int, default=256)

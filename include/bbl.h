@@ -93,6 +93,10 @@ typedef struct {
                                    block that passes.  The rms-change criterion
                                    always tests every block.                       */
     void* stream;               /* cudaStream_t                                    */
+    int ritz_overlap;           /* 1 (default): the Ritz solve of block j runs on a
+                                   second stream while block j+1 is formed (one
+                                   speculative block at the end); 0: on `stream`,
+                                   read before the next block                      */
 } bbl_options;
 
 typedef struct {

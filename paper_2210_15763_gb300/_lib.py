@@ -16,7 +16,8 @@ CSR, SELL = 0, 1
 class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_vectors", C.c_int), ("criterion", C.c_int), ("rms_tol", C.c_double),
                 ("seed", C.c_uint64), ("defl_tol", C.c_double), ("storage", C.c_int), ("polish", C.c_int),
-                ("stage1_tol", C.c_double), ("check_every", C.c_int), ("stream", C.c_void_p)]
+                ("stage1_tol", C.c_double), ("check_every", C.c_int), ("stream", C.c_void_p),
+                ("ritz_overlap", C.c_int)]
 
 
 class Stats(C.Structure):

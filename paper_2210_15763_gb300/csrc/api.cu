@@ -72,6 +72,7 @@ void bbl_options_default(bbl_options* o) {
     o->polish = 1;
     o->stage1_tol = 2e-6;
     o->check_every = 0;
+    o->ritz_overlap = 1;
     o->stream = nullptr;
 }
 

@@ -9,9 +9,11 @@
 //               factorisation of T - sigma I is the number of eigenvalues below
 //               sigma.  For p in {1, 2, 4, 8, 16} a group of p+1 lanes holds
 //               the elimination window in registers and evaluates one shift
-//               (32/(p+1) shifts per warp, 24 per CTA for p = 8); otherwise a
-//               warp per shift with the window in shared memory.  Multisection
-//               runs in FP32 (58x the FP64 rate on this GPU) to a bracket of
+//               (32/(p+1) shifts per warp, 24 per CTA for p = 8); for
+//               p in {1, 2, 4, 8} every thread holds a whole window and
+//               evaluates its own shift (256 per CTA); otherwise a warp per
+//               shift with the window in shared memory.  Multisection runs in
+//               FP32 (58x the FP64 rate on this GPU) to a bracket of
 //               1e-5 * scale, starting from the previous Ritz value when one is
 //               given (Cauchy interlacing makes it an upper bound); FP64 counts
 //               check the bracket and FP64 multisection narrows it to
@@ -190,6 +192,220 @@ __device__ int inertia_count_reg(const double* __restrict__ Tb, int m, double si
         piv = (piv + 1 == P1) ? 0 : piv + 1;
     }
     return neg;
+}
+
+// The same count by a single lane: the lower triangle of the (P+1)x(P+1)
+// active window lives in the lane's registers, relative to the pivot row,
+// and every thread of a CTA evaluates its own shift.  A step forms the
+// multipliers of column k from one reciprocal, updates the 36 (P = 8)
+// remaining entries, shifts the window and takes the next row of T (the
+// same address for all lanes).  No lane talks to another.
+template <typename F>
+__device__ __forceinline__ F recip(F d) {
+    if constexpr (sizeof(F) == 4) {
+        return __frcp_rn(d);
+    } else {
+        // FP32 seed and one Newton step (relative error ~2^-46)
+        const double ad = fabs(d);
+        if (ad > 1e-30 && ad < 1e30) {
+            const double r0 = (double)__frcp_rn((float)d);
+            return r0 * fma(-d, r0, 2.0);
+        }
+        return 1.0 / d;
+    }
+}
+
+template <typename F, int P>
+__device__ int count_lane(const double* __restrict__ Tb, int m, double sigma, double pivmin) {
+    constexpr int P1 = P + 1;
+    const F big = (F)1e30;
+    const F fpivmin = (F)pivmin;
+    F E[P1][P1];
+#pragma unroll
+    for (int r = 0; r < P1; ++r)
+#pragma unroll
+        for (int c = 0; c < P1; ++c) {
+            F v = F(0);
+            if (c <= r) {
+                if (r >= m) {
+                    v = (r == c) ? big : F(0);
+                } else {
+                    double t = Tb[(int64_t)r * P1 + (r - c)];
+                    if (r == c) t -= sigma;
+                    v = (F)t;
+                }
+            }
+            E[r][c] = v;
+        }
+    int neg = 0;
+    for (int k = 0; k < m; ++k) {
+        F d = E[0][0];
+        if (fabs(d) < fpivmin) d = -fpivmin;
+        neg += (d < F(0)) ? 1 : 0;
+        const F rd = recip<F>(d);
+        F l[P1];
+#pragma unroll
+        for (int r = 1; r < P1; ++r) l[r] = E[r][0] * rd;
+#pragma unroll
+        for (int r = 1; r < P1; ++r)
+#pragma unroll
+            for (int c = 1; c <= r; ++c) E[r - 1][c - 1] = fma(-l[r], E[c][0], E[r][c]);
+        const int R = k + P1;  // row entering the window: columns k+1 .. k+P+1
+        if (R < m) {
+            const double* row = Tb + (int64_t)R * P1;
+#pragma unroll
+            for (int c = 0; c < P1; ++c) {
+                double t = row[P - c];
+                if (c == P) t -= sigma;
+                E[P][c] = (F)t;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < P1; ++c) E[P][c] = (c == P) ? big : F(0);
+        }
+    }
+    return neg;
+}
+
+// Bisection with one shift per thread (p in {1, 2, 4, 8}): FP32 multisection
+// with 256 shifts per round to a 1e-5 * scale bracket, its ends checked with
+// FP64 counts, then FP64 multisection by four lanes to 1e-8 * scale; a failed
+// check restarts from the Gershgorin interval (warm start) or falls back to
+// FP64 multisection by one warp (32 shifts a round).
+template <int P>
+__global__ void __launch_bounds__(256) bisect_lane_kernel(int m, int nev, const double* __restrict__ Tg,
+                                                         double* __restrict__ theta_out, double* __restrict__ width_out,
+                                                         int band_in_smem, SegArgs sa, const double* __restrict__ warm,
+                                                         int warm_count) {
+    constexpr int NT = 256;
+    constexpr int p = P;
+    __shared__ int counts[NT];
+    __shared__ double red[2][NT];
+    __shared__ double s_lo, s_hi;
+    extern __shared__ double tb_sh[];
+    const int i = blockIdx.x;
+    const int seg = blockIdx.y;
+    if (sa.active && !sa.active[seg]) return;
+    if (sa.d_m) m = *sa.d_m;
+    if (i >= min(nev, m)) return;
+    Tg += seg * sa.sT;
+    theta_out += seg * sa.sTh;
+    width_out += seg * sa.sTh;
+    const int tid = threadIdx.x;
+    const double* Tb = Tg;
+    if (band_in_smem) {
+        for (int e = tid; e < m * (p + 1); e += NT) tb_sh[e] = Tg[e];
+        __syncthreads();
+        Tb = tb_sh;
+    }
+    double gmin = 1e308, gmax = -1e308;
+    for (int r = tid; r < m; r += NT) {
+        double off = 0.0;
+        for (int c = max(0, r - p); c <= min(m - 1, r + p); ++c)
+            if (c != r) off += fabs(band_get(Tb, p, m, r, c));
+        const double d = band_get(Tb, p, m, r, r);
+        gmin = fmin(gmin, d - off);
+        gmax = fmax(gmax, d + off);
+    }
+    red[0][tid] = gmin;
+    red[1][tid] = gmax;
+    __syncthreads();
+    if (tid == 0) {
+        for (int t = 1; t < NT; ++t) {
+            gmin = fmin(gmin, red[0][t]);
+            gmax = fmax(gmax, red[1][t]);
+        }
+        const double scale = fmax(fabs(gmin), fabs(gmax));
+        const double pad = 1e-10 * scale + 1e-300;
+        s_lo = gmin - pad;
+        s_hi = gmax + pad;
+    }
+    __syncthreads();
+    const double scale = fmax(fmax(fabs(s_lo), fabs(s_hi)), 1e-300);
+    const double pivmin64 = 1e-14 * scale;
+    const double pivmin32 = 1e-7 * scale;
+    const double glo = s_lo, ghi = s_hi;
+    double lo = glo, hi = ghi;
+    const bool warm_used = warm && i < warm_count;
+    if (warm_used) {
+        const double w = warm[i];
+        hi = fmin(ghi, w + 1e-9 * scale);
+        lo = fmax(glo, w - 1e-3 * scale);
+        if (!(lo < hi)) {
+            lo = glo;
+            hi = ghi;
+        }
+    }
+    auto update = [&](int ns, double& a, double& b) -> bool {
+        // counts[0..ns) at a + (b-a)(t+1)/(ns+1); returns false when they are inconsistent
+        double nlo = a, nhi = b;
+        for (int t = 0; t < ns; ++t) {
+            const double s = a + (b - a) * (double)(t + 1) / (double)(ns + 1);
+            if (counts[t] <= i) nlo = fmax(nlo, s);
+            else nhi = fmin(nhi, s);
+        }
+        if (nlo >= nhi) return false;
+        a = nlo;
+        b = nhi;
+        return true;
+    };
+    bool verified = false;
+    for (int attempt = 0; attempt < (warm_used ? 2 : 1) && !verified; ++attempt) {
+        if (attempt == 1) {
+            lo = glo;
+            hi = ghi;
+        }
+        for (int round = 0; round < 40 && (hi - lo) > 1e-5 * scale; ++round) {
+            const double sigma = lo + (hi - lo) * (double)(tid + 1) / (double)(NT + 1);
+            counts[tid] = count_lane<float, P>(Tb, m, sigma, pivmin32);
+            __syncthreads();
+            const bool ok = update(NT, lo, hi);
+            __syncthreads();
+            if (!ok) break;  // inconsistent FP32 counts: the FP64 check decides
+        }
+        if (tid < 32) {
+            // FP64 counts at the two ends (lanes 0 and 1; the rest of the warp idles)
+            int c = 0;
+            if (tid < 2) c = count_lane<double, P>(Tb, m, tid == 0 ? lo : hi, pivmin64);
+            if (tid < 2) counts[tid] = c;
+        }
+        __syncthreads();
+        verified = counts[0] <= i && counts[1] > i;
+        __syncthreads();
+    }
+    if (!verified) {
+        // FP64 multisection by warp 0 from the Gershgorin interval to 1e-8 * scale
+        lo = glo;
+        hi = ghi;
+        for (int round = 0; round < 60 && (hi - lo) > 1e-8 * scale; ++round) {
+            if (tid < 32) {
+                const double sigma = lo + (hi - lo) * (double)(tid + 1) / 33.0;
+                counts[tid] = count_lane<double, P>(Tb, m, sigma, pivmin64);
+            }
+            __syncthreads();
+            const bool ok = update(32, lo, hi);
+            __syncthreads();
+            if (!ok) break;
+        }
+    } else {
+        // FP64 multisection of the verified bracket to 1e-8 * scale with four
+        // lanes (FP64 throughput is 1/64 of FP32: few lanes, latency-bound)
+        for (int round = 0; round < 20 && (hi - lo) > 1e-8 * scale; ++round) {
+            if (tid < 32) {
+                int c = 0;
+                if (tid < 4) c = count_lane<double, P>(Tb, m, lo + (hi - lo) * (double)(tid + 1) / 5.0, pivmin64);
+                if (tid < 4) counts[tid] = c;
+            }
+            __syncthreads();
+            const bool ok = update(4, lo, hi);
+            __syncthreads();
+            if (!ok) break;
+        }
+    }
+    if (tid == 0) {
+        theta_out[i] = 0.5 * (lo + hi);
+        width_out[i] = hi - lo;
+    }
 }
 
 // Shifts evaluated at once per CTA: one per warp (window in shared memory,
@@ -586,82 +802,93 @@ __global__ void __launch_bounds__(32) invit_reg_kernel(int m, const double* __re
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) scale = fmax(scale, __shfl_xor_sync(0xffffffffu, scale, off));
     const double tiny = 1e-14 * fmax(scale, 1e-300);
-    // ---- banded LU with partial pivoting of T - sigma I (rows k..k+p, columns k..k+2p in the window)
-    for (int e = lane; e < P1 * UW; e += 32) {
-        const int r = e / UW, c = e % UW;
-        double v = (r < m && c < m) ? band_get(Tb, p, m, r, c) : 0.0;
-        if (r == c && r < m) v -= sigma;
-        win[(r % P1) * UW + (c % UW)] = v;
+    // ---- banded LU with partial pivoting of T - sigma I.  The window is
+    // rows k..k+p x columns k..k+2p; lane l holds column k+c with
+    // c = (l - k) mod (2p+1) as registers col[r] = A_k[k+r][k+c], r = 0..p.
+    // Step k: the pivot column's lane finds the pivot row, every lane swaps
+    // rows 0 and bi of its column, the multipliers of column k are broadcast,
+    // every lane updates its column, writes row k of U, shifts its rows up
+    // and takes its entry of the next row of T.  The lane of column k then
+    // holds column k+2p+1.
+    auto tget = [&](int r, int c) -> double {  // T - sigma I, 0 outside
+        if (r < 0 || c < 0 || r >= m || c >= m) return 0.0;
+        const int d = r - c;
+        double v = 0.0;
+        if (d >= 0 && d <= p) v = Tb[(int64_t)r * P1 + d];
+        else if (d < 0 && -d <= p) v = Tb[(int64_t)c * P1 - d];
+        if (d == 0) v -= sigma;
+        return v;
+    };
+    double col[P1];
+    int cl = lane < UW ? lane : 0;  // this lane's column offset from k
+#pragma unroll
+    for (int r = 0; r < P1; ++r) col[r] = (lane < UW) ? tget(r, cl) : 0.0;
+    int lk = 0;  // lane holding column k
+    for (int k = 0; k < m; ++k) {
+        // pivot: largest |entry| of column k among rows k..min(k+p, m-1) (lowest index on ties)
+        int bi = 0;
+        {
+            double best = fabs(col[0]);
+#pragma unroll
+            for (int r = 1; r < P1; ++r) {
+                const double v = fabs(col[r]);
+                if (k + r < m && v > best) {
+                    best = v;
+                    bi = r;
+                }
+            }
+        }
+        bi = __shfl_sync(0xffffffffu, bi, lk);
+        // interchange rows 0 and bi in every column
+#pragma unroll
+        for (int r = 1; r < P1; ++r) {
+            if (r == bi) {
+                const double t = col[0];
+                col[0] = col[r];
+                col[r] = t;
+            }
+        }
+        double u = __shfl_sync(0xffffffffu, col[0], lk);
+        if (fabs(u) < tiny) u = (u < 0.0) ? -tiny : tiny;
+        if (lane == lk) col[0] = u;
+        const double ru = recip<double>(u);
+        double lmul[P1];
+#pragma unroll
+        for (int r = 1; r < P1; ++r) lmul[r] = (k + r < m) ? __shfl_sync(0xffffffffu, col[r], lk) * ru : 0.0;
+        if (lane < UW) {
+            U[(int64_t)k * UW + cl] = col[0];
+            if (lane != lk) {
+#pragma unroll
+                for (int r = 1; r < P1; ++r) col[r] = fma(-lmul[r], col[0], col[r]);
+            }
+        }
+        if (lane >= 1 && lane <= p) {
+#pragma unroll
+            for (int r = 1; r < P1; ++r)
+                if (r == lane) L[(int64_t)k * p + r - 1] = lmul[r];
+        }
+        if (lane == 0) piv[k] = k + bi;
+        // shift rows up; the new bottom row is row k+p+1 of T
+        if (lane < UW) {
+#pragma unroll
+            for (int r = 0; r < P; ++r) col[r] = col[r + 1];
+            if (lane == lk) {
+                cl = UW - 1;  // this lane now holds column k+1+2p
+#pragma unroll
+                for (int r = 0; r < P; ++r) col[r] = 0.0;
+            } else {
+                cl -= 1;
+            }
+            col[P] = tget(k + P1, k + 1 + cl);
+        }
+        lk = (lk + 1 == UW) ? 0 : lk + 1;
     }
     __syncwarp();
-    for (int k = 0; k < m; ++k) {
-        const int ks = k % P1;
-        const int kc = k % UW;
-        double best = -1.0;
-        int bi = 0;
-        if (lane <= p && k + lane < m) {
-            best = fabs(win[((k + lane) % P1) * UW + kc]);
-            bi = lane;
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, off);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-            if (ob > best || (ob == best && oi < bi)) {
-                best = ob;
-                bi = oi;
-            }
-        }
-        const int ps = (k + bi) % P1;
-        if (bi != 0) {
-            for (int c = lane; c < UW; c += 32) {
-                const int cs = (k + c) % UW;
-                const double a = win[ks * UW + cs], b2 = win[ps * UW + cs];
-                win[ks * UW + cs] = b2;
-                win[ps * UW + cs] = a;
-            }
-        }
-        __syncwarp();
-        if (lane == 0) {
-            piv[k] = k + bi;
-            double u = win[ks * UW + kc];
-            if (fabs(u) < tiny) u = (u < 0.0) ? -tiny : tiny;
-            win[ks * UW + kc] = u;
-        }
-        __syncwarp();
-        for (int c = lane; c < UW; c += 32) U[(int64_t)k * UW + c] = win[ks * UW + (k + c) % UW];
-        const double u0 = win[ks * UW + kc];
-        if (lane >= 1 && lane <= p) {
-            const double l = (k + lane < m) ? win[((k + lane) % P1) * UW + kc] / u0 : 0.0;
-            lsh[lane - 1] = l;
-            L[(int64_t)k * p + lane - 1] = l;
-        }
-        __syncwarp();
-        for (int c = lane; c < UW; c += 32) {
-            if (c == 0) continue;
-            const int cs = (k + c) % UW;
-            const double top = win[ks * UW + cs];
-#pragma unroll
-            for (int r = 1; r <= p; ++r) {
-                const int rs = (k + r) % P1;
-                win[rs * UW + cs] -= lsh[r - 1] * top;
-            }
-        }
-        __syncwarp();
-        const int R = k + p + 1;
-        for (int c = lane; c < UW; c += 32) {
-            const int C = k + 1 + c;
-            double v = 0.0;
-            if (R < m && C < m) v = band_get(Tb, p, m, R, C) - (R == C ? sigma : 0.0);
-            win[ks * UW + (C % UW)] = v;
-        }
-        if (lane >= 1 && lane <= p) win[((k + lane) % P1) * UW + kc] = 0.0;
-        __syncwarp();
-    }
     // ---- inverse iteration: the shift is within 1e-8 * scale of the
     // eigenvalue and eigenvalues closer than 1e-3 * scale form a cluster, so
-    // each step shrinks the other components by 1e-5 or more: three suffice
-    // the divisions of the backward solve use the reciprocals of U's diagonal
+    // each step shrinks the other components by 1e-5 or more: three steps
+    // reach working precision.  The backward solve multiplies by the
+    // reciprocals of U's diagonal.
     for (int r = lane; r < m; r += 32) U[(int64_t)r * UW] = 1.0 / U[(int64_t)r * UW];
     for (int r = lane; r < m; r += 32) x[r] = hash_uniform((uint64_t)i + 1, (uint64_t)r);
     __syncwarp();
@@ -971,10 +1198,10 @@ bbl_status set_ritz_attrs() {
     static bool attr_set = false;
     if (!attr_set) {
         BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
-        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
-        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
-        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
-        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(bisect_lane_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(bisect_lane_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(bisect_lane_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(bisect_lane_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
         BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
         BBL_CUDA(cudaFuncSetAttribute(invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024)));
         BBL_CUDA(cudaFuncSetAttribute(invit_reg_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvitSmemMax));
@@ -993,10 +1220,10 @@ bbl_status launch_bisect(dim3 grid, int m, int p, int nev, const double* Tb, dou
     const size_t sm = band_smem ? band_bytes : 0;
     const unsigned th = 32 * kBisectWarps;
     switch (p) {
-        case 1: bisect_kernel<1><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
-        case 2: bisect_kernel<2><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
-        case 4: bisect_kernel<4><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
-        case 8: bisect_kernel<8><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
+        case 1: bisect_lane_kernel<1><<<grid, 256, sm, st>>>(m, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
+        case 2: bisect_lane_kernel<2><<<grid, 256, sm, st>>>(m, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
+        case 4: bisect_lane_kernel<4><<<grid, 256, sm, st>>>(m, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
+        case 8: bisect_lane_kernel<8><<<grid, 256, sm, st>>>(m, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
         case 16: bisect_kernel<16><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
         default: bisect_kernel<0><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count);
     }

@@ -380,8 +380,12 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     // j+1 was speculative and is not used.
     Timer tm;
     BBL_TRY(tm.init());
+    // ritz_overlap = 0: the Ritz solve runs on the caller's stream right after
+    // its block and is read at once (no speculative block, no concurrency)
+    const bool serial = o.ritz_overlap == 0;
     cudaStream_t side = nullptr;
-    BBL_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    if (serial) side = st;
+    else BBL_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
     struct SideGuard {
         cudaStream_t s;
         cudaEvent_t e[6];
@@ -393,7 +397,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             for (auto& x : e)
                 if (x) cudaEventDestroy(x);
         }
-    } guard{side, {}};
+    } guard{serial ? nullptr : side, {}};
     for (int q = 0; q < 6; ++q) BBL_CUDA(cudaEventCreate(&guard.e[q]));
     cudaEvent_t* ev_main = guard.e;       // [2] main-stream block done
     cudaEvent_t* ev_r0 = guard.e + 2;     // [2] Ritz start
@@ -520,6 +524,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             // a new Ritz solve may reuse the buffers of block j-2 only: the one of block j-1 is pending
             BBL_TRY(launch_ritz(j));
         }
+        if (serial && want) pending = j;  // read this block's report now
         if (pending >= 0) {
             bool done = false;
             BBL_TRY(check_ritz(pending, &done));
@@ -530,7 +535,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
                 break;
             }
         }
-        if (want) pending = j;
+        if (want && !serial) pending = j;
         if (last) break;
         if (h_ndefl[0] > last_defl) {
             BBL_TRY(replace_deflated(j + 1, Wn, d_mask));
