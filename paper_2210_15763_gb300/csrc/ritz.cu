@@ -243,13 +243,17 @@ __device__ int count_lane(const double* __restrict__ Tb, int m, double sigma, do
         if (fabs(d) < fpivmin) d = -fpivmin;
         neg += (d < F(0)) ? 1 : 0;
         const F rd = recip<F>(d);
-        F l[P1];
+        F l[P1], e0[P1];
 #pragma unroll
-        for (int r = 1; r < P1; ++r) l[r] = E[r][0] * rd;
+        for (int r = 1; r < P1; ++r) {
+            e0[r] = E[r][0];
+            l[r] = e0[r] * rd;
+        }
+        // in place: entry (r, c) moves to (r-1, c-1) after it has been read
 #pragma unroll
         for (int r = 1; r < P1; ++r)
 #pragma unroll
-            for (int c = 1; c <= r; ++c) E[r - 1][c - 1] = fma(-l[r], E[c][0], E[r][c]);
+            for (int c = 1; c <= r; ++c) E[r - 1][c - 1] = fma(-l[r], e0[c], E[r][c]);
         const int R = k + P1;  // row entering the window: columns k+1 .. k+P+1
         if (R < m) {
             const double* row = Tb + (int64_t)R * P1;
