@@ -101,3 +101,36 @@ __device__ __forceinline__ T shfl_xor_any(unsigned mask, T v, int off) {
 }
 
 }  // namespace bbl
+
+namespace bbl {
+namespace dfm {
+
+// normalised float-float operations for the sequential recurrences of the
+// Ritz solve (where FP64 would cost one 64-cycle issue slot per instruction)
+__device__ __forceinline__ df32 dmul(df32 a, df32 b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return renorm(p, e);
+}
+
+// c + a * b, normalised
+__device__ __forceinline__ df32 dfma(df32 a, df32 b, df32 c) {
+    const df32 t = fma(a, b, c);
+    return renorm(t.hi, t.lo);
+}
+
+__device__ __forceinline__ df32 dneg(df32 a) { return df32(-a.hi, -a.lo); }
+
+// 1 / a: FP32 seed and one Newton step in float-float (about 46 bits)
+__device__ __forceinline__ df32 drcp(df32 a) {
+    const float r0 = __frcp_rn(a.hi);
+    // e = 1 - a * r0 (exact product terms, then the float-float difference)
+    const df32 ar = dmul(a, df32(r0));
+    const df32 e = df32(1.0f) - ar;
+    return dfma(df32(r0), e, df32(r0));
+}
+
+}  // namespace dfm
+}  // namespace bbl

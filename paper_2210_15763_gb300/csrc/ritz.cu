@@ -30,6 +30,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "df32.cuh"
 
 namespace bbl {
 namespace {
@@ -194,45 +195,56 @@ __device__ int inertia_count_reg(const double* __restrict__ Tb, int m, double si
     return neg;
 }
 
-// The same count by a single lane: the lower triangle of the (P+1)x(P+1)
-// active window lives in the lane's registers, relative to the pivot row,
+// The same count by a single thread: the lower triangle of the (P+1)x(P+1)
+// active window lives in the thread's registers, relative to the pivot row,
 // and every thread of a CTA evaluates its own shift.  A step forms the
-// multipliers of column k from one reciprocal, updates the 36 (P = 8)
-// remaining entries, shifts the window and takes the next row of T (the
-// same address for all lanes).  No lane talks to another.
+// multipliers of column k from one reciprocal, updates the remaining
+// entries, shifts the window and takes the next row of T (the same address
+// for all threads).  No thread talks to another.  The band comes as an FP32
+// or float-float copy (band[i*(P+1) + d] = T[i][i-d]): GB300 issues one FP64
+// warp instruction per 64 cycles per scheduler, so the recurrences run on
+// the FP32 pipes only, in FP32 (F = float) or float-float (F = df32).
 template <typename F>
-__device__ __forceinline__ F recip(F d) {
-    if constexpr (sizeof(F) == 4) {
-        return __frcp_rn(d);
-    } else {
-        // FP32 seed and one Newton step (relative error ~2^-46)
-        const double ad = fabs(d);
-        if (ad > 1e-30 && ad < 1e30) {
-            const double r0 = (double)__frcp_rn((float)d);
-            return r0 * fma(-d, r0, 2.0);
-        }
-        return 1.0 / d;
-    }
-}
+struct RitzArith;
+
+template <>
+struct RitzArith<float> {
+    static __device__ __forceinline__ float fms(float l, float e, float x) { return __fmaf_rn(-l, e, x); }  // x - l e
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float hi(float a) { return a; }
+    static __device__ __forceinline__ float make(float h) { return h; }
+};
+
+template <>
+struct RitzArith<df32> {
+    static __device__ __forceinline__ df32 fms(df32 l, df32 e, df32 x) { return dfm::dfma(dfm::dneg(l), e, x); }
+    static __device__ __forceinline__ df32 mul(df32 a, df32 b) { return dfm::dmul(a, b); }
+    static __device__ __forceinline__ df32 rcp(df32 a) { return dfm::drcp(a); }
+    static __device__ __forceinline__ df32 sub(df32 a, df32 b) { return a - b; }
+    static __device__ __forceinline__ float hi(df32 a) { return a.hi; }
+    static __device__ __forceinline__ df32 make(float h) { return df32(h); }
+};
 
 template <typename F, int P>
-__device__ int count_lane(const double* __restrict__ Tb, int m, double sigma, double pivmin) {
+__device__ int count_lane(const F* __restrict__ band, int m, F sigma, float pivmin) {
+    using A = RitzArith<F>;
     constexpr int P1 = P + 1;
-    const F big = (F)1e30;
-    const F fpivmin = (F)pivmin;
+    const F big = A::make(1e30f);
+    const F zero = A::make(0.0f);
     F E[P1][P1];
 #pragma unroll
     for (int r = 0; r < P1; ++r)
 #pragma unroll
         for (int c = 0; c < P1; ++c) {
-            F v = F(0);
+            F v = zero;
             if (c <= r) {
                 if (r >= m) {
-                    v = (r == c) ? big : F(0);
+                    v = (r == c) ? big : zero;
                 } else {
-                    double t = Tb[(int64_t)r * P1 + (r - c)];
-                    if (r == c) t -= sigma;
-                    v = (F)t;
+                    v = band[r * P1 + (r - c)];
+                    if (r == c) v = A::sub(v, sigma);
                 }
             }
             E[r][c] = v;
@@ -240,53 +252,53 @@ __device__ int count_lane(const double* __restrict__ Tb, int m, double sigma, do
     int neg = 0;
     for (int k = 0; k < m; ++k) {
         F d = E[0][0];
-        if (fabs(d) < fpivmin) d = -fpivmin;
-        neg += (d < F(0)) ? 1 : 0;
-        const F rd = recip<F>(d);
+        if (fabsf(A::hi(d)) < pivmin) d = A::make(-pivmin);
+        neg += (A::hi(d) < 0.0f) ? 1 : 0;
+        const F rd = A::rcp(d);
         F l[P1], e0[P1];
 #pragma unroll
         for (int r = 1; r < P1; ++r) {
             e0[r] = E[r][0];
-            l[r] = e0[r] * rd;
+            l[r] = A::mul(e0[r], rd);
         }
         // in place: entry (r, c) moves to (r-1, c-1) after it has been read
 #pragma unroll
         for (int r = 1; r < P1; ++r)
 #pragma unroll
-            for (int c = 1; c <= r; ++c) E[r - 1][c - 1] = fma(-l[r], e0[c], E[r][c]);
+            for (int c = 1; c <= r; ++c) E[r - 1][c - 1] = A::fms(l[r], e0[c], E[r][c]);
         const int R = k + P1;  // row entering the window: columns k+1 .. k+P+1
         if (R < m) {
-            const double* row = Tb + (int64_t)R * P1;
+            const F* row = band + R * P1;
 #pragma unroll
-            for (int c = 0; c < P1; ++c) {
-                double t = row[P - c];
-                if (c == P) t -= sigma;
-                E[P][c] = (F)t;
-            }
+            for (int c = 0; c < P1; ++c) E[P][c] = row[P - c];
+            E[P][P] = A::sub(E[P][P], sigma);
         } else {
 #pragma unroll
-            for (int c = 0; c < P1; ++c) E[P][c] = (c == P) ? big : F(0);
+            for (int c = 0; c < P1; ++c) E[P][c] = (c == P) ? big : zero;
         }
     }
     return neg;
 }
 
-// Bisection with one shift per thread (p in {1, 2, 4, 8}): FP32 multisection
-// with 256 shifts per round to a 1e-5 * scale bracket, its ends checked with
-// FP64 counts, then FP64 multisection by four lanes to 1e-8 * scale; a failed
-// check restarts from the Gershgorin interval (warm start) or falls back to
-// FP64 multisection by one warp (32 shifts a round).
+// Bisection with one shift per thread (p in {1, 2, 4, 8}): FP32
+// multisection with 256 shifts per round to a 1e-5 * scale bracket, then one
+// float-float round by a warp whose first and last lanes sit on the bracket
+// ends (the check) and whose 30 others narrow it 31-fold; a failed check
+// restarts from the Gershgorin interval (warm start) and then falls back to
+// float-float multisection by one warp.  The band is staged in shared memory
+// as FP32 and float-float copies (bands longer than the staging area use
+// the slower copies in the caller-provided scratch).
 template <int P>
 __global__ void __launch_bounds__(256) bisect_lane_kernel(int m, int nev, const double* __restrict__ Tg,
                                                          double* __restrict__ theta_out, double* __restrict__ width_out,
                                                          int band_in_smem, SegArgs sa, const double* __restrict__ warm,
                                                          int warm_count) {
     constexpr int NT = 256;
-    constexpr int p = P;
+    constexpr int p = P, P1 = P + 1;
     __shared__ int counts[NT];
     __shared__ double red[2][NT];
     __shared__ double s_lo, s_hi;
-    extern __shared__ double tb_sh[];
+    extern __shared__ __align__(16) unsigned char bl_smem[];
     const int i = blockIdx.x;
     const int seg = blockIdx.y;
     if (sa.active && !sa.active[seg]) return;
@@ -296,12 +308,16 @@ __global__ void __launch_bounds__(256) bisect_lane_kernel(int m, int nev, const 
     theta_out += seg * sa.sTh;
     width_out += seg * sa.sTh;
     const int tid = threadIdx.x;
-    const double* Tb = Tg;
-    if (band_in_smem) {
-        for (int e = tid; e < m * (p + 1); e += NT) tb_sh[e] = Tg[e];
-        __syncthreads();
-        Tb = tb_sh;
+    // FP32 and float-float copies of the band (shared memory)
+    df32* bdf = reinterpret_cast<df32*>(bl_smem);
+    float* b32 = reinterpret_cast<float*>(bdf + (size_t)m * P1);
+    for (int e = tid; e < m * P1; e += NT) {
+        const double v = Tg[e];
+        bdf[e] = df32(v);
+        b32[e] = (float)v;
     }
+    __syncthreads();
+    const double* Tb = Tg;
     double gmin = 1e308, gmax = -1e308;
     for (int r = tid; r < m; r += NT) {
         double off = 0.0;
@@ -326,8 +342,8 @@ __global__ void __launch_bounds__(256) bisect_lane_kernel(int m, int nev, const 
     }
     __syncthreads();
     const double scale = fmax(fmax(fabs(s_lo), fabs(s_hi)), 1e-300);
-    const double pivmin64 = 1e-14 * scale;
-    const double pivmin32 = 1e-7 * scale;
+    const float pivmin32 = (float)(1e-7 * scale);
+    const float pivmindf = (float)(1e-13 * scale);
     const double glo = s_lo, ghi = s_hi;
     double lo = glo, hi = ghi;
     const bool warm_used = warm && i < warm_count;
@@ -340,13 +356,13 @@ __global__ void __launch_bounds__(256) bisect_lane_kernel(int m, int nev, const 
             hi = ghi;
         }
     }
+    // counts[t] at lo + (hi-lo)*(t+1)/(ns+1); false when they are inconsistent
     auto update = [&](int ns, double& a, double& b) -> bool {
-        // counts[0..ns) at a + (b-a)(t+1)/(ns+1); returns false when they are inconsistent
         double nlo = a, nhi = b;
         for (int t = 0; t < ns; ++t) {
-            const double s = a + (b - a) * (double)(t + 1) / (double)(ns + 1);
-            if (counts[t] <= i) nlo = fmax(nlo, s);
-            else nhi = fmin(nhi, s);
+            const double sg = a + (b - a) * (double)(t + 1) / (double)(ns + 1);
+            if (counts[t] <= i) nlo = fmax(nlo, sg);
+            else nhi = fmin(nhi, sg);
         }
         if (nlo >= nhi) return false;
         a = nlo;
@@ -360,48 +376,45 @@ __global__ void __launch_bounds__(256) bisect_lane_kernel(int m, int nev, const 
             hi = ghi;
         }
         for (int round = 0; round < 40 && (hi - lo) > 1e-5 * scale; ++round) {
-            const double sigma = lo + (hi - lo) * (double)(tid + 1) / (double)(NT + 1);
-            counts[tid] = count_lane<float, P>(Tb, m, sigma, pivmin32);
+            const double sg = lo + (hi - lo) * (double)(tid + 1) / (double)(NT + 1);
+            counts[tid] = count_lane<float, P>(b32, m, (float)sg, pivmin32);
             __syncthreads();
             const bool ok = update(NT, lo, hi);
             __syncthreads();
-            if (!ok) break;  // inconsistent FP32 counts: the FP64 check decides
+            if (!ok) break;  // inconsistent FP32 counts: the float-float round decides
         }
+        // float-float round: lane 0 at lo, lane 31 at hi, lanes 1..30 inside
         if (tid < 32) {
-            // FP64 counts at the two ends (lanes 0 and 1; the rest of the warp idles)
-            int c = 0;
-            if (tid < 2) c = count_lane<double, P>(Tb, m, tid == 0 ? lo : hi, pivmin64);
-            if (tid < 2) counts[tid] = c;
+            const double sg = lo + (hi - lo) * (double)tid / 31.0;
+            counts[tid] = count_lane<df32, P>(bdf, m, df32(sg), pivmindf);
         }
         __syncthreads();
-        verified = counts[0] <= i && counts[1] > i;
+        verified = counts[0] <= i && counts[31] > i;
+        if (verified) {
+            double nlo = lo, nhi = hi;
+            for (int t = 1; t < 31; ++t) {
+                const double sg = lo + (hi - lo) * (double)t / 31.0;
+                if (counts[t] <= i) nlo = fmax(nlo, sg);
+                else nhi = fmin(nhi, sg);
+            }
+            if (nlo < nhi) {
+                lo = nlo;
+                hi = nhi;
+            }
+        }
         __syncthreads();
     }
     if (!verified) {
-        // FP64 multisection by warp 0 from the Gershgorin interval to 1e-8 * scale
+        // float-float multisection by warp 0 from the Gershgorin interval to 1e-8 * scale
         lo = glo;
         hi = ghi;
         for (int round = 0; round < 60 && (hi - lo) > 1e-8 * scale; ++round) {
             if (tid < 32) {
-                const double sigma = lo + (hi - lo) * (double)(tid + 1) / 33.0;
-                counts[tid] = count_lane<double, P>(Tb, m, sigma, pivmin64);
+                const double sg = lo + (hi - lo) * (double)(tid + 1) / 33.0;
+                counts[tid] = count_lane<df32, P>(bdf, m, df32(sg), pivmindf);
             }
             __syncthreads();
             const bool ok = update(32, lo, hi);
-            __syncthreads();
-            if (!ok) break;
-        }
-    } else {
-        // FP64 multisection of the verified bracket to 1e-8 * scale with four
-        // lanes (FP64 throughput is 1/64 of FP32: few lanes, latency-bound)
-        for (int round = 0; round < 20 && (hi - lo) > 1e-8 * scale; ++round) {
-            if (tid < 32) {
-                int c = 0;
-                if (tid < 4) c = count_lane<double, P>(Tb, m, lo + (hi - lo) * (double)(tid + 1) / 5.0, pivmin64);
-                if (tid < 4) counts[tid] = c;
-            }
-            __syncthreads();
-            const bool ok = update(4, lo, hi);
             __syncthreads();
             if (!ok) break;
         }
@@ -754,22 +767,30 @@ __global__ void __launch_bounds__(32) invit_kernel(int m, int p, const double* _
     for (int r = lane; r < m; r += 32) S[(int64_t)r * nev + i] = x[r];
 }
 
-// Inverse iteration for bandwidths P in {1, 2, 4, 8}: the same banded LU
-// with partial pivoting as invit_kernel, with its factors kept in shared
-// memory when they fit (lu_in_smem), and column-oriented triangular solves
-// whose active rows live in registers: the forward solve keeps rows
-// k..k+P in lanes (row r in lane r mod (P+1)), applies the row interchange
-// of step k with two shuffles and updates the rows below with the
-// multipliers of column k; the backward solve keeps rows k-2P..k in lanes
-// (row r in lane r mod (2P+1)), forms x_k = y_k / U_kk and updates the rows
-// above.  One shuffle latency per row instead of a reduction per row.
+// Inverse iteration for bandwidths P in {1, 2, 4, 8}, in float-float
+// arithmetic on the FP32 pipes (a chain of FP64 instructions would wait 64
+// cycles per instruction on GB300).  The band is staged in shared memory as
+// float-float values.  Banded LU with partial pivoting: the window rows
+// k..k+P x columns k..k+2P, lane l holding column k + ((l - k) mod (2P+1))
+// in registers col[r] = A_k[k+r][k+c]; the pivot column's lane finds the
+// pivot row, every lane swaps rows 0 and bi of its column, the multipliers
+// are broadcast, every lane updates its column, writes row k of U, shifts
+// its rows up and takes its entry of the next row of T.  The factors live
+// in shared memory when they fit.  Then four steps of inverse iteration
+// with column-oriented triangular solves whose active rows live in
+// registers (forward: rows k..k+P, backward: rows k-2P..k); the vector is
+// normalised and its Rayleigh quotient formed in FP64.
 template <int P>
-__global__ void __launch_bounds__(32) invit_reg_kernel(int m, const double* __restrict__ Tg, double* __restrict__ theta,
-                                                        double* __restrict__ S, int nev, double* __restrict__ ws,
-                                                        int lu_in_smem, SegArgs sa) {
+__global__ void __launch_bounds__(32) invit_df_kernel(int m, const double* __restrict__ Tg, double* __restrict__ theta,
+                                                       double* __restrict__ S, int nev, double* __restrict__ ws,
+                                                       int lu_in_smem, SegArgs sa) {
+    using dfm::dfma;
+    using dfm::dmul;
+    using dfm::dneg;
+    using dfm::drcp;
     constexpr int p = P, P1 = P + 1, UW = 2 * P + 1;
     static_assert(UW <= 32, "backward window exceeds a warp");
-    extern __shared__ double sm[];
+    extern __shared__ __align__(16) unsigned char ism[];
     const int i = blockIdx.x;
     const int seg = blockIdx.y;
     if (sa.active && !sa.active[seg]) return;
@@ -780,62 +801,56 @@ __global__ void __launch_bounds__(32) invit_reg_kernel(int m, const double* __re
     S += seg * sa.sS;
     ws += seg * sa.sWs;
     const int lane = threadIdx.x;
-    double* win = sm;             // P1 x UW circular window
-    double* x = win + P1 * UW;    // m
-    double* lsh = x + m;          // p multipliers (+ pad)
-    double* U;
-    double* L;
+    df32* bdf = reinterpret_cast<df32*>(ism);   // band, m x (P+1)
+    df32* x = bdf + (size_t)m * P1;              // m
+    df32* U;
+    df32* L;
     int* piv;
     if (lu_in_smem) {
-        U = lsh + p + 8;
-        L = U + (int64_t)m * UW;
-        piv = reinterpret_cast<int*>(L + (int64_t)m * p);
+        U = x + m;
+        L = U + (size_t)m * UW;
+        piv = reinterpret_cast<int*>(L + (size_t)m * p);
     } else {
-        U = ws + (int64_t)i * m * (3 * p + 1);
-        L = U + (int64_t)m * UW;
+        U = reinterpret_cast<df32*>(ws + (int64_t)i * m * (3 * p + 1));
+        L = U + (size_t)m * UW;
         piv = reinterpret_cast<int*>(ws + (int64_t)nev * m * (3 * p + 1)) + (int64_t)i * m;
     }
-    const double* Tb = Tg;
+    for (int e = lane; e < m * P1; e += 32) bdf[e] = df32(Tg[e]);
+    __syncwarp();
     const double sigma = theta[i];
-    double scale = 0.0;
+    const df32 sig(sigma);
+    float scale = 0.0f;
     for (int r = lane; r < m; r += 32) {
-        double s = 0.0;
-        for (int c = max(0, r - p); c <= min(m - 1, r + p); ++c) s += fabs(band_get(Tb, p, m, r, c));
-        scale = fmax(scale, s);
+        float s = 0.0f;
+        for (int d = 0; d <= p && d <= r; ++d) s += fabsf(bdf[r * P1 + d].hi);
+        for (int d = 1; d <= p && r + d < m; ++d) s += fabsf(bdf[(r + d) * P1 + d].hi);
+        scale = fmaxf(scale, s);
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) scale = fmax(scale, __shfl_xor_sync(0xffffffffu, scale, off));
-    const double tiny = 1e-14 * fmax(scale, 1e-300);
-    // ---- banded LU with partial pivoting of T - sigma I.  The window is
-    // rows k..k+p x columns k..k+2p; lane l holds column k+c with
-    // c = (l - k) mod (2p+1) as registers col[r] = A_k[k+r][k+c], r = 0..p.
-    // Step k: the pivot column's lane finds the pivot row, every lane swaps
-    // rows 0 and bi of its column, the multipliers of column k are broadcast,
-    // every lane updates its column, writes row k of U, shifts its rows up
-    // and takes its entry of the next row of T.  The lane of column k then
-    // holds column k+2p+1.
-    auto tget = [&](int r, int c) -> double {  // T - sigma I, 0 outside
-        if (r < 0 || c < 0 || r >= m || c >= m) return 0.0;
+    for (int off = 16; off > 0; off >>= 1) scale = fmaxf(scale, __shfl_xor_sync(0xffffffffu, scale, off));
+    const float tiny = 1e-14f * fmaxf(scale, 1e-30f);
+    const df32 zero(0.0f);
+    auto tget = [&](int r, int c) -> df32 {  // T - sigma I, 0 outside
+        if (r < 0 || c < 0 || r >= m || c >= m) return zero;
         const int d = r - c;
-        double v = 0.0;
-        if (d >= 0 && d <= p) v = Tb[(int64_t)r * P1 + d];
-        else if (d < 0 && -d <= p) v = Tb[(int64_t)c * P1 - d];
-        if (d == 0) v -= sigma;
-        return v;
+        if (d == 0) return bdf[r * P1] - sig;
+        if (d > 0 && d <= p) return bdf[r * P1 + d];
+        if (d < 0 && -d <= p) return bdf[c * P1 - d];
+        return zero;
     };
-    double col[P1];
+    // ---- banded LU with partial pivoting of T - sigma I
+    df32 col[P1];
     int cl = lane < UW ? lane : 0;  // this lane's column offset from k
 #pragma unroll
-    for (int r = 0; r < P1; ++r) col[r] = (lane < UW) ? tget(r, cl) : 0.0;
+    for (int r = 0; r < P1; ++r) col[r] = (lane < UW) ? tget(r, cl) : zero;
     int lk = 0;  // lane holding column k
     for (int k = 0; k < m; ++k) {
-        // pivot: largest |entry| of column k among rows k..min(k+p, m-1) (lowest index on ties)
         int bi = 0;
         {
-            double best = fabs(col[0]);
+            float best = fabsf(col[0].hi);
 #pragma unroll
             for (int r = 1; r < P1; ++r) {
-                const double v = fabs(col[r]);
+                const float v = fabsf(col[r].hi);
                 if (k + r < m && v > best) {
                     best = v;
                     bi = r;
@@ -843,43 +858,44 @@ __global__ void __launch_bounds__(32) invit_reg_kernel(int m, const double* __re
             }
         }
         bi = __shfl_sync(0xffffffffu, bi, lk);
-        // interchange rows 0 and bi in every column
 #pragma unroll
         for (int r = 1; r < P1; ++r) {
             if (r == bi) {
-                const double t = col[0];
+                const df32 t = col[0];
                 col[0] = col[r];
                 col[r] = t;
             }
         }
-        double u = __shfl_sync(0xffffffffu, col[0], lk);
-        if (fabs(u) < tiny) u = (u < 0.0) ? -tiny : tiny;
+        df32 u(__shfl_sync(0xffffffffu, col[0].hi, lk), __shfl_sync(0xffffffffu, col[0].lo, lk));
+        if (fabsf(u.hi) < tiny) u = df32(u.hi < 0.0f ? -tiny : tiny);
         if (lane == lk) col[0] = u;
-        const double ru = recip<double>(u);
-        double lmul[P1];
+        const df32 ru = drcp(u);
+        df32 lmul[P1];
 #pragma unroll
-        for (int r = 1; r < P1; ++r) lmul[r] = (k + r < m) ? __shfl_sync(0xffffffffu, col[r], lk) * ru : 0.0;
+        for (int r = 1; r < P1; ++r) {
+            const df32 a(__shfl_sync(0xffffffffu, col[r].hi, lk), __shfl_sync(0xffffffffu, col[r].lo, lk));
+            lmul[r] = (k + r < m) ? dmul(a, ru) : zero;
+        }
         if (lane < UW) {
-            U[(int64_t)k * UW + cl] = col[0];
+            U[(size_t)k * UW + cl] = col[0];
             if (lane != lk) {
 #pragma unroll
-                for (int r = 1; r < P1; ++r) col[r] = fma(-lmul[r], col[0], col[r]);
+                for (int r = 1; r < P1; ++r) col[r] = dfma(dneg(lmul[r]), col[0], col[r]);
             }
         }
         if (lane >= 1 && lane <= p) {
 #pragma unroll
             for (int r = 1; r < P1; ++r)
-                if (r == lane) L[(int64_t)k * p + r - 1] = lmul[r];
+                if (r == lane) L[(size_t)k * p + r - 1] = lmul[r];
         }
         if (lane == 0) piv[k] = k + bi;
-        // shift rows up; the new bottom row is row k+p+1 of T
         if (lane < UW) {
 #pragma unroll
             for (int r = 0; r < P; ++r) col[r] = col[r + 1];
             if (lane == lk) {
-                cl = UW - 1;  // this lane now holds column k+1+2p
+                cl = UW - 1;  // this lane now holds column k+1+2P
 #pragma unroll
-                for (int r = 0; r < P; ++r) col[r] = 0.0;
+                for (int r = 0; r < P; ++r) col[r] = zero;
             } else {
                 cl -= 1;
             }
@@ -888,82 +904,100 @@ __global__ void __launch_bounds__(32) invit_reg_kernel(int m, const double* __re
         lk = (lk + 1 == UW) ? 0 : lk + 1;
     }
     __syncwarp();
-    // ---- inverse iteration: the shift is within 1e-8 * scale of the
-    // eigenvalue and eigenvalues closer than 1e-3 * scale form a cluster, so
-    // each step shrinks the other components by 1e-5 or more: three steps
-    // reach working precision.  The backward solve multiplies by the
-    // reciprocals of U's diagonal.
-    for (int r = lane; r < m; r += 32) U[(int64_t)r * UW] = 1.0 / U[(int64_t)r * UW];
-    for (int r = lane; r < m; r += 32) x[r] = hash_uniform((uint64_t)i + 1, (uint64_t)r);
+    // reciprocals of U's diagonal for the backward solve
+    for (int r = lane; r < m; r += 32) U[(size_t)r * UW] = drcp(U[(size_t)r * UW]);
+    // pseudo-random start (splitmix-style hash of (index, row))
+    for (int r = lane; r < m; r += 32) {
+        uint64_t z = ((uint64_t)i + 1) * 0x9E3779B97F4A7C15ull + (uint64_t)r + 0x632BE59BD9B4E019ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        x[r] = df32((float)(z >> 40) * 0x1.0p-23f - 1.0f);
+    }
     __syncwarp();
-    for (int it = 0; it < 3; ++it) {
-        // forward: row interchanges and L (rows k..k+P in lanes)
+    for (int it = 0; it < 4; ++it) {
+        // forward: row interchanges and L (row r in lane r mod (P+1))
         {
-            double xv = (lane < P1 && lane < m) ? x[lane] : 0.0;
+            df32 xv = (lane < P1 && lane < m) ? x[lane] : zero;
+            int sk = 0;
             for (int k = 0; k < m; ++k) {
-                const int sk = k % P1;
                 const int pk = piv[k];
-                const int sp = pk % P1;
-                const double xk_new = __shfl_sync(0xffffffffu, xv, sp);
-                const double xk_old = __shfl_sync(0xffffffffu, xv, sk);
-                if (lane == sp) xv = xk_old;
-                if (lane == sk) xv = xk_new;
+                int sp = sk + (pk - k);
+                if (sp >= P1) sp -= P1;
+                const df32 xn(__shfl_sync(0xffffffffu, xv.hi, sp), __shfl_sync(0xffffffffu, xv.lo, sp));
+                const df32 xo(__shfl_sync(0xffffffffu, xv.hi, sk), __shfl_sync(0xffffffffu, xv.lo, sk));
+                if (lane == sp) xv = xo;
+                if (lane == sk) xv = xn;
                 if (lane < P1 && lane != sk) {
                     const int d = lane - sk + (lane < sk ? P1 : 0);  // row k + d
-                    if (k + d < m) xv = fma(-L[(int64_t)k * p + d - 1], xk_new, xv);
+                    if (k + d < m) xv = dfma(dneg(L[(size_t)k * p + d - 1]), xn, xv);
                 }
                 if (lane == sk) {
-                    x[k] = xk_new;
-                    xv = (k + P1 < m) ? x[k + P1] : 0.0;
+                    x[k] = xn;
+                    xv = (k + P1 < m) ? x[k + P1] : zero;
                 }
+                sk = (sk + 1 == P1) ? 0 : sk + 1;
             }
         }
         __syncwarp();
-        // backward: U x = y (rows k-2P..k in lanes)
+        // backward: U x = y (row r in lane r mod (2P+1))
         {
-            double yv = 0.0, rd = 0.0;
+            df32 yv = zero, rd = zero;
+            int sk = (m - 1) % UW;
             {
-                // lane l holds the row r <= m-1 with r % UW == l among the last UW rows
-                const int r = (m - 1) - (((m - 1) % UW - lane + UW) % UW);
+                const int r = (m - 1) - ((sk - lane + UW) % UW);
                 if (lane < UW && r >= 0) {
                     yv = x[r];
-                    rd = U[(int64_t)r * UW];
+                    rd = U[(size_t)r * UW];
                 }
             }
             for (int k = m - 1; k >= 0; --k) {
-                const int sk = k % UW;
-                const double xk = __shfl_sync(0xffffffffu, yv * rd, sk);
+                const df32 t = dmul(yv, rd);
+                const df32 xk(__shfl_sync(0xffffffffu, t.hi, sk), __shfl_sync(0xffffffffu, t.lo, sk));
                 if (lane < UW && lane != sk) {
                     const int c = sk - lane + (lane > sk ? UW : 0);  // row k - c
-                    if (k - c >= 0) yv = fma(-U[(int64_t)(k - c) * UW + c], xk, yv);
+                    if (k - c >= 0) yv = dfma(dneg(U[(size_t)(k - c) * UW + c]), xk, yv);
                 }
                 if (lane == sk) {
                     x[k] = xk;
                     const int r = k - UW;
-                    yv = (r >= 0) ? x[r] : 0.0;
-                    rd = (r >= 0) ? U[(int64_t)r * UW] : 0.0;
+                    yv = (r >= 0) ? x[r] : zero;
+                    rd = (r >= 0) ? U[(size_t)r * UW] : zero;
                 }
+                sk = (sk == 0) ? UW - 1 : sk - 1;
             }
         }
         __syncwarp();
-        double nn = 0.0;
-        for (int r = lane; r < m; r += 32) nn += x[r] * x[r];
+        // rescale (the exact normalisation comes at the end, in FP64)
+        float nn = 0.0f;
+        for (int r = lane; r < m; r += 32) nn = fmaf(x[r].hi, x[r].hi, nn);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, off);
-        const double inv = 1.0 / sqrt(nn);
-        for (int r = lane; r < m; r += 32) x[r] *= inv;
+        const float inv = rsqrtf(nn);
+        for (int r = lane; r < m; r += 32) x[r] = dmul(x[r], df32(inv));
         __syncwarp();
     }
+    // FP64: normalise, Rayleigh quotient, output
+    double* xd = reinterpret_cast<double*>(x);
+    for (int r = lane; r < m; r += 32) xd[r] = (double)x[r];
+    __syncwarp();
+    double nn = 0.0;
+    for (int r = lane; r < m; r += 32) nn += xd[r] * xd[r];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, off);
+    const double inv = 1.0 / sqrt(nn);
+    for (int r = lane; r < m; r += 32) xd[r] *= inv;
+    __syncwarp();
     double rq = 0.0;
     for (int r = lane; r < m; r += 32) {
         double tx = 0.0;
-        for (int c = max(0, r - p); c <= min(m - 1, r + p); ++c) tx += band_get(Tb, p, m, r, c) * x[c];
-        rq += x[r] * tx;
+        for (int c = max(0, r - p); c <= min(m - 1, r + p); ++c) tx += band_get(Tg, p, m, r, c) * xd[c];
+        rq += xd[r] * tx;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) rq += __shfl_xor_sync(0xffffffffu, rq, off);
     if (lane == 0) theta[i] = rq;
-    for (int r = lane; r < m; r += 32) S[(int64_t)r * nev + i] = x[r];
+    for (int r = lane; r < m; r += 32) S[(int64_t)r * nev + i] = xd[r];
 }
 
 // Groups close eigenvalues, orthonormalises their vectors, Rayleigh-Ritz in
@@ -1207,11 +1241,15 @@ bbl_status set_ritz_attrs() {
         BBL_CUDA(cudaFuncSetAttribute(bisect_lane_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
         BBL_CUDA(cudaFuncSetAttribute(bisect_lane_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
         BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(bisect_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
         BBL_CUDA(cudaFuncSetAttribute(invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024)));
-        BBL_CUDA(cudaFuncSetAttribute(invit_reg_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvitSmemMax));
-        BBL_CUDA(cudaFuncSetAttribute(invit_reg_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvitSmemMax));
-        BBL_CUDA(cudaFuncSetAttribute(invit_reg_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvitSmemMax));
-        BBL_CUDA(cudaFuncSetAttribute(invit_reg_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvitSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(invit_df_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvitSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(invit_df_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvitSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(invit_df_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvitSmemMax));
+        BBL_CUDA(cudaFuncSetAttribute(invit_df_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvitSmemMax));
         attr_set = true;
     }
     return BBL_OK;
@@ -1223,13 +1261,25 @@ bbl_status launch_bisect(dim3 grid, int m, int p, int nev, const double* Tb, dou
                          cudaStream_t st) {
     const size_t sm = band_smem ? band_bytes : 0;
     const unsigned th = 32 * kBisectWarps;
-    switch (p) {
-        case 1: bisect_lane_kernel<1><<<grid, 256, sm, st>>>(m, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
-        case 2: bisect_lane_kernel<2><<<grid, 256, sm, st>>>(m, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
-        case 4: bisect_lane_kernel<4><<<grid, 256, sm, st>>>(m, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
-        case 8: bisect_lane_kernel<8><<<grid, 256, sm, st>>>(m, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
-        case 16: bisect_kernel<16><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
-        default: bisect_kernel<0><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count);
+    // one shift per thread: FP32 + float-float band copies in shared memory
+    const size_t lane_smem = (size_t)m * (p + 1) * (sizeof(float) + sizeof(df32));
+    const bool lane = (p == 1 || p == 2 || p == 4 || p == 8) && lane_smem <= kBandSmemMax;
+    if (lane) {
+        switch (p) {
+            case 1: bisect_lane_kernel<1><<<grid, 256, lane_smem, st>>>(m, nev, Tb, theta, width, 1, sa, warm, warm_count); break;
+            case 2: bisect_lane_kernel<2><<<grid, 256, lane_smem, st>>>(m, nev, Tb, theta, width, 1, sa, warm, warm_count); break;
+            case 4: bisect_lane_kernel<4><<<grid, 256, lane_smem, st>>>(m, nev, Tb, theta, width, 1, sa, warm, warm_count); break;
+            default: bisect_lane_kernel<8><<<grid, 256, lane_smem, st>>>(m, nev, Tb, theta, width, 1, sa, warm, warm_count); break;
+        }
+    } else {
+        switch (p) {
+            case 1: bisect_kernel<1><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
+            case 2: bisect_kernel<2><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
+            case 4: bisect_kernel<4><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
+            case 8: bisect_kernel<8><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
+            case 16: bisect_kernel<16><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count); break;
+            default: bisect_kernel<0><<<grid, th, sm, st>>>(m, p, nev, Tb, theta, width, band_smem, sa, warm, warm_count);
+        }
     }
     BBL_LAUNCH_CHECK();
     return BBL_OK;
@@ -1241,19 +1291,20 @@ bbl_status launch_invit(dim3 grid, int m, int p, int nev, const double* Tb, doub
                         SegArgs sa, cudaStream_t st) {
     if (p == 1 || p == 2 || p == 4 || p == 8) {
         const int UW = 2 * p + 1, P1 = p + 1;
-        const size_t base = sizeof(double) * ((size_t)P1 * UW + m + p + 8);
-        const size_t lu = sizeof(double) * (size_t)m * (UW + p) + sizeof(int) * (size_t)m;
-        const int lu_smem = (base + lu <= kInvitSmemMax) ? 1 : 0;
-        const size_t smem = base + (lu_smem ? lu : 0);
-        if (smem > kInvitSmemMax) return set_error(BBL_ERR_UNSUPPORTED, "ritz: m=%d too large for the inverse iteration", m);
-        switch (p) {
-            case 1: invit_reg_kernel<1><<<grid, 32, smem, st>>>(m, Tb, theta, S, nev, ws, lu_smem, sa); break;
-            case 2: invit_reg_kernel<2><<<grid, 32, smem, st>>>(m, Tb, theta, S, nev, ws, lu_smem, sa); break;
-            case 4: invit_reg_kernel<4><<<grid, 32, smem, st>>>(m, Tb, theta, S, nev, ws, lu_smem, sa); break;
-            default: invit_reg_kernel<8><<<grid, 32, smem, st>>>(m, Tb, theta, S, nev, ws, lu_smem, sa); break;
+        const size_t base = sizeof(df32) * ((size_t)m * P1 + m) + 16;
+        const size_t lu = sizeof(df32) * (size_t)m * (UW + p) + sizeof(int) * (size_t)m;
+        if (base <= kInvitSmemMax) {
+            const int lu_smem = (base + lu <= kInvitSmemMax) ? 1 : 0;
+            const size_t smem = base + (lu_smem ? lu : 0);
+            switch (p) {
+                case 1: invit_df_kernel<1><<<grid, 32, smem, st>>>(m, Tb, theta, S, nev, ws, lu_smem, sa); break;
+                case 2: invit_df_kernel<2><<<grid, 32, smem, st>>>(m, Tb, theta, S, nev, ws, lu_smem, sa); break;
+                case 4: invit_df_kernel<4><<<grid, 32, smem, st>>>(m, Tb, theta, S, nev, ws, lu_smem, sa); break;
+                default: invit_df_kernel<8><<<grid, 32, smem, st>>>(m, Tb, theta, S, nev, ws, lu_smem, sa); break;
+            }
+            BBL_LAUNCH_CHECK();
+            return BBL_OK;
         }
-        BBL_LAUNCH_CHECK();
-        return BBL_OK;
     }
     const size_t band_bytes = sizeof(double) * (size_t)m * (p + 1);
     const size_t base = sizeof(double) * ((size_t)(p + 1) * (2 * p + 1) + m + p + 8);
