@@ -298,6 +298,7 @@ __global__ void __launch_bounds__(256) bisect_lane_kernel(int m, int nev, const 
     __shared__ int counts[NT];
     __shared__ double red[2][NT];
     __shared__ double s_lo, s_hi;
+    __shared__ int s_tlo[NT / 32], s_thi[NT / 32];
     extern __shared__ __align__(16) unsigned char bl_smem[];
     const int i = blockIdx.x;
     const int seg = blockIdx.y;
@@ -356,15 +357,35 @@ __global__ void __launch_bounds__(256) bisect_lane_kernel(int m, int nev, const 
             hi = ghi;
         }
     }
-    // counts[t] at lo + (hi-lo)*(t+1)/(ns+1); false when they are inconsistent
+    // New bracket from counts[t] at a + (b-a)(t+1)/(ns+1): the last sample
+    // with at most i eigenvalues below it and the first with more, found by
+    // integer max/min reductions (FP64 instructions are kept out of per-sample
+    // work); false when the counts are inconsistent.
     auto update = [&](int ns, double& a, double& b) -> bool {
-        double nlo = a, nhi = b;
-        for (int t = 0; t < ns; ++t) {
-            const double sg = a + (b - a) * (double)(t + 1) / (double)(ns + 1);
-            if (counts[t] <= i) nlo = fmax(nlo, sg);
-            else nhi = fmin(nhi, sg);
+        const int lane = tid & 31, w = tid >> 5;
+        int tl = -1, th = ns;
+        if (tid < ns) {
+            if (counts[tid] <= i) tl = tid;
+            else th = tid;
         }
-        if (nlo >= nhi) return false;
+        tl = __reduce_max_sync(0xffffffffu, tl);
+        th = __reduce_min_sync(0xffffffffu, th);
+        if (lane == 0) {
+            s_tlo[w] = tl;
+            s_thi[w] = th;
+        }
+        __syncthreads();
+        tl = -1;
+        th = ns;
+        for (int q = 0; q < NT / 32; ++q) {
+            tl = max(tl, s_tlo[q]);
+            th = min(th, s_thi[q]);
+        }
+        __syncthreads();
+        if (tl >= th) return false;
+        const double step = (b - a) / (double)(ns + 1);
+        const double nlo = tl >= 0 ? a + step * (double)(tl + 1) : a;
+        const double nhi = th < ns ? a + step * (double)(th + 1) : b;
         a = nlo;
         b = nhi;
         return true;
@@ -376,7 +397,7 @@ __global__ void __launch_bounds__(256) bisect_lane_kernel(int m, int nev, const 
             hi = ghi;
         }
         for (int round = 0; round < 40 && (hi - lo) > 1e-5 * scale; ++round) {
-            const double sg = lo + (hi - lo) * (double)(tid + 1) / (double)(NT + 1);
+            const double sg = lo + (hi - lo) * ((double)(tid + 1) * (1.0 / (double)(NT + 1)));
             counts[tid] = count_lane<float, P>(b32, m, (float)sg, pivmin32);
             __syncthreads();
             const bool ok = update(NT, lo, hi);
@@ -385,24 +406,22 @@ __global__ void __launch_bounds__(256) bisect_lane_kernel(int m, int nev, const 
         }
         // float-float round: lane 0 at lo, lane 31 at hi, lanes 1..30 inside
         if (tid < 32) {
-            const double sg = lo + (hi - lo) * (double)tid / 31.0;
+            const double sg = tid == 31 ? hi : lo + (hi - lo) * ((double)tid * (1.0 / 31.0));
             counts[tid] = count_lane<df32, P>(bdf, m, df32(sg), pivmindf);
         }
         __syncthreads();
         verified = counts[0] <= i && counts[31] > i;
+        __syncthreads();
         if (verified) {
-            double nlo = lo, nhi = hi;
-            for (int t = 1; t < 31; ++t) {
-                const double sg = lo + (hi - lo) * (double)t / 31.0;
-                if (counts[t] <= i) nlo = fmax(nlo, sg);
-                else nhi = fmin(nhi, sg);
-            }
-            if (nlo < nhi) {
-                lo = nlo;
-                hi = nhi;
+            // the 30 inner samples: counts[1..30] at lo + (hi-lo) t/31
+            if (tid < 30) counts[tid] = counts[tid + 1];
+            __syncthreads();
+            double a = lo, b = hi;
+            if (update(30, a, b)) {
+                lo = a;
+                hi = b;
             }
         }
-        __syncthreads();
     }
     if (!verified) {
         // float-float multisection by warp 0 from the Gershgorin interval to 1e-8 * scale
@@ -410,7 +429,7 @@ __global__ void __launch_bounds__(256) bisect_lane_kernel(int m, int nev, const 
         hi = ghi;
         for (int round = 0; round < 60 && (hi - lo) > 1e-8 * scale; ++round) {
             if (tid < 32) {
-                const double sg = lo + (hi - lo) * (double)(tid + 1) / 33.0;
+                const double sg = lo + (hi - lo) * ((double)(tid + 1) * (1.0 / 33.0));
                 counts[tid] = count_lane<df32, P>(bdf, m, df32(sg), pivmindf);
             }
             __syncthreads();
