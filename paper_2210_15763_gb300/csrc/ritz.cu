@@ -282,8 +282,8 @@ __device__ int count_lane(const F* __restrict__ band, int m, F sigma, float pivm
 
 // Bisection with one shift per thread (p in {1, 2, 4, 8}): FP32
 // multisection with 256 shifts per round to a 1e-5 * scale bracket, then one
-// float-float round by a warp whose first and last lanes sit on the bracket
-// ends (the check) and whose 30 others narrow it 31-fold; a failed check
+// float-float round whose first and last threads sit on the bracket ends
+// (the check) and whose 254 others narrow it 255-fold; a failed check
 // restarts from the Gershgorin interval (warm start) and then falls back to
 // float-float multisection by one warp.  The band is staged in shared memory
 // as FP32 and float-float copies (bands longer than the staging area use
@@ -405,19 +405,23 @@ __global__ void __launch_bounds__(256) bisect_lane_kernel(int m, int nev, const 
             if (!ok) break;  // inconsistent FP32 counts: the float-float round decides
         }
         // float-float round: lane 0 at lo, lane 31 at hi, lanes 1..30 inside
-        if (tid < 32) {
-            const double sg = tid == 31 ? hi : lo + (hi - lo) * ((double)tid * (1.0 / 31.0));
+        {
+            // every thread evaluates one float-float shift (the wall time is
+            // that of one thread's chain): 0 at lo, NT-1 at hi, the rest inside
+            const double sg = tid == NT - 1 ? hi : lo + (hi - lo) * ((double)tid * (1.0 / (double)(NT - 1)));
             counts[tid] = count_lane<df32, P>(bdf, m, df32(sg), pivmindf);
         }
         __syncthreads();
-        verified = counts[0] <= i && counts[31] > i;
+        verified = counts[0] <= i && counts[NT - 1] > i;
         __syncthreads();
         if (verified) {
-            // the 30 inner samples: counts[1..30] at lo + (hi-lo) t/31
-            if (tid < 30) counts[tid] = counts[tid + 1];
+            // the inner samples: counts[1..NT-2] at lo + (hi-lo) t/(NT-1)
+            const int c = (tid < NT - 2) ? counts[tid + 1] : 0;
+            __syncthreads();
+            if (tid < NT - 2) counts[tid] = c;
             __syncthreads();
             double a = lo, b = hi;
-            if (update(30, a, b)) {
+            if (update(NT - 2, a, b)) {
                 lo = a;
                 hi = b;
             }
@@ -795,7 +799,7 @@ __global__ void __launch_bounds__(32) invit_kernel(int m, int p, const double* _
 // pivot row, every lane swaps rows 0 and bi of its column, the multipliers
 // are broadcast, every lane updates its column, writes row k of U, shifts
 // its rows up and takes its entry of the next row of T.  The factors live
-// in shared memory when they fit.  Then four steps of inverse iteration
+// in shared memory when they fit.  Then three steps of inverse iteration
 // with column-oriented triangular solves whose active rows live in
 // registers (forward: rows k..k+P, backward: rows k-2P..k); the vector is
 // normalised and its Rayleigh quotient formed in FP64.
@@ -934,7 +938,10 @@ __global__ void __launch_bounds__(32) invit_df_kernel(int m, const double* __res
         x[r] = df32((float)(z >> 40) * 0x1.0p-23f - 1.0f);
     }
     __syncwarp();
-    for (int it = 0; it < 4; ++it) {
+    // the shift is within 4e-8 * scale of the eigenvalue and eigenvalues closer
+    // than 1e-3 * scale form a cluster: each step shrinks the other components
+    // by 4e-5 or more, three reach working precision
+    for (int it = 0; it < 3; ++it) {
         // forward: row interchanges and L (row r in lane r mod (P+1))
         {
             df32 xv = (lane < P1 && lane < m) ? x[lane] : zero;
