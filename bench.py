@@ -551,7 +551,7 @@ def run_c3(args):
     import synth
     import paper_2210_15763_gb300 as bbl
     t0 = time.time()
-    A = synth.kron_matrix("kron_n2e7")
+    A = synth.kron_matrix("kron_n2e7", fp32_values=True)
     tgen = time.time() - t0
     out = {"mode": "c3", "n": int(A.n), "nnz": int(A.nnz), "nnz_per_row": A.nnz / A.n, "generate_s": tgen}
     st = torch.cuda.current_stream()
