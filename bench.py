@@ -218,7 +218,7 @@ def run_ours(args):
         b0 = torch.cuda.Event(enable_timing=True)
         b1 = torch.cuda.Event(enable_timing=True)
         b0.record(st)
-        P = bbl.pivot_bootstrap(M32, TRUNC, B, sub_tol=1e-10, seed=20221028)
+        P = bbl.pivot_bootstrap(M32, TRUNC, B, sub_tol=args.sub_tol, seed=20221028)
         b1.record(st)
         boot_ev.append((b0, b1))
         r = bbl.solve(M32, NEV, B, pivot=P, tol=TOL, evecs="device", max_vectors=2000, **solve_opts)
@@ -315,7 +315,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     h0 = time.perf_counter()
     Me = make_matrix()
-    Pe = bbl.pivot_bootstrap(Me, TRUNC, B, sub_tol=1e-10, seed=20221028)
+    Pe = bbl.pivot_bootstrap(Me, TRUNC, B, sub_tol=args.sub_tol, seed=20221028)
     re = bbl.solve(Me, NEV, B, pivot=Pe, tol=TOL, evecs="host", max_vectors=2000)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - h0
@@ -533,7 +533,8 @@ def run_learned(args):
            "mean_iters": {"learned": mean("learned_iters"), "bootstrap": mean("boot_iters"),
                           "random": mean("random_iters")},
            "mean_time_s": {"learned": mean("learned_s"), "bootstrap": mean("boot_s"), "random": mean("random_s")},
-           "learned_used_fraction": mean("learned_used"), "all_converged": all(r["converged"] for r in rows),
+           "learned_used_fraction": mean("learned_used"), "bootstrap_built_fraction": mean("bootstrap_built"),
+           "all_converged": all(r["converged"] for r in rows),
            "max_eval_diff_learned_vs_random": max(r["max_eval_diff"] for r in rows), "per_g": rows}
     print(json.dumps(res))
 
@@ -599,6 +600,7 @@ def main():
     ap.add_argument("--c3-vectors", type=int, default=300)
     ap.add_argument("--c3-fp64", action="store_true")
     ap.add_argument("--ritz-overlap", type=int, default=None)
+    ap.add_argument("--sub-tol", type=float, default=1e-10)
     ap.add_argument("--epochs", type=int, default=3000)
     ap.add_argument("--family-scale", type=float, default=1.0)
     ap.add_argument("--count", type=int, default=256)

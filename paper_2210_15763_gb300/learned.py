@@ -7,9 +7,10 @@ values are orthonormalised block by block (CGS2 + CholQR2 on the GPU) into
 the stored basis U (FP32, nbasis = n_basis_g * nev columns).  The network
 is trained to map g to the coefficients C(g) = U^T X(g) (FP64 Gram on the
 GPU).  At inference P = U f(g); Lanczos remains the judge: the learned pivot
-is used only if the Rayleigh-Ritz residual of its span is not worse than the
-bootstrapped pivot's, and a solve that does not converge is restarted from
-the bootstrapped pivot.
+is used only if the Rayleigh-Ritz residual of its span is below that of
+every bootstrapped pivot seen in training (else the bootstrapped pivot is
+built and the better of the two taken), and a solve that does not converge
+is restarted from the bootstrapped pivot.
 
 Every numerical step runs in libbbl.so; this module sequences the calls.
 """
@@ -42,6 +43,7 @@ class LearnedPivot:
     g_train: np.ndarray
     loss: np.ndarray
     train_iters: list
+    rr_boot_train: float = float("inf")  # smallest Rayleigh-Ritz residual of a training bootstrap pivot
 
     def pivot(self, g: float):
         return self.mlp.pivot(g, self.U, self.nev)
@@ -53,10 +55,12 @@ def fit(make_matrix, g_train, nev: int, b: int, trunc_dim: int, n_basis_g: int =
     """make_matrix(g) -> host CSR; solves H(g) for every training g."""
     import torch
     g_train = np.asarray(g_train, dtype=np.float64)
-    X, iters = [], []
+    X, iters, rr_boot = [], [], []
     for g in g_train:
         M = Matrix(make_matrix(g), storage=storage, fmt=fmt, sell_sigma=256 if fmt == "sell" else 0)
         P = pivot_bootstrap(M, trunc_dim, b, sub_tol=1e-10, seed=seed)
+        _, rb = pivot_rr_residual(M, P)
+        rr_boot.append(float(np.max(rb[:min(nev, rb.size)])))
         r = solve(M, nev, b, pivot=P, tol=tol)
         X.append(r.evecs)
         iters.append(r.stats["iters"] + r.stats["polish_iters"])
@@ -81,7 +85,7 @@ def fit(make_matrix, g_train, nev: int, b: int, trunc_dim: int, n_basis_g: int =
     net.set_params(init_params(hidden, out_dim, seed))
     gd = torch.tensor(g_train, dtype=torch.float32, device="cuda")
     loss = net.train(gd, T, epochs, lr)
-    return LearnedPivot(net, U, nev, g_train, loss, iters)
+    return LearnedPivot(net, U, nev, g_train, loss, iters, float(np.min(rr_boot)))
 
 
 def choose_pivot(A: Matrix, P_learned, P_boot, nev: int):
@@ -96,12 +100,26 @@ def choose_pivot(A: Matrix, P_learned, P_boot, nev: int):
 
 def solve_with_learned_pivot(A: Matrix, lp: LearnedPivot, g: float, b: int, trunc_dim: int, tol: float = 1e-8,
                              seed: int = 0):
+    """Lanczos judges the learned pivot.  When its Rayleigh-Ritz residual is
+    below every bootstrapped pivot's seen in training, it is used at once;
+    otherwise the bootstrapped pivot is built and the better of the two is
+    taken.  A solve from the learned pivot that does not converge is redone
+    from the bootstrapped pivot."""
     P_l = lp.pivot(g)
-    P_b = pivot_bootstrap(A, trunc_dim, b, sub_tol=1e-10, seed=seed)
-    P, used, rl, rb = choose_pivot(A, P_l, P_b, lp.nev)
+    _, rl_all = pivot_rr_residual(A, P_l)
+    rl = float(np.max(rl_all[:min(lp.nev, rl_all.size)]))
+    P_b = None
+    if rl < lp.rr_boot_train:
+        P, used, rb = P_l, True, None
+    else:
+        P_b = pivot_bootstrap(A, trunc_dim, b, sub_tol=1e-10, seed=seed)
+        P, used, rl, rb = choose_pivot(A, P_l, P_b, lp.nev)
     r = solve(A, lp.nev, b, pivot=P, tol=tol)
     fallback = False
     if not r.converged and used:
+        if P_b is None:
+            P_b = pivot_bootstrap(A, trunc_dim, b, sub_tol=1e-10, seed=seed)
         r = solve(A, lp.nev, b, pivot=P_b, tol=tol)
         fallback = True
-    return r, {"learned_used": used, "rr_learned": rl, "rr_boot": rb, "fallback": fallback}
+    return r, {"learned_used": used, "rr_learned": rl, "rr_boot": rb, "fallback": fallback,
+               "bootstrap_built": P_b is not None}
