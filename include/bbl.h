@@ -222,7 +222,9 @@ bbl_status bbl_cholqr2(int64_t n, int b, bbl_dtype dtype, void* W, double* B, do
  *   unit columns (sign: first largest-magnitude entry positive).
  * Method: Sylvester-inertia bisection (LDL^T of T - sigma I) then inverse
  * iteration (banded LU with partial pivoting) and Rayleigh quotients; the
- * vectors of clustered eigenvalues are orthonormalised together.
+ * vectors of clustered eigenvalues are orthonormalised together.  For
+ * p in {1, 2, 4, 8} the recurrences run in FP32 and float-float (~48-bit)
+ * arithmetic; normalisation and Rayleigh quotients are FP64.
  * 1 <= nev <= min(m, 32), p <= 16, m <= 16384.                                   */
 bbl_status bbl_ritz_banded(int m, int p, int nev, const double* Tband, double* theta, double* S,
                            void* stream);
