@@ -337,7 +337,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}: Kronecker H=Hp(x)I+I(x)Hn+sum_12 Cp(x)Cn, n={A.n}, nnz={A.nnz}, "
-                               f"b={B}, nev={NEV}, tol={TOL}, bootstrap trunc_dim={TRUNC}, FP32 stage "
+                               f"b={B}, nev={NEV}, tol={TOL}, bootstrap trunc_dim={TRUNC} sub_tol={args.sub_tol:g}, FP32 stage "
                                f"({sched['fmt']}, lanes {sched['lanes']}, sigma {sched['sigma']}) + float-float polish, "
                                f"FP64 residuals",
                    "parallelism": "replicas only" if world > 1 else "single GPU",
@@ -600,7 +600,7 @@ def main():
     ap.add_argument("--c3-vectors", type=int, default=300)
     ap.add_argument("--c3-fp64", action="store_true")
     ap.add_argument("--ritz-overlap", type=int, default=None)
-    ap.add_argument("--sub-tol", type=float, default=1e-10)
+    ap.add_argument("--sub-tol", type=float, default=1e-6)
     ap.add_argument("--epochs", type=int, default=3000)
     ap.add_argument("--family-scale", type=float, default=1.0)
     ap.add_argument("--count", type=int, default=256)

@@ -171,27 +171,36 @@ __global__ void __launch_bounds__(256) spmm_csr_generic(int64_t n, int b, const 
     }
 }
 
-// SELL-C-sigma, a warp per 32-row slice, one lane per row.
+// SELL-C-sigma: LPR = b*sizeof(TX)/16 lanes share a row (each loads 16
+// bytes of the gathered row of V, so one warp load covers whole rows and the
+// L1 serves one line per nonzero), a warp covers 32/LPR rows of a slice and
+// LPR warps cover the 32-row slice.  The index and value loads of a warp are
+// consecutive (lanes of a row read the same word).  Output row = perm[slot].
 template <typename TM, typename TX, int B>
 __global__ void __launch_bounds__(256) spmm_sell_kernel(int64_t nslices, const int64_t* __restrict__ sp,
                                                         const int* __restrict__ sc, const TM* __restrict__ sv,
                                                         const int* __restrict__ slen, const int* __restrict__ perm,
                                                         const TX* __restrict__ V, TX* __restrict__ W) {
-    constexpr int CH = (B * sizeof(TX) >= 16) ? 16 / (int)sizeof(TX) : B;  // values per vector load
-    constexpr int NCH = B / CH;
+    using L = VecLayout<TX, B>;
+    constexpr int LPR = L::LPN, VEC = L::VEC;
+    constexpr int RPP = 32 / LPR;  // rows per warp pass
+    static_assert(LPR >= 1 && LPR <= 32 && (32 % LPR) == 0, "sell lane groups");
     const int lane = threadIdx.x & 31;
-    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int64_t s = gw / LPR;
     if (s >= nslices) return;
-    const int64_t slot = s * kSellC + lane;
+    const int r = (int)(gw % LPR) * RPP + lane / LPR;  // row within the slice
+    const int part = lane % LPR;
+    const int64_t slot = s * kSellC + r;
     const int len = slen[slot];
-    const int64_t base = sp[s] + lane;
-    TX acc[B];
+    const int64_t base = sp[s] + r;
+    TX acc[VEC];
 #pragma unroll
-    for (int q = 0; q < B; ++q) acc[q] = TX(0);
+    for (int q = 0; q < VEC; ++q) acc[q] = TX(0);
     // Each nonzero is a dependent pair of loads (column index, then the
     // gathered row of V); batches of U nonzeros issue all index loads, then
     // all gathers, so that U gathers per lane are in flight at once.
-    constexpr int U = (B * sizeof(TX) <= 32) ? 8 : 4;
+    constexpr int U = 8;
     int k = 0;
     for (; k + U <= len; k += U) {
         int c[U];
@@ -201,46 +210,24 @@ __global__ void __launch_bounds__(256) spmm_sell_kernel(int64_t nslices, const i
             c[u] = __ldg(sc + base + (int64_t)(k + u) * kSellC);
             h[u] = (HType<TM, TX>)__ldg(sv + base + (int64_t)(k + u) * kSellC);
         }
-        TX v[U][B];
+        TX v[U][VEC];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const TX* vp = V + (int64_t)c[u] * B;
-#pragma unroll
-            for (int ch = 0; ch < NCH; ++ch) {
-                TX t[CH];
-                load_pack<TX, CH>(vp + ch * CH, t);
-#pragma unroll
-                for (int q = 0; q < CH; ++q) v[u][ch * CH + q] = t[q];
-            }
-        }
+        for (int u = 0; u < U; ++u) load_pack<TX, VEC>(V + (int64_t)c[u] * B + part * VEC, v[u]);
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int q = 0; q < B; ++q) acc[q] = fma(h[u], v[u][q], acc[q]);
+            for (int q = 0; q < VEC; ++q) acc[q] = fma(h[u], v[u][q], acc[q]);
     }
     for (; k < len; ++k) {
         const int c = __ldg(sc + base + (int64_t)k * kSellC);
         const HType<TM, TX> h = (HType<TM, TX>)__ldg(sv + base + (int64_t)k * kSellC);
-        const TX* vp = V + (int64_t)c * B;
+        TX v[VEC];
+        load_pack<TX, VEC>(V + (int64_t)c * B + part * VEC, v);
 #pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) {
-            TX v[CH];
-            load_pack<TX, CH>(vp + ch * CH, v);
-#pragma unroll
-            for (int q = 0; q < CH; ++q) acc[ch * CH + q] = fma(h, v[q], acc[ch * CH + q]);
-        }
+        for (int q = 0; q < VEC; ++q) acc[q] = fma(h, v[q], acc[q]);
     }
     const int row = perm[slot];
-    if (row >= 0) {
-        TX* wp = W + (int64_t)row * B;
-#pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) {
-            TX v[CH];
-#pragma unroll
-            for (int q = 0; q < CH; ++q) v[q] = acc[ch * CH + q];
-            store_pack<TX, CH>(wp + ch * CH, v);
-        }
-    }
+    if (row >= 0) store_pack<TX, VEC>(W + (int64_t)row * B + part * VEC, acc);
 }
 
 template <typename TM, typename TX>
@@ -319,12 +306,13 @@ bbl_status spmm_typed(const bbl_matrix* A, int b, const TM* csr_val, const TM* s
         auto sc = A->sell_col.as<int>();
         auto sl = A->sell_len.as<int>();
         auto pm = A->perm.as<int>();
+        auto sell_blocks = [&](int lpr) { return (unsigned)ceil_div(A->nslices * 32 * lpr, 256); };
         switch (pow2 ? b : 0) {
-            case 1: spmm_sell_kernel<TM, TX, 1><<<(unsigned)blocks, 256, 0, st>>>(A->nslices, sp, sc, sell_val, sl, pm, V, W); break;
-            case 2: spmm_sell_kernel<TM, TX, 2><<<(unsigned)blocks, 256, 0, st>>>(A->nslices, sp, sc, sell_val, sl, pm, V, W); break;
-            case 4: spmm_sell_kernel<TM, TX, 4><<<(unsigned)blocks, 256, 0, st>>>(A->nslices, sp, sc, sell_val, sl, pm, V, W); break;
-            case 8: spmm_sell_kernel<TM, TX, 8><<<(unsigned)blocks, 256, 0, st>>>(A->nslices, sp, sc, sell_val, sl, pm, V, W); break;
-            case 16: spmm_sell_kernel<TM, TX, 16><<<(unsigned)blocks, 256, 0, st>>>(A->nslices, sp, sc, sell_val, sl, pm, V, W); break;
+            case 1: spmm_sell_kernel<TM, TX, 1><<<sell_blocks(VecLayout<TX, 1>::LPN), 256, 0, st>>>(A->nslices, sp, sc, sell_val, sl, pm, V, W); break;
+            case 2: spmm_sell_kernel<TM, TX, 2><<<sell_blocks(VecLayout<TX, 2>::LPN), 256, 0, st>>>(A->nslices, sp, sc, sell_val, sl, pm, V, W); break;
+            case 4: spmm_sell_kernel<TM, TX, 4><<<sell_blocks(VecLayout<TX, 4>::LPN), 256, 0, st>>>(A->nslices, sp, sc, sell_val, sl, pm, V, W); break;
+            case 8: spmm_sell_kernel<TM, TX, 8><<<sell_blocks(VecLayout<TX, 8>::LPN), 256, 0, st>>>(A->nslices, sp, sc, sell_val, sl, pm, V, W); break;
+            case 16: spmm_sell_kernel<TM, TX, 16><<<sell_blocks(VecLayout<TX, 16>::LPN), 256, 0, st>>>(A->nslices, sp, sc, sell_val, sl, pm, V, W); break;
             default:
                 spmm_sell_generic<TM, TX><<<(unsigned)blocks, 256, 0, st>>>(A->nslices, b, sp, sc, sell_val, sl, pm, V, W);
         }
