@@ -55,6 +55,18 @@ def test_spmm_csr_lane_groups(lanes):
         assert np.all(np.abs(W - ref) <= 64 * EPS64 * abs_bound(A, V) + 1e-300)
 
 
+@pytest.mark.parametrize("b", [1, 2, 8, 16])
+def test_spmm_sell_fp64_storage(b):
+    """FP64 values in SELL-C-sigma: 16-byte loads, b*8/16 lanes per row (up
+    to 8 for b = 16), against the oracle's product."""
+    torch, bbl = need_gpu()
+    A = _mat("ragged")
+    M = bbl.Matrix(A, storage="fp64", fmt="sell", sell_sigma=64)
+    V = np.random.default_rng(30 + b).standard_normal((A.n, b))
+    W = bbl.spmm(M, to_dev(torch, V)).cpu().numpy()
+    assert np.all(np.abs(W - ospmm(A, V)) <= 64 * EPS64 * abs_bound(A, V))
+
+
 @pytest.mark.parametrize("fmt,sigma", [("csr", 0), ("sell", 32), ("sell", 256), ("sell", 1024)])
 @pytest.mark.parametrize("b", [1, 4, 5, 8, 16])
 def test_spmm_fp32_csr_and_sell(fmt, sigma, b):

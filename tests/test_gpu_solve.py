@@ -84,6 +84,22 @@ def test_solve_random_pivot_null_uses_the_published_generator():
     assert abs(res.stats["iters"] - ref.iters) <= 1
 
 
+def test_ritz_solve_in_line_matches_the_side_stream():
+    """ritz_overlap = 0 runs each Ritz solve on the caller's stream before the
+    next block; it reports the same block, eigenvalues and vectors."""
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4", scale=0.5)
+    piv = OR.normal_block(12, H.n, 4)
+    M = bbl.Matrix(H)
+    r1 = bbl.solve(M, 4, 4, pivot=piv, tol=1e-9, check_every=1, ritz_overlap=1)
+    r0 = bbl.solve(M, 4, 4, pivot=piv, tol=1e-9, check_every=1, ritz_overlap=0)
+    assert r0.converged and r1.converged
+    assert r0.stats["iters"] == r1.stats["iters"]
+    np.testing.assert_allclose(r0.evals, r1.evals, rtol=1e-13)
+    X0, X1 = r0.evecs.cpu().numpy(), r1.evecs.cpu().numpy()
+    assert np.abs(X0 - X1).max() < 1e-10
+
+
 def test_solve_laplacian_1d_closed_form_b1():
     torch, bbl = need_gpu()
     n = 300
