@@ -198,21 +198,38 @@ __global__ void __launch_bounds__(256) spmm_sell_kernel(int64_t nslices, const i
 #pragma unroll
     for (int q = 0; q < VEC; ++q) acc[q] = TX(0);
     // Each nonzero is a dependent pair of loads (column index, then the
-    // gathered row of V); batches of U nonzeros issue all index loads, then
-    // all gathers, so that U gathers per lane are in flight at once.
+    // gathered row of V).  Batches of U nonzeros: the gathers of a batch are
+    // issued together, and the index/value loads of the next batch are issued
+    // before this batch's products, so the two latencies overlap.
     constexpr int U = 8;
     int k = 0;
+    int cn[U];
+    HType<TM, TX> hn[U];
+    if (U <= len) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cn[u] = __ldg(sc + base + (int64_t)u * kSellC);
+            hn[u] = (HType<TM, TX>)__ldg(sv + base + (int64_t)u * kSellC);
+        }
+    }
     for (; k + U <= len; k += U) {
         int c[U];
         HType<TM, TX> h[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            c[u] = __ldg(sc + base + (int64_t)(k + u) * kSellC);
-            h[u] = (HType<TM, TX>)__ldg(sv + base + (int64_t)(k + u) * kSellC);
+            c[u] = cn[u];
+            h[u] = hn[u];
         }
         TX v[U][VEC];
 #pragma unroll
         for (int u = 0; u < U; ++u) load_pack<TX, VEC>(V + (int64_t)c[u] * B + part * VEC, v[u]);
+        if (k + 2 * U <= len) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                cn[u] = __ldg(sc + base + (int64_t)(k + U + u) * kSellC);
+                hn[u] = (HType<TM, TX>)__ldg(sv + base + (int64_t)(k + U + u) * kSellC);
+            }
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
