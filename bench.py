@@ -179,6 +179,17 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def max_over_ranks(x: float, world: int, device: str) -> float:
+    """The largest of the ranks' values (one collective); x itself at N = 1."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -242,13 +253,11 @@ def run_ours(args):
     results = [step() for _ in range(args.steps)]
     e1.record(st)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     launches = lib.bbl_kernel_launches() - launches0
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / max(args.steps, 1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / max(args.steps, 1), world, "cuda")
     r = results[-1]
     ok = all(x.converged for x in results)
     nrm = M32.norm_inf
