@@ -609,7 +609,7 @@ def main():
     ap.add_argument("--c3-vectors", type=int, default=300)
     ap.add_argument("--c3-fp64", action="store_true")
     ap.add_argument("--ritz-overlap", type=int, default=None)
-    ap.add_argument("--sub-tol", type=float, default=1e-6)
+    ap.add_argument("--sub-tol", type=float, default=1e-4)
     ap.add_argument("--epochs", type=int, default=3000)
     ap.add_argument("--family-scale", type=float, default=1.0)
     ap.add_argument("--count", type=int, default=256)

@@ -5,6 +5,7 @@
 //   S1  W = H V_j                                   (spmm.cu)
 //   S2  C1 = Q^T W, W -= Q C1;  A_j = sym(C1[j]);    (block.cu; Q = [V_0..V_j])
 //       C2 = Q^T W, W -= Q C2                       (second Gram-Schmidt pass)
+//       (float-float blocks: C1 from FP32 copies of Q and W, A_j = sym(C1[j] + C2[j]))
 //   S3  V_{j+1} R2 R1 = W (CholQR2), B_j = R2 R1     (block.cu)
 //   S4  T_j (Eq. 12) -> theta, S; estimates ||B_j S[last b, i]||   (ritz.cu)
 // then X = Q S and the FP64 residuals ||H x_i - theta_i x_i||.
@@ -49,6 +50,26 @@ __global__ void fill_A_kernel(int j, int b, const double* __restrict__ C1, doubl
     const int jb = j * b;
     const double v = 0.5 * (C1[(int64_t)(jb + r) * b + c] + C1[(int64_t)(jb + c) * b + r]);
     Tb[(int64_t)(jb + r) * (b + 1) + (r - c)] = v;
+}
+
+// A_j = sym(C1[j-block] + C2[j-block]): both Gram-Schmidt passes' own-block
+// coefficients (used when the first pass is computed from FP32 copies)
+__global__ void fill_A2_kernel(int j, int b, const double* __restrict__ C1, const double* __restrict__ C2,
+                               double* __restrict__ Tb) {
+    const int e = threadIdx.x;
+    if (e >= b * b) return;
+    const int r = e / b, c = e % b;
+    if (c > r) return;
+    const int jb = j * b;
+    const int64_t rc = (int64_t)(jb + r) * b + c, cr = (int64_t)(jb + c) * b + r;
+    const double v = 0.5 * ((C1[rc] + C2[rc]) + (C1[cr] + C2[cr]));
+    Tb[(int64_t)(jb + r) * (b + 1) + (r - c)] = v;
+}
+
+// the high FP32 parts of float-float values
+__global__ void df32_hi_kernel(int64_t count, const df32* __restrict__ in, float* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = in[e].hi;
 }
 
 // B_j (upper triangular) into block (j+1, j) of T
@@ -291,7 +312,8 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     {
         size_t freeb = 0, totalb = 0;
         BBL_CUDA(cudaMemGetInfo(&freeb, &totalb));
-        const size_t per_block = (size_t)n * b * s;
+        // float-float blocks also keep an FP32 copy (first Gram-Schmidt pass)
+        const size_t per_block = (size_t)n * b * (s + (dtype == kDF32 ? sizeof(float) : 0));
         const size_t reserve = (size_t)(2ull << 30) + 8 * (size_t)n * b * 8;
         if (freeb > reserve) {
             const int fit = (int)std::min<size_t>((freeb - reserve) / per_block, (size_t)1 << 30);
@@ -301,7 +323,16 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     const int m_max = J_max * b;
     if (nev > m_max) return set_error(BBL_ERR_INVALID_ARG, "solve: nev=%d exceeds the basis capacity %d", nev, m_max);
     DevBuf basis, Z, coeff, partials, small, Tb, S, rwork, flags, bj;
+    // float-float blocks: FP32 copies of the basis (high parts) and of W for
+    // the first Gram-Schmidt pass, whose coefficients only need to remove the
+    // bulk (the second pass, in float-float, takes out the rest; A_j then
+    // sums both passes' own-block coefficients)
+    DevBuf shadow, whi;
     BBL_TRY(basis.alloc((size_t)J_max * n * b * s));
+    if (dtype == kDF32) {
+        BBL_TRY(shadow.alloc((size_t)J_max * n * b * sizeof(float)));
+        BBL_TRY(whi.alloc((size_t)n * b * sizeof(float)));
+    }
     BBL_TRY(Z.alloc((size_t)n * b * s));
     BBL_TRY(coeff.alloc(sizeof(double) * 2 * (size_t)m_max * b));
     const int t_rows = m_max + b;
@@ -373,6 +404,14 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     BBL_CUDA(cudaMemcpyAsync(h_ndefl, d_ndefl + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     BBL_CUDA(cudaStreamSynchronize(st));
     if (h_ndefl[0] > 0) BBL_TRY(replace_deflated(0, blockp(0), d_mask));
+    auto shadow_block = [&](int jb) -> bbl_status {
+        if (dtype != kDF32 || jb >= J_max) return BBL_OK;
+        df32_hi_kernel<<<cg, 256, 0, st>>>(n * b, reinterpret_cast<const df32*>(blockp(jb)),
+                                           shadow.as<float>() + (size_t)jb * n * b);
+        BBL_LAUNCH_CHECK();
+        return BBL_OK;
+    };
+    BBL_TRY(shadow_block(0));
 
     // The Ritz solve of T_j runs on a side stream while the main stream goes
     // on with block j+1 (whose SpMM does not need it); the host checks the
@@ -489,13 +528,25 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         double* C1 = coeff.as<double>();
         double* C2 = C1 + (size_t)m_max * b;
         BBL_CUDA(cudaEventRecord(tm.ev[4], st));
-        BBL_TRY(gram(n, b, j + 1, dtype, basis.p, Wn, C1, partials, st));
+        if (dtype == kDF32) {
+            df32_hi_kernel<<<cg, 256, 0, st>>>(n * b, reinterpret_cast<const df32*>(Wn), whi.as<float>());
+            BBL_LAUNCH_CHECK();
+            BBL_TRY(gram(n, b, j + 1, BBL_FP32, shadow.p, whi.p, C1, partials, st));
+        } else {
+            BBL_TRY(gram(n, b, j + 1, dtype, basis.p, Wn, C1, partials, st));
+        }
         BBL_CUDA(cudaEventRecord(tm.ev[5], st));
         BBL_TRY(update(n, b, j + 1, dtype, basis.p, C1, Wn, st));
-        fill_A_kernel<<<1, 256, 0, st>>>(j, b, C1, Tb.as<double>());
-        BBL_LAUNCH_CHECK();
+        if (dtype != kDF32) {
+            fill_A_kernel<<<1, 256, 0, st>>>(j, b, C1, Tb.as<double>());
+            BBL_LAUNCH_CHECK();
+        }
         BBL_TRY(gram(n, b, j + 1, dtype, basis.p, Wn, C2, partials, st));
         BBL_TRY(update(n, b, j + 1, dtype, basis.p, C2, Wn, st));
+        if (dtype == kDF32) {
+            fill_A2_kernel<<<1, 256, 0, st>>>(j, b, C1, C2, Tb.as<double>());
+            BBL_LAUNCH_CHECK();
+        }
         BBL_CUDA(cudaEventRecord(tm.ev[2], st));
         BBL_TRY(cholqr2_dev(n, b, dtype, Wn, bj.as<double>(), thresh2, d_ndefl, d_mask, partials, small, st));
         fill_B_kernel<<<1, 256, 0, st>>>(j, b, t_rows, bj.as<double>(), Tb.as<double>());
@@ -542,6 +593,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             last_defl = h_ndefl[0];
             if (exhausted) break;  // no direction left to extend the basis with
         }
+        BBL_TRY(shadow_block(j + 1));
     }
     if (pending >= 0 && !stop) {
         bool done = false;
