@@ -42,6 +42,9 @@ TRUNC = 20000
 # of the same family (dram__bytes_read.sum + dram__bytes_write.sum =
 # 1.185 GB for 139,708,000 nonzeros); traffic grows with the nonzeros.
 SPMM_TRAFFIC_PER_NNZ = 1.185e9 / 139_708_000
+# the same for the FP32 SELL-C-sigma SpMM (b = 8; sigma = 256 in the capture):
+# 1.248 GB for 139,708,000 nonzeros
+SELL_TRAFFIC_PER_NNZ = 1.248e9 / 139_708_000
 SELL_SIGMA = 256
 METRIC = "time-to-solve lowest 8 eigenpairs @resid 1e-8 (s)"
 
@@ -286,8 +289,8 @@ def run_ours(args):
                  else "spmm_sell_kernel<float,float,8>", "launches": spmm_calls,
                  "total_ms": spmm_total_ms, "achieved": spmm_kernel_gbs,
                  "bytes_per_launch": stats_log[-1]["spmm_bytes"],
-                 "traffic": SPMM_TRAFFIC_PER_NNZ * A.nnz if sched["fmt"] == "csr" and (sched["lanes"] or 32) == 32
-                 else None},
+                 "traffic": (SPMM_TRAFFIC_PER_NNZ * A.nnz if sched["fmt"] == "csr" and (sched["lanes"] or 32) == 32
+                             else SELL_TRAFFIC_PER_NNZ * A.nnz if sched["fmt"] == "sell" else None)},
         "gram": {"kernel": "gram_rows_kernel<float,8> + reduce_partials_kernel (first pass; the second pass "
                  "is the same kernel)", "launches": 2 * gram_calls, "total_ms": 2 * tot["t_gram_ms"],
                  "achieved": gram_gbs, "bytes_per_launch": tot["gram_bytes_total"] / max(gram_calls, 1),
