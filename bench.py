@@ -463,28 +463,31 @@ def run_batched(args):
     e1.record()
     torch.cuda.synchronize()
     t_batch = e0.elapsed_time(e1) / 1e3
-    # one launch sequence per matrix
-    Ms = [bbl.Matrix(m, storage="fp32", fmt=best["fmt"], sell_sigma=best["sigma"]) for m in mats]
-    torch.cuda.synchronize()
-    e0.record()
+    # one launch sequence per matrix (skipped with --skip-plain)
     its1 = []
     conv1 = 0
-    for M in Ms:
-        r = bbl.solve(M, 4, 4, pivot=None, tol=1e-7, polish=0, max_vectors=args.batch_max_vectors, seed=20221034,
-                      evecs=None)
-        its1.append(r.stats["iters"])
-        conv1 += r.converged
-    e1.record()
-    torch.cuda.synchronize()
-    t_single = e0.elapsed_time(e1) / 1e3
+    t_single = float("nan")
+    if not args.skip_plain:
+        Ms = [bbl.Matrix(m, storage="fp32", fmt=best["fmt"], sell_sigma=best["sigma"]) for m in mats]
+        torch.cuda.synchronize()
+        e0.record()
+        for M in Ms:
+            r = bbl.solve(M, 4, 4, pivot=None, tol=1e-7, polish=0, max_vectors=args.batch_max_vectors,
+                          seed=20221034, evecs=None)
+            its1.append(r.stats["iters"])
+            conv1 += r.converged
+        e1.record()
+        torch.cuda.synchronize()
+        t_single = e0.elapsed_time(e1) / 1e3
     nrm = np.array([float(np.abs(m.to_scipy()).sum(axis=1).max()) for m in mats])
     out = {"metric": "batched solves/s (256 Kronecker matrices, n in [2e3, 2e5], b=4, nev=4, tol 1e-7)",
            "value": args.count / t_batch, "unit": "solves/s", "higher_is_better": True,
-           "batched_s": t_batch, "one_launch_per_matrix_s": t_single,
-           "one_launch_per_matrix_solves_per_s": args.count / t_single, "speedup": t_single / t_batch,
+           "batched_s": t_batch, "one_launch_per_matrix_s": t_single if its1 else None,
+           "one_launch_per_matrix_solves_per_s": args.count / t_single if its1 else None,
+           "speedup": t_single / t_batch if its1 else None,
            "converged": int(np.sum(st == 0)), "converged_single": conv1, "count": args.count,
            "n_total": int(offsets[-1]), "nnz_total": int(rp[-1]),
-           "iters_max": int(it.max()), "iters_mean": float(it.mean()), "iters_single_mean": float(np.mean(its1)),
+           "iters_max": int(it.max()), "iters_mean": float(it.mean()), "iters_single_mean": float(np.mean(its1)) if its1 else None,
            "max_resid_rel": float(np.max(rs.max(axis=1) / nrm)),
            "schedule": {k: best[k] for k in ("fmt", "lanes", "sigma", "ms", "class")},
            "graph_kernels_per_iteration": stats["polish_iters"], "generate_s": tgen}
