@@ -454,12 +454,13 @@ def run_batched(args):
     if best["fmt"] == "csr":
         Bt.set_schedule(best["lanes"])
     opts = dict(tol=1e-7, max_vectors=args.batch_max_vectors, seed=20221034)
-    Bt.solve(4, 4, use_graph=True, **opts)  # warm-up (graph build, caches)
+    graph = bool(args.batch_graph)
+    Bt.solve(4, 4, use_graph=graph, **opts)  # warm-up (graph build, caches)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    ev, rs, it, st, stats = Bt.solve(4, 4, use_graph=True, **opts)
+    ev, rs, it, st, stats = Bt.solve(4, 4, use_graph=graph, **opts)
     e1.record()
     torch.cuda.synchronize()
     t_batch = e0.elapsed_time(e1) / 1e3
@@ -490,7 +491,7 @@ def run_batched(args):
            "iters_max": int(it.max()), "iters_mean": float(it.mean()), "iters_single_mean": float(np.mean(its1)) if its1 else None,
            "max_resid_rel": float(np.max(rs.max(axis=1) / nrm)),
            "schedule": {k: best[k] for k in ("fmt", "lanes", "sigma", "ms", "class")},
-           "graph_kernels_per_iteration": stats["polish_iters"], "generate_s": tgen}
+           "graph_kernels_per_iteration": stats["polish_iters"], "graph": graph, "generate_s": tgen}
     print(json.dumps(out))
 
 
@@ -620,6 +621,7 @@ def main():
     ap.add_argument("--family-scale", type=float, default=1.0)
     ap.add_argument("--count", type=int, default=256)
     ap.add_argument("--batch-max-vectors", type=int, default=400)
+    ap.add_argument("--batch-graph", type=int, default=1, help="batched mode: 1 = one graph launch, 0 = host-driven")
     ap.add_argument("--scale", type=float, default=0.5)
     ap.add_argument("--blocks", type=int, default=50)
     ap.add_argument("--reps", type=int, default=5)

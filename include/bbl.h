@@ -308,8 +308,9 @@ bbl_status bbl_batch_set_schedule(bbl_batch* B, int lanes_per_row);
  * kernel sequence over all problems; with use_graph = 1 it is captured as the
  * body of a CUDA graph while-node and the whole solve is one graph launch,
  * with use_graph = 0 the host drives the same sequence.  Each problem stops
- * when its nev estimates ||B_j s_i[last b]|| are <= tol*||H_s||_inf; random
- * pivots (opt->seed).  Outputs (host): evals, resid [count x nev] (true FP64
+ * when its nev estimates ||B_j s_i[last b]|| are <= tol*||H_s||_inf, tested
+ * on opt->check_every's schedule (0: adaptive, per problem, as in
+ * bbl_solve); random pivots (opt->seed).  Outputs (host): evals, resid [count x nev] (true FP64
  * residuals), iters [count], status [count] (BBL_OK, BBL_ERR_NOT_CONVERGED,
  * BBL_ERR_NUMERICAL for a breakdown).  b in {1, 2, 4, 8, 16}, nev <= 16.
  * Returns BBL_OK when every problem converged.                           */

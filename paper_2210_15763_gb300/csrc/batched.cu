@@ -10,7 +10,9 @@
 // "while" node whose condition a control kernel sets from the number of
 // segments still running.  The whole batched solve is then a single
 // cudaGraphLaunch: no host round trip per iteration.  Segments that converge
-// are switched off (their Gram-Schmidt, CholQR2 and Ritz work is skipped).
+// are switched off (their Gram-Schmidt, CholQR2 and Ritz work is skipped);
+// each segment runs its Ritz solve and test only on the blocks its own
+// adaptive schedule picks.
 //
 // Storage: FP32 or FP64 blocks as the matrix; coefficients, Gram matrices,
 // T and the final residuals in FP64 (no polish stage: each segment stops at
@@ -32,6 +34,7 @@ bbl_status chol_seg(int b, int nseg, const double* G, const double* thresh2, int
                     int* ndefl, int* mask, int* status, const int* active, cudaStream_t st);
 bbl_status trmul_seg(int b, int nseg, const double* R2, const double* R1, double* B, const int* active, cudaStream_t st);
 size_t ritz_seg_workspace_doubles(int m_max, int p, int nev);
+int gram_seg_chunk_rows(int b, int dtype);
 bbl_status ritz_dev_batched(int m_max, int p, int nev, int nseg, const double* Tb, int64_t sT, double* theta,
                             int64_t sTh, double* width, double* S, int64_t sS, double* ws, double* tmp, const int* d_m,
                             const int* active, cudaStream_t st);
@@ -125,20 +128,39 @@ __global__ void fill_AB_seg_kernel(int b, int m_max, int rows_alloc, const int* 
     }
 }
 
-// per segment: estimates, convergence / deflation decisions
+// which segments test convergence at block j: with every > 0 each every-th
+// block, else (adaptive) from block next_chk[s] on; always on a breakdown
+// and at the last block
+__global__ void due_seg_kernel(int nseg, int J_max, int every, const int* __restrict__ d_j,
+                               const int* __restrict__ active, const int* __restrict__ ndefl,
+                               const int* __restrict__ next_chk, int* __restrict__ due) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    const int j = *d_j;
+    const bool sched = every > 0 ? ((j + 1) % every == 0) : (j >= next_chk[s]);
+    due[s] = (active[s] && (sched || ndefl[s] > 0 || j + 1 >= J_max)) ? 1 : 0;
+}
+
+// per due segment: estimates, convergence / deflation decisions, and the
+// next test block: rho = max_i est_i / (tol ||H_s||) and its decay per block
+// since the previous test predict the blocks left; the next test is at half
+// that distance, 1 to 8 blocks ahead (one block until two tests exist)
 __global__ void converge_seg_kernel(int b, int nev, int nseg, int m_max, int rows_alloc, int J_max,
                                     const int* __restrict__ d_j, const double* __restrict__ Tb,
                                     const double* __restrict__ S, const double* __restrict__ norm, double tol,
-                                    const int* __restrict__ ndefl, int* __restrict__ active, int* __restrict__ final_j,
-                                    int* __restrict__ status, double* __restrict__ est_out) {
+                                    const int* __restrict__ ndefl, const int* __restrict__ due,
+                                    int* __restrict__ active, int* __restrict__ final_j, int* __restrict__ status,
+                                    double* __restrict__ est_out, int* __restrict__ next_chk, int* __restrict__ jprev,
+                                    double* __restrict__ lprev) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nseg || !active[s]) return;
+    if (s >= nseg || !due[s]) return;
     const int j = *d_j;
     const int m = (j + 1) * b;
     const int k = min(nev, m);
     const double* T = Tb + (int64_t)s * rows_alloc * (b + 1);
     const double* Ss = S + (int64_t)s * m_max * nev;
     bool done = (k == nev);
+    double rho = 0.0;
     for (int i = 0; i < k; ++i) {
         double s2 = 0.0;
         for (int r = 0; r < b; ++r) {
@@ -149,6 +171,7 @@ __global__ void converge_seg_kernel(int b, int nev, int nseg, int m_max, int row
         const double e = sqrt(s2);
         est_out[(int64_t)s * nev + i] = e;
         done = done && (e <= tol * norm[s]);
+        rho = fmax(rho, e / (tol * norm[s]));
     }
     final_j[s] = j;
     if (done) {
@@ -160,6 +183,15 @@ __global__ void converge_seg_kernel(int b, int nev, int nseg, int m_max, int row
     } else if (j + 1 >= J_max) {
         status[s] = BBL_ERR_NOT_CONVERGED;
     }
+    const double l = log(fmax(rho, 1e-300));
+    int step = 1;
+    if (jprev[s] >= 0 && j > jprev[s] && l < lprev[s] && l > 0.0) {
+        const double blocks = l / ((lprev[s] - l) / (double)(j - jprev[s]));
+        step = (int)fmin(8.0, fmax(1.0, floor(0.5 * blocks)));
+    }
+    jprev[s] = j;
+    lprev[s] = l;
+    next_chk[s] = j + step;
 }
 
 // advances the iteration and sets the while-node condition
@@ -319,7 +351,9 @@ bbl_status bbl_batch_solve(bbl_batch* Bt, int nev, int b, const bbl_options* opt
         }
     } sg{cap};
     // ---- work tables (host) ----
-    const int64_t rpc = std::max<int64_t>(256, ((n / 600) + 63) / 64 * 64);
+    // Gram chunks: the row-contiguous kernel's tile (R rows) where it exists
+    const int rows_tile = gram_seg_chunk_rows(b, dtype);
+    const int64_t rpc = rows_tile > 0 ? (int64_t)rows_tile : std::max<int64_t>(256, ((n / 600) + 63) / 64 * 64);
     std::vector<int64_t> chunks, ctas;
     std::vector<int> chunk_ptr(nseg + 1, 0);
     for (int s = 0; s < nseg; ++s) {
@@ -339,7 +373,7 @@ bbl_status bbl_batch_solve(bbl_batch* Bt, int nev, int b, const bbl_options* opt
     const int nchunks = (int)(chunks.size() / 3), nctas = (int)(ctas.size() / 3);
     // ---- device buffers ----
     DevBuf d_chunks, d_ctas, d_chunk_ptr, basis, Vfix, Wfix, C1, C2, G, R1, R1i, R2, R2i, Bj, partial, Tb, theta, width,
-        S, est, ws, tmp, ints, thr, X, Y, rpart, piv;
+        S, est, ws, tmp, ints, thr, X, Y, rpart, piv, lprev;
     BBL_TRY(d_chunks.alloc(sizeof(int64_t) * chunks.size()));
     BBL_TRY(d_ctas.alloc(sizeof(int64_t) * ctas.size()));
     BBL_TRY(d_chunk_ptr.alloc(sizeof(int) * (nseg + 1)));
@@ -355,7 +389,8 @@ bbl_status bbl_batch_solve(bbl_batch* Bt, int nev, int b, const bbl_options* opt
     BBL_TRY(R2.alloc(bb));
     BBL_TRY(R2i.alloc(bb));
     BBL_TRY(Bj.alloc(bb));
-    BBL_TRY(partial.alloc(sizeof(double) * (size_t)nchunks * m_max * b));
+    // per chunk: up to 8 slots of m x b when m < 8b (row shares), else one
+    BBL_TRY(partial.alloc(sizeof(double) * (size_t)nchunks * std::max(m_max, 8 * b) * b));
     BBL_TRY(Tb.alloc(sizeof(double) * (size_t)nseg * rows_alloc * (b + 1)));
     BBL_TRY(theta.alloc(sizeof(double) * (size_t)nseg * nev));
     BBL_TRY(width.alloc(sizeof(double) * (size_t)nseg * nev));
@@ -363,8 +398,10 @@ bbl_status bbl_batch_solve(bbl_batch* Bt, int nev, int b, const bbl_options* opt
     BBL_TRY(est.alloc(sizeof(double) * (size_t)nseg * nev));
     BBL_TRY(ws.alloc(sizeof(double) * (size_t)nseg * ritz_seg_workspace_doubles(m_max, b, nev)));
     BBL_TRY(tmp.alloc(sizeof(double) * (size_t)nseg * m_max * nev));
-    // ints: d_j, d_m, d_b, iters, then per segment: active, final_j, status, ndefl, mask[b], ms
-    BBL_TRY(ints.alloc(sizeof(int) * (8 + (size_t)nseg * (5 + b))));
+    // ints: d_j, d_m, d_b, iters, then per segment: active, final_j, status, ndefl, mask[b], ms, due, next_chk,
+    // jprev
+    BBL_TRY(ints.alloc(sizeof(int) * (8 + (size_t)nseg * (8 + b))));
+    BBL_TRY(lprev.alloc(sizeof(double) * nseg));
     BBL_TRY(thr.alloc(sizeof(double) * nseg * 2));
     int* d_j = ints.as<int>();
     int* d_m = d_j + 1;
@@ -376,18 +413,22 @@ bbl_status bbl_batch_solve(bbl_batch* Bt, int nev, int b, const bbl_options* opt
     int* ndefl = seg_status + nseg;
     int* mask = ndefl + nseg;
     int* ms = mask + (size_t)nseg * b;
+    int* due = ms + nseg;
+    int* next_chk = due + nseg;
+    int* jprev = next_chk + nseg;
     BBL_CUDA(cudaMemcpyAsync(d_chunks.p, chunks.data(), sizeof(int64_t) * chunks.size(), cudaMemcpyHostToDevice, st));
     BBL_CUDA(cudaMemcpyAsync(d_ctas.p, ctas.data(), sizeof(int64_t) * ctas.size(), cudaMemcpyHostToDevice, st));
     BBL_CUDA(cudaMemcpyAsync(d_chunk_ptr.p, chunk_ptr.data(), sizeof(int) * (nseg + 1), cudaMemcpyHostToDevice, st));
     BBL_CUDA(cudaMemsetAsync(Tb.p, 0, Tb.bytes, st));
     BBL_CUDA(cudaMemsetAsync(ints.p, 0, ints.bytes, st));
     {
-        std::vector<int> h(8 + (size_t)nseg * (5 + b), 0);
+        std::vector<int> h(8 + (size_t)nseg * (8 + b), 0);
         h[0] = 0;
         h[1] = b;
         h[2] = b;
         for (int s = 0; s < nseg; ++s) h[8 + s] = 1;  // active
         for (int s = 0; s < nseg; ++s) h[8 + 2 * nseg + s] = BBL_ERR_NOT_CONVERGED;
+        for (int s = 0; s < nseg; ++s) h[8 + (size_t)nseg * (7 + b) + s] = -1;  // jprev: no test yet
         BBL_CUDA(cudaMemcpyAsync(ints.p, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice, st));
         const double dt = o.defl_tol > 0 ? o.defl_tol : (dtype == BBL_FP64 ? 1e-10 : 1e-6);
         std::vector<double> th(2 * nseg);
@@ -475,12 +516,15 @@ bbl_status bbl_batch_solve(bbl_batch* Bt, int nev, int b, const bbl_options* opt
             copy_slot_kernel<float><<<cg, 256, 0, st>>>(n * b, d_j, 1, Wfix.as<float>(), basis.as<float>(),
                                                         Vfix.as<float>());
         BBL_LAUNCH_CHECK();
+        due_seg_kernel<<<(unsigned)ceil_div(nseg, 256), 256, 0, st>>>(nseg, J_max, std::max(0, o.check_every), d_j,
+                                                                       active, ndefl, next_chk, due);
+        BBL_LAUNCH_CHECK();
         BBL_TRY(ritz_dev_batched(m_max, b, nev, nseg, Tb.as<double>(), (int64_t)rows_alloc * (b + 1), theta.as<double>(),
                                  nev, width.as<double>(), S.as<double>(), (int64_t)m_max * nev, ws.as<double>(),
-                                 tmp.as<double>(), d_m, active, st));
+                                 tmp.as<double>(), d_m, due, st));
         converge_seg_kernel<<<(unsigned)ceil_div(nseg, 64), 64, 0, st>>>(
             b, nev, nseg, m_max, rows_alloc, J_max, d_j, Tb.as<double>(), S.as<double>(), Bt->d_norm.as<double>(), o.tol,
-            ndefl, active, final_j, seg_status, est.as<double>());
+            ndefl, due, active, final_j, seg_status, est.as<double>(), next_chk, jprev, lprev.as<double>());
         BBL_LAUNCH_CHECK();
         control_kernel<<<1, 32, 0, st>>>(nseg, b, J_max, d_j, d_m, active, handle, use_graph ? 1 : 0, d_iters);
         BBL_LAUNCH_CHECK();

@@ -274,30 +274,36 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// warps per basis block when a chunk has fewer blocks than warps
+__host__ __device__ __forceinline__ int gram_rows_wpb(int nblocks) {
+    int wpb = 1;
+    while (wpb < kThreads / 32 && nblocks * wpb * 2 <= kThreads / 32) wpb <<= 1;
+    return wpb;
+}
+
+// One chunk, rows [r0, r0 + rows) with rows <= R, for all threads of the
+// CTA: W's rows staged in shared memory (ws), then each warp streams the
+// chunk's rows of its blocks (share sub: rows [sub * rsub, (sub + 1) * rsub))
+// through its ring and adds its B x B partials to slot sub of `slots`
+// (wpb slots of m x B FP64).  The barrier after the W tile also orders any
+// plain stores the caller made to `slots` before the adds.
 template <typename T, int B>
-__global__ void __launch_bounds__(kThreads) gram_rows_kernel(int64_t n, int m, int wpb, int rc, int nchunks,
-                                                             const T* __restrict__ Q, const T* __restrict__ W,
-                                                             double* __restrict__ partial, int* __restrict__ ticket) {
+__device__ __forceinline__ void gram_rows_chunk(int64_t n, int m, int wpb, int64_t r0, int rows, int rsub,
+                                                const T* __restrict__ Q, const T* __restrict__ W,
+                                                double* __restrict__ slots, T* __restrict__ ws) {
     using S = GramRowsShape<T, B>;
     constexpr int CPL = S::CPL, LPR = S::LPR, RL = S::RL, R = S::R, U = S::U, NV = S::NV, LOGRL = S::LOGRL;
     constexpr int NS = S::NS, SROWS = S::SROWS;
     constexpr int PIECES = SROWS * LPR / 32;  // 16-byte copies per lane per stage
     static_assert(LPR >= 1 && LPR <= 32 && 32 % LPR == 0 && B % CPL == 0 && (1 << LOGRL) == RL, "gram_rows shape");
     static_assert((SROWS * LPR) % 32 == 0, "stage pieces");
-    // [ W tile: layout [h][row][CPL] | per-warp rings: NS stages of SROWS rows ]
-    extern __shared__ __align__(16) unsigned char gram_rows_smem[];
-    T* ws = reinterpret_cast<T*>(gram_rows_smem);
-    __shared__ int s_chunk;
     const int nblocks = m / B;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane % LPR, t = lane / LPR;
     T* ring = ws + (size_t)R * B + (size_t)warp * NS * SROWS * B;
     const int ngrp = S::kWarps / wpb;
     const int grp = warp / wpb, sub = warp % wpb;
-    const int rsub = rc / wpb;  // rc <= R rows per chunk (fewer for small n)
-    double* part = partial + ((int64_t)blockIdx.x * wpb + sub) * m * B;
-    for (int64_t e = threadIdx.x; e < (int64_t)wpb * m * B; e += kThreads)
-        partial[(int64_t)blockIdx.x * wpb * m * B + e] = 0.0;
+    double* part = slots + (int64_t)sub * m * B;
     // after the butterfly lane t holds sums vbase .. vbase + NK - 1; when
     // NV < RL the last rounds are plain all-reduces and only t < NV write
     constexpr int NK = NV >= RL ? NV / RL : 1;
@@ -306,6 +312,155 @@ __global__ void __launch_bounds__(kThreads) gram_rows_kernel(int64_t n, int m, i
     for (int k = 0; k < LOGRL; ++k)
         if ((NV >> k) > 1 && (t & (1 << k))) vbase += NV >> (k + 1);
     const bool writer = (NV >= RL) || (t < NV);
+    for (int e = threadIdx.x; e < R * LPR; e += kThreads) {
+        const int r = e / LPR, h = e % LPR;
+        T v[CPL];
+        if (r < rows) {
+            ldvec<T, CPL>(W + (r0 + r) * B + h * CPL, v);
+        } else {
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) v[q] = T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) ws[(h * R + r) * CPL + q] = v[q];
+    }
+    __syncthreads();
+    const int rb = sub * rsub;
+    const int re = min(rows, rb + rsub);
+    if (re <= rb) return;
+    const int nst = (re - rb + SROWS - 1) / SROWS;       // stages per block
+    const int nblk = (nblocks - grp + ngrp - 1) / ngrp;  // blocks of this warp
+    const int total = nblk * nst;
+    // stage k: block grp + (k / nst) * ngrp, rows rb + (k % nst) * SROWS ..
+    auto issue = [&](int k) {
+        T* buf = ring + (size_t)(k % NS) * SROWS * B;
+        if (k < total) {
+            const int j = grp + (k / nst) * ngrp;
+            const int s0 = rb + (k % nst) * SROWS;
+            const T* src = Q + ((int64_t)j * n + r0 + s0) * B;
+#pragma unroll
+            for (int i = 0; i < PIECES; ++i) {
+                const int pc = lane + 32 * i;
+                const int row = pc / LPR, h = pc % LPR;
+                const bool ok = s0 + row < re;
+                cp_async16(buf + (size_t)pc * CPL, ok ? (const void*)(src + (size_t)row * B + h * CPL) : (const void*)Q,
+                           ok ? 16 : 0);
+            }
+        }
+        cp_async_commit();  // an empty group past the end keeps the count uniform
+    };
+#pragma unroll
+    for (int k = 0; k < NS - 1; ++k) issue(k);
+    T acc[CPL][B];
+#pragma unroll
+    for (int i = 0; i < CPL; ++i)
+#pragma unroll
+        for (int cc = 0; cc < B; ++cc) acc[i][cc] = T(0);
+    for (int k = 0; k < total; ++k) {
+        cp_async_wait<NS - 2>();
+        __syncwarp();
+        issue(k + NS - 1);  // into the buffer consumed at k - 1
+        const T* buf = ring + (size_t)(k % NS) * SROWS * B;
+        const int s0 = rb + (k % nst) * SROWS;
+        T bat[CPL][B];
+#pragma unroll
+        for (int i = 0; i < CPL; ++i)
+#pragma unroll
+            for (int cc = 0; cc < B; ++cc) bat[i][cc] = T(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int rr = t + u * RL;              // row within the stage (zero past the share)
+            const int row = min(s0 + rr, R - 1);    // row within the W tile
+            T q[CPL];
+            T w[B];
+            const T* qs = buf + (size_t)rr * B + g * CPL;
+            if constexpr (sizeof(T) == 4) {
+                const float4 x = *reinterpret_cast<const float4*>(qs);
+                q[0] = x.x;
+                q[1] = x.y;
+                q[2] = x.z;
+                q[3] = x.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < CPL; ++i) q[i] = qs[i];
+            }
+#pragma unroll
+            for (int h = 0; h < LPR; ++h) {
+                const T* src = ws + (h * R + row) * CPL;
+                if constexpr (sizeof(T) == 4) {
+                    const float4 x = *reinterpret_cast<const float4*>(src);
+                    w[h * CPL + 0] = x.x;
+                    w[h * CPL + 1] = x.y;
+                    w[h * CPL + 2] = x.z;
+                    w[h * CPL + 3] = x.w;
+                } else {
+#pragma unroll
+                    for (int q2 = 0; q2 < CPL; ++q2) w[h * CPL + q2] = src[q2];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                for (int cc = 0; cc < B; ++cc) bat[i][cc] = fma(q[i], w[cc], bat[i][cc]);
+        }
+#pragma unroll
+        for (int i = 0; i < CPL; ++i)
+#pragma unroll
+            for (int cc = 0; cc < B; ++cc) acc[i][cc] = add_any(acc[i][cc], bat[i][cc]);
+        if ((k % nst) == nst - 1) {
+            // last stage of block j: butterfly over the RL row lanes
+            const int j = grp + (k / nst) * ngrp;
+            T v[NV];
+#pragma unroll
+            for (int e = 0; e < NV; ++e) v[e] = acc[e / B][e % B];
+#pragma unroll
+            for (int kk = 0; kk < LOGRL; ++kk) {
+                const int o = (1 << kk) * LPR;
+                const bool up = (t & (1 << kk)) != 0;
+                if ((NV >> kk) > 1) {
+                    const int hv = NV >> (kk + 1);
+#pragma unroll
+                    for (int x = 0; x < NV / 2; ++x) {
+                        if (x < hv) {
+                            const T send = up ? v[x] : v[x + hv];
+                            const T keep = up ? v[x + hv] : v[x];
+                            v[x] = add_any(keep, shfl_xor_any(0xffffffffu, send, o));
+                        }
+                    }
+                } else {
+                    v[0] = add_any(v[0], shfl_xor_any(0xffffffffu, v[0], o));
+                }
+            }
+            if (writer) {
+#pragma unroll
+                for (int x = 0; x < NK; ++x) {
+                    const int e = vbase + x;
+                    const int i = e / B, cc = e % B;
+                    part[(int64_t)(j * B + g * CPL + i) * B + cc] += (double)v[x];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                for (int cc = 0; cc < B; ++cc) acc[i][cc] = T(0);
+        }
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+}
+
+// Single problem: persistent CTAs take chunks of rc rows from the ticket
+// counter and accumulate into their own wpb slots.
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads) gram_rows_kernel(int64_t n, int m, int wpb, int rc, int nchunks,
+                                                             const T* __restrict__ Q, const T* __restrict__ W,
+                                                             double* __restrict__ partial, int* __restrict__ ticket) {
+    // [ W tile: layout [h][row][CPL] | per-warp rings: NS stages of SROWS rows ]
+    extern __shared__ __align__(16) unsigned char gram_rows_smem[];
+    T* ws = reinterpret_cast<T*>(gram_rows_smem);
+    __shared__ int s_chunk;
+    double* slots = partial + (int64_t)blockIdx.x * wpb * m * B;
+    for (int64_t e = threadIdx.x; e < (int64_t)wpb * m * B; e += kThreads) slots[e] = 0.0;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1);
@@ -314,142 +469,32 @@ __global__ void __launch_bounds__(kThreads) gram_rows_kernel(int64_t n, int m, i
         if (c >= nchunks) break;
         const int64_t r0 = (int64_t)c * rc;
         const int rows = (int)min((int64_t)rc, n - r0);
-        for (int e = threadIdx.x; e < R * LPR; e += kThreads) {
-            const int r = e / LPR, h = e % LPR;
-            T v[CPL];
-            if (r < rows) {
-                ldvec<T, CPL>(W + (r0 + r) * B + h * CPL, v);
-            } else {
-#pragma unroll
-                for (int q = 0; q < CPL; ++q) v[q] = T(0);
-            }
-#pragma unroll
-            for (int q = 0; q < CPL; ++q) ws[(h * R + r) * CPL + q] = v[q];
-        }
-        __syncthreads();
-        const int rb = sub * rsub;
-        const int re = min(rows, rb + rsub);
-        if (re <= rb) continue;
-        const int nst = (re - rb + SROWS - 1) / SROWS;       // stages per block
-        const int nblk = (nblocks - grp + ngrp - 1) / ngrp;  // blocks of this warp
-        const int total = nblk * nst;
-        // stage k: block grp + (k / nst) * ngrp, rows rb + (k % nst) * SROWS ..
-        auto issue = [&](int k) {
-            T* buf = ring + (size_t)(k % NS) * SROWS * B;
-            if (k < total) {
-                const int j = grp + (k / nst) * ngrp;
-                const int s0 = rb + (k % nst) * SROWS;
-                const T* src = Q + ((int64_t)j * n + r0 + s0) * B;
-#pragma unroll
-                for (int i = 0; i < PIECES; ++i) {
-                    const int pc = lane + 32 * i;
-                    const int row = pc / LPR, h = pc % LPR;
-                    const bool ok = s0 + row < re;
-                    cp_async16(buf + (size_t)pc * CPL, ok ? (const void*)(src + (size_t)row * B + h * CPL) : (const void*)Q,
-                               ok ? 16 : 0);
-                }
-            }
-            cp_async_commit();  // an empty group past the end keeps the count uniform
-        };
-#pragma unroll
-        for (int k = 0; k < NS - 1; ++k) issue(k);
-        T acc[CPL][B];
-#pragma unroll
-        for (int i = 0; i < CPL; ++i)
-#pragma unroll
-            for (int cc = 0; cc < B; ++cc) acc[i][cc] = T(0);
-        for (int k = 0; k < total; ++k) {
-            cp_async_wait<NS - 2>();
-            __syncwarp();
-            issue(k + NS - 1);  // into the buffer consumed at k - 1
-            const T* buf = ring + (size_t)(k % NS) * SROWS * B;
-            const int s0 = rb + (k % nst) * SROWS;
-            T bat[CPL][B];
-#pragma unroll
-            for (int i = 0; i < CPL; ++i)
-#pragma unroll
-                for (int cc = 0; cc < B; ++cc) bat[i][cc] = T(0);
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int rr = t + u * RL;              // row within the stage (zero past the share)
-                const int row = min(s0 + rr, R - 1);    // row within the W tile
-                T q[CPL];
-                T w[B];
-                const T* qs = buf + (size_t)rr * B + g * CPL;
-                if constexpr (sizeof(T) == 4) {
-                    const float4 x = *reinterpret_cast<const float4*>(qs);
-                    q[0] = x.x;
-                    q[1] = x.y;
-                    q[2] = x.z;
-                    q[3] = x.w;
-                } else {
-#pragma unroll
-                    for (int i = 0; i < CPL; ++i) q[i] = qs[i];
-                }
-#pragma unroll
-                for (int h = 0; h < LPR; ++h) {
-                    const T* src = ws + (h * R + row) * CPL;
-                    if constexpr (sizeof(T) == 4) {
-                        const float4 x = *reinterpret_cast<const float4*>(src);
-                        w[h * CPL + 0] = x.x;
-                        w[h * CPL + 1] = x.y;
-                        w[h * CPL + 2] = x.z;
-                        w[h * CPL + 3] = x.w;
-                    } else {
-#pragma unroll
-                        for (int q2 = 0; q2 < CPL; ++q2) w[h * CPL + q2] = src[q2];
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < CPL; ++i)
-#pragma unroll
-                    for (int cc = 0; cc < B; ++cc) bat[i][cc] = fma(q[i], w[cc], bat[i][cc]);
-            }
-#pragma unroll
-            for (int i = 0; i < CPL; ++i)
-#pragma unroll
-                for (int cc = 0; cc < B; ++cc) acc[i][cc] = add_any(acc[i][cc], bat[i][cc]);
-            if ((k % nst) == nst - 1) {
-                // last stage of block j: butterfly over the RL row lanes
-                const int j = grp + (k / nst) * ngrp;
-                T v[NV];
-#pragma unroll
-                for (int e = 0; e < NV; ++e) v[e] = acc[e / B][e % B];
-#pragma unroll
-                for (int kk = 0; kk < LOGRL; ++kk) {
-                    const int o = (1 << kk) * LPR;
-                    const bool up = (t & (1 << kk)) != 0;
-                    if ((NV >> kk) > 1) {
-                        const int hv = NV >> (kk + 1);
-#pragma unroll
-                        for (int x = 0; x < NV / 2; ++x) {
-                            if (x < hv) {
-                                const T send = up ? v[x] : v[x + hv];
-                                const T keep = up ? v[x + hv] : v[x];
-                                v[x] = add_any(keep, shfl_xor_any(0xffffffffu, send, o));
-                            }
-                        }
-                    } else {
-                        v[0] = add_any(v[0], shfl_xor_any(0xffffffffu, v[0], o));
-                    }
-                }
-                if (writer) {
-#pragma unroll
-                    for (int x = 0; x < NK; ++x) {
-                        const int e = vbase + x;
-                        const int i = e / B, cc = e % B;
-                        part[(int64_t)(j * B + g * CPL + i) * B + cc] += (double)v[x];
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < CPL; ++i)
-#pragma unroll
-                    for (int cc = 0; cc < B; ++cc) acc[i][cc] = T(0);
-            }
-        }
-        cp_async_wait<0>();
-        __syncwarp();
+        gram_rows_chunk<T, B>(n, m, wpb, r0, rows, rc / wpb, Q, W, slots, ws);
     }
+}
+
+// Batch of problems stacked row-wise: CTA x takes chunk x, rows
+// [chunks[3x+1], chunks[3x+2]) of segment chunks[3x] (at most R rows, never
+// crossing a segment), and writes its own wpb slots at partial[x * wpb * m * B].
+// m is read from device memory so that one captured graph serves every
+// iteration; chunks of inactive segments do nothing.
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads) gram_rows_seg_kernel(int64_t n, const int* __restrict__ d_m,
+                                                                 const int64_t* __restrict__ chunks,
+                                                                 const int* __restrict__ seg_active,
+                                                                 const T* __restrict__ Q, const T* __restrict__ W,
+                                                                 double* __restrict__ partial) {
+    extern __shared__ __align__(16) unsigned char gram_rows_smem[];
+    const int64_t seg = chunks[3 * blockIdx.x];
+    if (seg_active && !seg_active[seg]) return;
+    const int m = *d_m;
+    const int wpb = gram_rows_wpb(m / B);
+    const int64_t r0 = chunks[3 * blockIdx.x + 1];
+    const int rows = (int)(chunks[3 * blockIdx.x + 2] - r0);
+    double* slots = partial + (int64_t)blockIdx.x * wpb * m * B;
+    for (int64_t e = threadIdx.x; e < (int64_t)wpb * m * B; e += kThreads) slots[e] = 0.0;
+    gram_rows_chunk<T, B>(n, m, wpb, r0, rows, (rows + wpb - 1) / wpb, Q, W, slots,
+                          reinterpret_cast<T*>(gram_rows_smem));
 }
 
 // Segmented Gram for a batch of independent problems stacked row-wise:
@@ -700,8 +745,7 @@ bbl_status launch_gram_rows(int64_t n, int m, const T* Q, const T* W, double* C,
         if (occ < 1) occ = 1;
     }
     const int nblocks = m / B;
-    int wpb = 1;  // warps per block when there are fewer blocks than warps
-    while (wpb < kThreads / 32 && nblocks * wpb * 2 <= kThreads / 32) wpb <<= 1;
+    const int wpb = gram_rows_wpb(nblocks);  // warps per block when there are fewer blocks than warps
     // leave a few SMs to the Ritz solve that runs beside the main stream: a
     // persistent CTA that cannot start until such a kernel ends would hold the
     // whole Gram back
@@ -1223,18 +1267,37 @@ bbl_status cholqr2_dev(int64_t n, int b, int dtype, void* W, double* B, double d
 // graph serves every iteration.
 namespace {
 
+// C[s] = sum of segment s's partial slots (rows_slots: the row-contiguous
+// kernel's wpb slots per chunk, else one), in chunk order
 __global__ void reduce_seg_kernel(int m_max, int b, const int* __restrict__ d_m, const int* __restrict__ seg_chunk_ptr,
                                   const int* __restrict__ active, const double* __restrict__ partial,
-                                  double* __restrict__ C) {
+                                  double* __restrict__ C, int rows_slots) {
     const int s = blockIdx.y;
     if (active && !active[s]) return;
     const int m = d_m ? *d_m : m_max;
+    const int per = rows_slots ? gram_rows_wpb(m / b) : 1;
     const int64_t count = (int64_t)m * b;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= count) return;
     double acc = 0.0;
-    for (int c = seg_chunk_ptr[s]; c < seg_chunk_ptr[s + 1]; ++c) acc += partial[(int64_t)c * count + e];
+    for (int c = seg_chunk_ptr[s] * per; c < seg_chunk_ptr[s + 1] * per; ++c) acc += partial[(int64_t)c * count + e];
     C[(int64_t)s * m_max * b + e] = acc;
+}
+
+template <typename T, int B>
+bbl_status launch_gram_rows_seg(int64_t n, const int* d_m, const T* Q, const T* W, const int64_t* chunks, int nchunks,
+                                const int* active, double* partial, cudaStream_t st) {
+    using S = GramRowsShape<T, B>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        BBL_CUDA(cudaFuncSetAttribute(gram_rows_seg_kernel<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)S::smem_bytes));
+        attr_set = true;
+    }
+    gram_rows_seg_kernel<T, B><<<(unsigned)nchunks, kThreads, S::smem_bytes, st>>>(n, d_m, chunks, active, Q, W,
+                                                                                   partial);
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
 }
 
 template <typename T, int B, int CPT>
@@ -1300,11 +1363,37 @@ bbl_status apply_seg_typed(int64_t n, int b, int kc, const int* ms, int mss, con
 
 }  // namespace
 
+int gram_seg_chunk_rows(int b, int dtype) {
+    if (dtype == BBL_FP64) {
+        if (b == 4) return GramRowsShape<double, 4>::R;
+        if (b == 8) return GramRowsShape<double, 8>::R;
+    } else if (dtype == BBL_FP32) {
+        if (b == 4) return GramRowsShape<float, 4>::R;
+        if (b == 8) return GramRowsShape<float, 8>::R;
+        if (b == 16) return GramRowsShape<float, 16>::R;
+    }
+    return 0;
+}
+
 bbl_status gram_seg(int64_t n, int b, int m_max, const int* d_m, int dtype, const void* Q, const void* W,
                     const int64_t* chunks, int nchunks, const int* seg_chunk_ptr, int nseg, const int* active,
                     double* partial, double* C, cudaStream_t st) {
     constexpr int kC = 4;
-    if (dtype == BBL_FP64) {
+    const int rows_slots = gram_seg_chunk_rows(b, dtype) > 0 ? 1 : 0;
+    if (rows_slots) {
+        if (dtype == BBL_FP64) {
+            auto q = static_cast<const double*>(Q);
+            auto w = static_cast<const double*>(W);
+            if (b == 4) BBL_TRY((launch_gram_rows_seg<double, 4>(n, d_m, q, w, chunks, nchunks, active, partial, st)));
+            else BBL_TRY((launch_gram_rows_seg<double, 8>(n, d_m, q, w, chunks, nchunks, active, partial, st)));
+        } else {
+            auto q = static_cast<const float*>(Q);
+            auto w = static_cast<const float*>(W);
+            if (b == 4) BBL_TRY((launch_gram_rows_seg<float, 4>(n, d_m, q, w, chunks, nchunks, active, partial, st)));
+            else if (b == 8) BBL_TRY((launch_gram_rows_seg<float, 8>(n, d_m, q, w, chunks, nchunks, active, partial, st)));
+            else BBL_TRY((launch_gram_rows_seg<float, 16>(n, d_m, q, w, chunks, nchunks, active, partial, st)));
+        }
+    } else if (dtype == BBL_FP64) {
         auto q = static_cast<const double*>(Q);
         auto w = static_cast<const double*>(W);
         switch (b) {
@@ -1328,7 +1417,7 @@ bbl_status gram_seg(int64_t n, int b, int m_max, const int* d_m, int dtype, cons
         }
     }
     dim3 g((unsigned)ceil_div((int64_t)m_max * b, 256), (unsigned)nseg);
-    reduce_seg_kernel<<<g, 256, 0, st>>>(m_max, b, d_m, seg_chunk_ptr, active, partial, C);
+    reduce_seg_kernel<<<g, 256, 0, st>>>(m_max, b, d_m, seg_chunk_ptr, active, partial, C, rows_slots);
     BBL_LAUNCH_CHECK();
     return BBL_OK;
 }

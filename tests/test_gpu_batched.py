@@ -37,6 +37,24 @@ def test_batched_solve_matches_dense_eigensolves(storage):
     assert np.all(rs.max(axis=1) <= (1e-8 if storage == "fp64" else 1e-4) * nrm)
 
 
+@pytest.mark.parametrize("storage,b", [("fp64", 2), ("fp64", 8), ("fp32", 8), ("fp32", 16)])
+def test_batched_block_sizes_match_dense_eigensolves(storage, b):
+    """Other block sizes: b = 8 and 16 take the row-contiguous segmented Gram
+    (tile-sized chunks), b = 2 the column-group one.  The FP64 oracle needs
+    up to 47 blocks of 8 on these matrices at 1e-10, so the basis may hold
+    640 vectors (capped per problem by the smallest one's size)."""
+    torch, bbl = need_gpu()
+    mats = _family(count=5, seed=17)
+    B = bbl.Batch(mats, storage=storage)
+    tol = 1e-10 if storage == "fp64" else 2e-6
+    ev, rs, it, st, stats = B.solve(4, b, tol=tol, max_vectors=640, seed=5)
+    assert np.all(st == 0), st
+    rel = 1e-10 if storage == "fp64" else 1e-5
+    for s, A in enumerate(mats):
+        want = np.linalg.eigvalsh(A.to_dense())[:4]
+        np.testing.assert_allclose(ev[s], want, rtol=rel, atol=rel * np.abs(want).max())
+
+
 def test_batched_graph_and_host_loop_agree():
     torch, bbl = need_gpu()
     mats = _family(count=5, seed=8)
@@ -45,6 +63,24 @@ def test_batched_graph_and_host_loop_agree():
     e2, r2, i2, s2, _ = B.solve(4, 4, use_graph=False, tol=1e-9, max_vectors=120, seed=2)
     np.testing.assert_array_equal(i1, i2)
     np.testing.assert_array_equal(e1, e2)
+
+
+def test_batched_adaptive_tests_stop_at_or_just_after_every_block_tests():
+    """Per-problem adaptive test schedule against a test after every block:
+    a problem can only stop at a tested block, so it stops at or after the
+    first block that passes, within the 8-block step bound; the eigenvalues
+    agree to the tolerance either way."""
+    torch, bbl = need_gpu()
+    mats = _family(count=6, seed=12)
+    B = bbl.Batch(mats, storage="fp64")
+    # the FP64 oracle needs 44-64 blocks of 4 on these matrices at 1e-9
+    e1, r1, i1, s1, _ = B.solve(4, 4, tol=1e-9, max_vectors=400, seed=4, check_every=1)
+    e0, r0, i0, s0, _ = B.solve(4, 4, tol=1e-9, max_vectors=400, seed=4, check_every=0)
+    assert np.all(s1 == 0) and np.all(s0 == 0), (s1, s0)
+    assert np.all(i0 >= i1) and np.all(i0 <= i1 + 8), (i0, i1)
+    nrm = np.array([np.abs(A.to_dense()).sum(axis=1).max() for A in mats])
+    np.testing.assert_allclose(e0, e1, rtol=0, atol=1e-8 * nrm.max())
+    assert np.all(r0.max(axis=1) <= 1e-7 * nrm)
 
 
 def test_batched_segment_equals_single_solve_with_the_same_pivot():
