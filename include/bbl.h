@@ -126,6 +126,20 @@ const char* bbl_status_string(bbl_status s);
 int bbl_version(void);
 /* Number of kernels this library has launched in the process so far. */
 uint64_t bbl_kernel_launches(void);
+/* Workspace cache.  The Lanczos bases (bbl_solve, bbl_pivot_bootstrap,
+ * bbl_batch_solve) are device allocations of up to max_vectors * n * s bytes;
+ * when a call ends they stay reserved for the next call on the same device
+ * instead of being freed (an allocation plus free of 16 GB costs about 10 ms).
+ * Reuse is ordered by an event on the stream that last used the memory, so
+ * calls on different streams may share the cache.  A call whose allocation
+ * fails frees the idle buffers and tries once more before reporting
+ * BBL_ERR_OOM; other users of the device get the memory back only through
+ * bbl_workspace_release.
+ *   bbl_workspace_bytes    bytes held idle for the current device
+ *   bbl_workspace_release  waits for and frees every idle buffer of the
+ *                          current device; BBL_ERR_CUDA if that fails      */
+size_t bbl_workspace_bytes(void);
+bbl_status bbl_workspace_release(void);
 
 /* ---------------------------------------------------------------- matrix
  * Copies a CSR matrix (host or device arrays) to the device.

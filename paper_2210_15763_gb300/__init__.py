@@ -231,6 +231,16 @@ def pivot_rr_residual(A: Matrix, P, stream=None):
     return th, rs
 
 
+def workspace_bytes() -> int:
+    """Bytes of Lanczos bases the library keeps idle for reuse on this device."""
+    return int(_lib.load().bbl_workspace_bytes())
+
+
+def workspace_release():
+    """Frees the idle cached bases of the current device."""
+    _lib.check(_lib.load().bbl_workspace_release())
+
+
 class MLP:
     """The learned-pivot network (bbl_mlp): 1 -> hidden -> hidden -> out."""
 

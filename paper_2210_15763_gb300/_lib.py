@@ -46,6 +46,8 @@ SIGNATURES = {
     "bbl_status_string": (C.c_char_p, [ST]),
     "bbl_version": (C.c_int, []),
     "bbl_kernel_launches": (C.c_uint64, []),
+    "bbl_workspace_bytes": (C.c_size_t, []),
+    "bbl_workspace_release": (ST, []),
     "bbl_matrix_create": (ST, [I64, I64, P, P, P, I32, I32, I32, I32, I32, I32, P, C.POINTER(P)]),
     "bbl_matrix_destroy": (None, [P]),
     "bbl_matrix_info": (ST, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(D), C.POINTER(I64), C.POINTER(I32),

@@ -1,6 +1,8 @@
-// Error state, option defaults and small ABI helpers.
+// Error state, option defaults, the workspace cache and small ABI helpers.
 #include <atomic>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -34,9 +36,121 @@ bool is_device_pointer(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// ------------------------------------------------------------------ workspace cache
+namespace {
+struct IdleBuf {
+    void* p;
+    size_t bytes;
+    int dev;
+    cudaEvent_t ready;  // recorded on the last stream that used it
+};
+std::mutex g_pool_mu;
+std::vector<IdleBuf> g_idle;
+
+// frees the idle buffers of device dev; the caller holds g_pool_mu and has
+// dev current
+void free_idle_locked(int dev) {
+    for (size_t i = 0; i < g_idle.size();) {
+        IdleBuf& e = g_idle[i];
+        if (e.dev == dev) {
+            cudaEventSynchronize(e.ready);
+            cudaEventDestroy(e.ready);
+            cudaFree(e.p);
+            g_idle.erase(g_idle.begin() + (std::ptrdiff_t)i);
+        } else {
+            ++i;
+        }
+    }
+}
+}  // namespace
+
+bbl_status PoolBuf::alloc(size_t nbytes, cudaStream_t stream) {
+    release();
+    if (nbytes == 0) nbytes = 16;
+    int d = 0;
+    BBL_CUDA(cudaGetDevice(&d));
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    int best = -1;
+    for (size_t i = 0; i < g_idle.size(); ++i) {
+        const IdleBuf& e = g_idle[i];
+        if (e.dev == d && e.bytes >= nbytes && (best < 0 || e.bytes < g_idle[(size_t)best].bytes)) best = (int)i;
+    }
+    if (best >= 0) {
+        const IdleBuf e = g_idle[(size_t)best];
+        g_idle.erase(g_idle.begin() + best);
+        const cudaError_t w = cudaStreamWaitEvent(stream, e.ready, 0);
+        cudaEventDestroy(e.ready);
+        if (w != cudaSuccess) {
+            cudaFree(e.p);
+            return set_error(BBL_ERR_CUDA, "workspace: cudaStreamWaitEvent: %s", cudaGetErrorString(w));
+        }
+        p = e.p;
+        bytes = e.bytes;
+        st = stream;
+        dev = d;
+        return BBL_OK;
+    }
+    cudaError_t e = cudaMalloc(&p, nbytes);
+    if (e == cudaErrorMemoryAllocation) {  // give the idle buffers back, then once more
+        (void)cudaGetLastError();
+        free_idle_locked(d);
+        e = cudaMalloc(&p, nbytes);
+    }
+    if (e != cudaSuccess) {
+        p = nullptr;
+        (void)cudaGetLastError();
+        return set_error(BBL_ERR_OOM, "cudaMalloc(%zu bytes): %s", nbytes, cudaGetErrorString(e));
+    }
+    bytes = nbytes;
+    st = stream;
+    dev = d;
+    return BBL_OK;
+}
+
+void PoolBuf::release() {
+    if (!p) return;
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess && cudaEventRecord(ev, st) == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        g_idle.push_back(IdleBuf{p, bytes, dev, ev});
+    } else {
+        // reuse cannot be ordered: give it back (cudaFree waits for the device)
+        if (ev) cudaEventDestroy(ev);
+        (void)cudaGetLastError();
+        cudaFree(p);
+    }
+    p = nullptr;
+    bytes = 0;
+}
+
+size_t pool_idle_bytes(int dev) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    size_t t = 0;
+    for (const IdleBuf& e : g_idle)
+        if (e.dev == dev) t += e.bytes;
+    return t;
+}
+
 }  // namespace bbl
 
 extern "C" {
+
+size_t bbl_workspace_bytes(void) {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return bbl::pool_idle_bytes(d);
+}
+
+bbl_status bbl_workspace_release(void) {
+    int d = 0;
+    BBL_CUDA(cudaGetDevice(&d));
+    std::lock_guard<std::mutex> lk(bbl::g_pool_mu);
+    bbl::free_idle_locked(d);
+    return BBL_OK;
+}
 
 const char* bbl_last_error(void) { return bbl::g_last_error.c_str(); }
 

@@ -372,12 +372,13 @@ bbl_status bbl_batch_solve(bbl_batch* Bt, int nev, int b, const bbl_options* opt
     chunk_ptr[nseg] = (int)(chunks.size() / 3);
     const int nchunks = (int)(chunks.size() / 3), nctas = (int)(ctas.size() / 3);
     // ---- device buffers ----
-    DevBuf d_chunks, d_ctas, d_chunk_ptr, basis, Vfix, Wfix, C1, C2, G, R1, R1i, R2, R2i, Bj, partial, Tb, theta, width,
+    PoolBuf basis;
+    DevBuf d_chunks, d_ctas, d_chunk_ptr, Vfix, Wfix, C1, C2, G, R1, R1i, R2, R2i, Bj, partial, Tb, theta, width,
         S, est, ws, tmp, ints, thr, X, Y, rpart, piv, lprev;
     BBL_TRY(d_chunks.alloc(sizeof(int64_t) * chunks.size()));
     BBL_TRY(d_ctas.alloc(sizeof(int64_t) * ctas.size()));
     BBL_TRY(d_chunk_ptr.alloc(sizeof(int) * (nseg + 1)));
-    BBL_TRY(basis.alloc((size_t)(J_max + 1) * n * b * sz));
+    BBL_TRY(basis.alloc((size_t)(J_max + 1) * n * b * sz, st));
     BBL_TRY(Vfix.alloc((size_t)n * b * sz));
     BBL_TRY(Wfix.alloc((size_t)n * b * sz));
     BBL_TRY(C1.alloc(sizeof(double) * (size_t)nseg * m_max * b));

@@ -91,6 +91,30 @@ struct DevBuf {
     T* as() const { return static_cast<T*>(p); }
 };
 
+// Large scratch kept across calls (the Lanczos bases): release() hands the
+// allocation to a per-device idle list with an event recorded on the stream
+// it was used on; alloc() takes the smallest idle allocation of this device
+// that is large enough and makes its own stream wait on that event, so reuse
+// is ordered on the GPU without a host synchronisation.  When cudaMalloc runs
+// out of memory the idle allocations of the device are freed and it is tried
+// once more.  bbl_workspace_release() frees every idle allocation.
+struct PoolBuf {
+    void* p = nullptr;
+    size_t bytes = 0;  // capacity
+    cudaStream_t st = nullptr;
+    int dev = 0;
+    PoolBuf() = default;
+    PoolBuf(const PoolBuf&) = delete;
+    PoolBuf& operator=(const PoolBuf&) = delete;
+    ~PoolBuf() { release(); }
+    bbl_status alloc(size_t nbytes, cudaStream_t stream);
+    void release();
+    template <typename T>
+    T* as() const { return static_cast<T*>(p); }
+};
+// bytes held idle for device dev (counted as free when sizing a basis)
+size_t pool_idle_bytes(int dev);
+
 // Pinned host staging buffer.
 struct HostBuf {
     void* p = nullptr;

@@ -312,6 +312,9 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     {
         size_t freeb = 0, totalb = 0;
         BBL_CUDA(cudaMemGetInfo(&freeb, &totalb));
+        int dev = 0;
+        BBL_CUDA(cudaGetDevice(&dev));
+        freeb += pool_idle_bytes(dev);  // cached bases are available to this call
         // float-float blocks also keep an FP32 copy (first Gram-Schmidt pass)
         const size_t per_block = (size_t)n * b * (s + (dtype == kDF32 ? sizeof(float) : 0));
         const size_t reserve = (size_t)(2ull << 30) + 8 * (size_t)n * b * 8;
@@ -322,15 +325,17 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     }
     const int m_max = J_max * b;
     if (nev > m_max) return set_error(BBL_ERR_INVALID_ARG, "solve: nev=%d exceeds the basis capacity %d", nev, m_max);
-    DevBuf basis, Z, coeff, partials, small, Tb, S, rwork, flags, bj;
+    DevBuf Z, coeff, partials, small, Tb, S, rwork, flags, bj;
+    PoolBuf basis;
     // float-float blocks: FP32 copies of the basis (high parts) and of W for
     // the first Gram-Schmidt pass, whose coefficients only need to remove the
     // bulk (the second pass, in float-float, takes out the rest; A_j then
     // sums both passes' own-block coefficients)
-    DevBuf shadow, whi;
-    BBL_TRY(basis.alloc((size_t)J_max * n * b * s));
+    PoolBuf shadow;
+    DevBuf whi;
+    BBL_TRY(basis.alloc((size_t)J_max * n * b * s, st));
     if (dtype == kDF32) {
-        BBL_TRY(shadow.alloc((size_t)J_max * n * b * sizeof(float)));
+        BBL_TRY(shadow.alloc((size_t)J_max * n * b * sizeof(float), st));
         BBL_TRY(whi.alloc((size_t)n * b * sizeof(float)));
     }
     BBL_TRY(Z.alloc((size_t)n * b * s));

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def header_functions():
     src = open(os.path.join(ROOT, "include", "bbl.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:bbl_status|void|int|const char\*)\s+(bbl_\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:bbl_status|void|int|size_t|uint64_t|const char\*)\s+(bbl_\w+)\s*\(", src, flags=re.M)))
 
 
 def test_header_declares_the_boundary():

@@ -264,3 +264,30 @@ def test_bad_arguments_and_not_converged():
     res = bbl.solve(M, 4, 4, pivot=OR.normal_block(5, H.n, 4), tol=1e-12, max_vectors=12)
     assert res.status == "BBL_ERR_NOT_CONVERGED" and res.stats["iters"] == 3
     assert np.all(np.isfinite(res.evals)) and np.all(res.resid > 0)
+
+
+def test_workspace_cache_reuses_the_bases_across_calls_and_streams():
+    """The bases stay cached after a call and the next call of the same size
+    takes them (no growth); a call on another stream shares them (its reuse
+    is ordered by an event); release empties the cache.  Results agree to
+    rounding (the persistent Gram kernels sum their chunks in ticket order)."""
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4", scale=0.5)
+    M = bbl.Matrix(H, storage="fp32")
+    bbl.workspace_release()
+    assert bbl.workspace_bytes() == 0
+    r1 = bbl.solve(M, 4, 4, pivot=None, seed=3, tol=1e-8, max_vectors=400)
+    held = bbl.workspace_bytes()
+    assert held > 0
+    r2 = bbl.solve(M, 4, 4, pivot=None, seed=3, tol=1e-8, max_vectors=400)
+    assert bbl.workspace_bytes() == held
+    side = torch.cuda.Stream()
+    r3 = bbl.solve(M, 4, 4, pivot=None, seed=3, tol=1e-8, max_vectors=400, stream=side)
+    torch.cuda.synchronize()
+    assert bbl.workspace_bytes() == held
+    for r in (r1, r2, r3):
+        assert r.converged
+    np.testing.assert_allclose(r2.evals, r1.evals, rtol=1e-12)
+    np.testing.assert_allclose(r3.evals, r1.evals, rtol=1e-12)
+    bbl.workspace_release()
+    assert bbl.workspace_bytes() == 0
