@@ -46,6 +46,10 @@ SPMM_TRAFFIC_PER_NNZ = 1.185e9 / 139_708_000
 # 1.248 GB for 139,708,000 nonzeros
 SELL_TRAFFIC_PER_NNZ = 1.248e9 / 139_708_000
 SELL_SIGMA = 256
+# DRAM bytes per algorithmic byte of gram_rows_kernel<float,8> (n*m*4 + n*8*4),
+# from an ncu capture at n = 500,000, m = 720 (1.514 GB for 1.456 GB); the
+# kernel reads the basis once, so traffic grows with n*m
+GRAM_TRAFFIC_PER_BYTE = 1.514e9 / 1.456e9
 METRIC = "time-to-solve lowest 8 eigenpairs @resid 1e-8 (s)"
 
 
@@ -296,7 +300,7 @@ def run_ours(args):
         "gram": {"kernel": "gram_rows_kernel<float,8> + reduce_partials_kernel (first pass; the second pass "
                  "is the same kernel)", "launches": 2 * gram_calls, "total_ms": 2 * tot["t_gram_ms"],
                  "achieved": gram_gbs, "bytes_per_launch": tot["gram_bytes_total"] / max(gram_calls, 1),
-                 "traffic": None},
+                 "traffic": GRAM_TRAFFIC_PER_BYTE * tot["gram_bytes_total"] / max(gram_calls, 1)},
     }
     dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
     kd = kernels[dom]
