@@ -46,10 +46,11 @@ SPMM_TRAFFIC_PER_NNZ = 1.185e9 / 139_708_000
 # 1.248 GB for 139,708,000 nonzeros
 SELL_TRAFFIC_PER_NNZ = 1.248e9 / 139_708_000
 SELL_SIGMA = 256
-# DRAM bytes per algorithmic byte of gram_rows_kernel<float,8> (n*m*4 + n*8*4),
-# from an ncu capture at n = 500,000, m = 720 (1.514 GB for 1.456 GB); the
-# kernel reads the basis once, so traffic grows with n*m
-GRAM_TRAFFIC_PER_BYTE = 1.514e9 / 1.456e9
+# DRAM bytes per algorithmic byte of the first-pass Gram from the FP16 basis
+# copy (gram_half_kernel, n*m*2 + n*8*4), from an ncu capture at n = 500,000,
+# m = 720 (0.7906 GB for 0.736 GB); it reads the copy once, so traffic grows
+# with n*m (None: not captured since the kernel last changed)
+GRAM16_TRAFFIC_PER_BYTE = 0.7906e9 / 0.736e9
 METRIC = "time-to-solve lowest 8 eigenpairs @resid 1e-8 (s)"
 
 
@@ -297,10 +298,11 @@ def run_ours(args):
                  "bytes_per_launch": stats_log[-1]["spmm_bytes"],
                  "traffic": (SPMM_TRAFFIC_PER_NNZ * A.nnz if sched["fmt"] == "csr" and (sched["lanes"] or 32) == 32
                              else SELL_TRAFFIC_PER_NNZ * A.nnz if sched["fmt"] == "sell" else None)},
-        "gram": {"kernel": "gram_rows_kernel<float,8> + reduce_partials_kernel (first pass; the second pass "
-                 "is the same kernel)", "launches": 2 * gram_calls, "total_ms": 2 * tot["t_gram_ms"],
+        "gram": {"kernel": "gram_half_kernel + reduce_partials_kernel (first Gram-Schmidt pass of the FP32 "
+                 "stage, from the FP16 copy of the basis)", "launches": gram_calls, "total_ms": tot["t_gram_ms"],
                  "achieved": gram_gbs, "bytes_per_launch": tot["gram_bytes_total"] / max(gram_calls, 1),
-                 "traffic": GRAM_TRAFFIC_PER_BYTE * tot["gram_bytes_total"] / max(gram_calls, 1)},
+                 "traffic": GRAM16_TRAFFIC_PER_BYTE * tot["gram_bytes_total"] / max(gram_calls, 1)
+                 if GRAM16_TRAFFIC_PER_BYTE else None},
     }
     dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
     kd = kernels[dom]
@@ -419,6 +421,10 @@ def run_kernels(args):
     m = nb * B
     t = timeit(lambda: bbl.block_gram(basis, Wr), args.reps)
     out["gram_fp32"] = {"ms": t, "GBs": (n * m * 4 + n * B * 4) / t / 1e6}
+    basis16 = basis.half()
+    t = timeit(lambda: bbl.block_gram_f16(basis16, Wr), args.reps)
+    out["gram_f16_first_pass"] = {"ms": t, "GBs": (n * m * 2 + n * B * 4) / t / 1e6}
+    del basis16
     basis /= float(np.sqrt(n))  # keep repeated in-place updates bounded
     Wt = torch.empty_like(Wr)
     t = timeit(lambda: bbl.block_reorth(basis, Wt.copy_(Wr), passes=1), args.reps)

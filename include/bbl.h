@@ -95,8 +95,16 @@ typedef struct {
     void* stream;               /* cudaStream_t                                    */
     int ritz_overlap;           /* 1 (default): the Ritz solve of block j runs on a
                                    second stream while block j+1 is formed (one
-                                   speculative block at the end); 0: on `stream`,
-                                   read before the next block                      */
+                                   speculative block at the end); 2: the same, but
+                                   block j+1's Gram-Schmidt waits for it (it
+                                   overlaps the SpMM only); 0: on `stream`, read
+                                   before the next block                           */
+    int half_first_pass;        /* FP32 storage with b = 8: 1 (default) the first
+                                   Gram-Schmidt pass of the FP32 stage reads an
+                                   FP16 copy of the basis (it only has to remove
+                                   the bulk; the FP32 second pass removes the
+                                   rest and A_j sums both passes' coefficients);
+                                   0: both passes read the FP32 basis             */
 } bbl_options;
 
 typedef struct {
@@ -112,11 +120,13 @@ typedef struct {
     double ortho_err;           /* max |V^T V - I| over the final basis (if measured) */
     double spmm_bytes_total;    /* algorithmic bytes of every SpMM of the call     */
     double reorth_bytes_total;  /* algorithmic bytes of every Gram-Schmidt pass:
-                                   per pass 2*n*m*s + 3*n*b*s (m basis columns)    */
+                                   per pass 2*n*m*s + 3*n*b*s (m basis columns;
+                                   an FP16 first-pass Gram counts n*m*s/2 less)    */
     int ritz_solves;            /* Ritz solves (convergence tests) of all stages   */
     int gram_calls;             /* main stage: first-pass Gram products C1 = Q^T W */
     double t_gram_ms;           /* their time (split-K kernel + partial reduction) */
-    double gram_bytes_total;    /* their algorithmic bytes: (n*m + n*b)*s each     */
+    double gram_bytes_total;    /* their algorithmic bytes: (n*m + n*b)*s each
+                                   (n*m*2 + n*b*4 when read from the FP16 copy)    */
     int spmm_calls;             /* main stage SpMM launches (spmm_gbs is over them) */
 } bbl_stats;
 
@@ -196,6 +206,15 @@ bbl_status bbl_block_reorth(int64_t n, int b, int nblocks, bbl_dtype dtype, cons
  * training targets U^T X).  Layouts as in bbl_block_reorth.              */
 bbl_status bbl_block_gram(int64_t n, int b, int nblocks, bbl_dtype dtype, const void* basis, const void* W,
                           double* C, void* stream);
+
+/* C ~= Q16^T W for b = 8, the first Gram-Schmidt pass of the FP32 stage
+ * (bbl_options.half_first_pass): Q16 the FP16 copy of an FP32 basis.
+ *   basis16 device FP16, nblocks consecutive n x 8 row-major blocks
+ *   W       device FP32 n x 8 (not modified)
+ *   C       device FP64 (nblocks*8) x 8 row-major
+ * Products and sums over a chunk of rows in FP32, chunks summed in FP64.
+ * Both pointers 16-byte aligned (BBL_ERR_INVALID_ARG otherwise).         */
+bbl_status bbl_block_gram_f16(int64_t n, int nblocks, const void* basis16, const float* W, double* C, void* stream);
 
 /* Allocation-free variant of bbl_block_gram (no counterpart in the paper).
  * For callers that must not allocate device memory: e.g. a process whose

@@ -220,6 +220,17 @@ def block_gram(basis, W, stream=None):
     return C_
 
 
+def block_gram_f16(basis16, W, stream=None):
+    """C ~= Q16^T W (FP64 m x 8) from an FP16 basis copy and FP32 W (b = 8)."""
+    torch = _torch()
+    nb, n, b = basis16.shape
+    if b != 8 or basis16.dtype != torch.float16 or W.dtype != torch.float32:
+        raise ValueError("block_gram_f16: FP16 basis of n x 8 blocks and FP32 W")
+    C_ = torch.empty((nb * 8, 8), dtype=torch.float64, device=W.device)
+    _lib.check(_lib.load().bbl_block_gram_f16(n, nb, _ptr(basis16), _ptr(W), _ptr(C_), _stream(stream)))
+    return C_
+
+
 def pivot_rr_residual(A: Matrix, P, stream=None):
     """Rayleigh-Ritz values and residual norms of span(P) (the pivot judge)."""
     b = P.shape[1]

@@ -17,7 +17,7 @@ class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_vectors", C.c_int), ("criterion", C.c_int), ("rms_tol", C.c_double),
                 ("seed", C.c_uint64), ("defl_tol", C.c_double), ("storage", C.c_int), ("polish", C.c_int),
                 ("stage1_tol", C.c_double), ("check_every", C.c_int), ("stream", C.c_void_p),
-                ("ritz_overlap", C.c_int)]
+                ("ritz_overlap", C.c_int), ("half_first_pass", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -66,6 +66,7 @@ SIGNATURES = {
     "bbl_solve": (ST, [P, I32, I32, P, C.POINTER(Options), P, P, P, C.POINTER(Stats)]),
     "bbl_block_gram": (ST, [I64, I32, I32, I32, P, P, P, P]),
     "bbl_block_gram_noalloc": (ST, [I64, I32, I32, I32, P, P, P, P]),
+    "bbl_block_gram_f16": (ST, [I64, I32, P, P, P, P]),
     "bbl_pivot_rr_residual": (ST, [P, I32, P, P, P, P]),
     "bbl_mlp_create": (ST, [I32, I32, C.POINTER(P)]),
     "bbl_mlp_destroy": (None, [P]),

@@ -187,6 +187,7 @@ void bbl_options_default(bbl_options* o) {
     o->stage1_tol = 2e-6;
     o->check_every = 0;
     o->ritz_overlap = 1;
+    o->half_first_pass = 1;
     o->stream = nullptr;
 }
 

@@ -18,6 +18,8 @@
 #include <algorithm>
 #include <mutex>
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "df32.cuh"
 
@@ -772,6 +774,133 @@ bbl_status launch_gram_rows(int64_t n, int m, const T* Q, const T* W, double* C,
     return BBL_OK;
 }
 
+// First-pass Gram from an FP16 copy of an FP32 basis (b = 8): C ~= Q16^T W.
+// The first Gram-Schmidt pass only has to take out the bulk of W's component
+// in span(Q) -- the FP32 second pass removes what is left, and A_j sums both
+// passes' coefficients -- so its coefficients may carry the FP16 rounding of
+// Q (relative 2^-11), and the pass reads 2 instead of 4 bytes per basis
+// element.  Persistent CTAs take chunks of kHalfRows rows from a ticket
+// counter and stage W's rows of the chunk in shared memory; a warp takes
+// basis blocks round-robin and walks the chunk's rows, lane l the rows l,
+// l + 32, ... (a warp's loads of one row position are 512 contiguous bytes),
+// kHalfUnroll rows of loads in flight per lane, 64 FP32 sums per lane;
+// a halving butterfly over the 32 lanes leaves two sums per lane, added to
+// the CTA's FP64 slot (m x 8).
+constexpr int kHalfRows = 1024;
+constexpr int kHalfUnroll = 8;
+
+__global__ void __launch_bounds__(kThreads) gram_half_kernel(int64_t n, int m, int nchunks,
+                                                             const __half* __restrict__ Q, const float* __restrict__ W,
+                                                             double* __restrict__ partial, int* __restrict__ ticket) {
+    constexpr int B = 8, NV = 64;
+    __shared__ __align__(16) float ws[kHalfRows * B];
+    __shared__ int s_chunk;
+    const int nblocks = m / B;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* part = partial + (int64_t)blockIdx.x * m * B;
+    for (int e = threadIdx.x; e < m * B; e += kThreads) part[e] = 0.0;
+    // after the butterfly lane l holds the sums vbase, vbase + 1
+    int vbase = 0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+        if (lane & (1 << k)) vbase += NV >> (k + 1);
+    const float4* ws4 = reinterpret_cast<const float4*>(ws);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int c = s_chunk;
+        if (c >= nchunks) break;
+        const int64_t r0 = (int64_t)c * kHalfRows;
+        const int rows = (int)min((int64_t)kHalfRows, n - r0);
+        for (int e = threadIdx.x; e < kHalfRows * 2; e += kThreads) {  // two float4 per row, zeros past the end
+            const int r = e >> 1;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < rows) v = __ldg(reinterpret_cast<const float4*>(W + (r0 + r) * B) + (e & 1));
+            reinterpret_cast<float4*>(ws)[e] = v;
+        }
+        __syncthreads();
+        for (int j = warp; j < nblocks; j += kThreads / 32) {
+            const uint4* qb = reinterpret_cast<const uint4*>(Q + ((int64_t)j * n + r0) * B);
+            float v[NV];
+#pragma unroll
+            for (int e = 0; e < NV; ++e) v[e] = 0.f;
+            for (int r = lane; r < rows; r += 32 * kHalfUnroll) {
+                uint4 qv[kHalfUnroll];
+#pragma unroll
+                for (int u = 0; u < kHalfUnroll; ++u) {
+                    const int rr = r + 32 * u;
+                    qv[u] = rr < rows ? __ldg(qb + rr) : make_uint4(0u, 0u, 0u, 0u);
+                }
+#pragma unroll
+                for (int u = 0; u < kHalfUnroll; ++u) {
+                    const int rr = min(r + 32 * u, kHalfRows - 1);  // past the rows q is zero
+                    const float4 w0 = ws4[2 * rr], w1 = ws4[2 * rr + 1];
+                    const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                    const __half2* h2 = reinterpret_cast<const __half2*>(&qv[u]);
+                    float q[8];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 f = __half22float2(h2[i]);
+                        q[2 * i] = f.x;
+                        q[2 * i + 1] = f.y;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int cc = 0; cc < 8; ++cc) v[i * 8 + cc] = fmaf(q[i], w[cc], v[i * 8 + cc]);
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < 5; ++kk) {
+                const int o = 1 << kk;
+                const bool up = (lane & o) != 0;
+                const int hv = NV >> (kk + 1);
+#pragma unroll
+                for (int x = 0; x < NV / 2; ++x) {
+                    if (x < hv) {
+                        const float send = up ? v[x] : v[x + hv];
+                        const float keep = up ? v[x + hv] : v[x];
+                        v[x] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                    }
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < 2; ++x) {
+                const int e = vbase + x;
+                part[(int64_t)(j * B + e / B) * B + (e % B)] += (double)v[x];
+            }
+        }
+    }
+}
+
+bbl_status launch_gram_half(int64_t n, int m, const __half* Q, const float* W, double* C, DevBuf& partials,
+                            cudaStream_t st) {
+    static int occ = 0;
+    if (occ == 0) {
+        BBL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gram_half_kernel, kThreads, 0));
+        if (occ < 1) occ = 1;
+    }
+    const int64_t slots_max = (int64_t)std::max(1, sm_count() - kRitzReserveSMs) * occ;
+    const int nch = (int)std::max<int64_t>(1, ceil_div(n, kHalfRows));
+    const int64_t workers = std::min<int64_t>(slots_max, nch);
+    const int64_t per = (int64_t)m * 8;
+    const size_t need = sizeof(double) * (size_t)(workers * per) + 256;
+    if (partials.bytes < need) BBL_TRY(partials.alloc(need));
+    int* ticket = reinterpret_cast<int*>(partials.as<char>() + sizeof(double) * (size_t)(workers * per));
+    BBL_CUDA(cudaMemsetAsync(ticket, 0, sizeof(int), st));
+    gram_half_kernel<<<(unsigned)workers, kThreads, 0, st>>>(n, m, nch, Q, W, partials.as<double>(), ticket);
+    BBL_LAUNCH_CHECK();
+    launch_reduce(per, (int)workers, partials.as<double>(), C, st);
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
+}
+
+__global__ void f32_to_f16_kernel(int64_t count, const float* __restrict__ in, __half* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = __float2half_rn(in[e]);
+}
+
 template <typename T, int B, int CPT>
 bbl_status launch_gram(int64_t n, int m, const T* Q, const T* W, double* C, DevBuf& partials, cudaStream_t st) {
     const int64_t per = (int64_t)m * B;
@@ -1153,6 +1282,19 @@ bbl_status gram(int64_t n, int b, int nblocks, int dtype, const void* Q, const v
     if (dtype == kDF32)
         return gram_typed<df32>(n, b, m, static_cast<const df32*>(Q), static_cast<const df32*>(W), C, partials, st);
     return gram_typed<float>(n, b, m, static_cast<const float*>(Q), static_cast<const float*>(W), C, partials, st);
+}
+
+// C ~= Q16^T W for b = 8: Q16 the FP16 copy of an FP32 basis of nblocks blocks
+bbl_status gram_half(int64_t n, int nblocks, const void* Q16, const float* W, double* C, DevBuf& partials,
+                     cudaStream_t st) {
+    return launch_gram_half(n, nblocks * 8, static_cast<const __half*>(Q16), W, C, partials, st);
+}
+
+// FP16 copy (round to nearest) of count FP32 values
+bbl_status to_half(int64_t count, const float* in, void* out, cudaStream_t st) {
+    f32_to_f16_kernel<<<152 * 8, 256, 0, st>>>(count, in, static_cast<__half*>(out));
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
 }
 
 bbl_status update(int64_t n, int b, int nblocks, int dtype, const void* Q, const double* C, void* W, cudaStream_t st) {

@@ -180,6 +180,11 @@ bbl_status gram(int64_t n, int b, int nblocks, int dtype, const void* Q, const v
                 DevBuf& partials, cudaStream_t st);
 bbl_status update(int64_t n, int b, int nblocks, int dtype, const void* Q, const double* C, void* W,
                   cudaStream_t st);
+// first-pass Gram C ~= Q16^T W from the FP16 copy Q16 of an FP32 basis (b = 8)
+bbl_status gram_half(int64_t n, int nblocks, const void* Q16, const float* W, double* C, DevBuf& partials,
+                     cudaStream_t st);
+// FP16 copy (round to nearest) of count FP32 values
+bbl_status to_half(int64_t count, const float* in, void* out, cudaStream_t st);
 bbl_status ritz_vectors(int64_t n, int b, int nblocks, int dtype, const void* Q, int k, const double* S,
                         double* X, cudaStream_t st);
 bbl_status cholqr2_dev(int64_t n, int b, int dtype, void* W, double* B, double defl_abs2, int* d_ndefl,

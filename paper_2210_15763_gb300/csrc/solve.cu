@@ -309,6 +309,8 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     const size_t s = dtype_size(dtype);
     const double nrm = A->norm_inf > 0 ? A->norm_inf : 1.0;
     int J_max = std::max(1, o.max_vectors / b);
+    // FP32 blocks, b = 8: the first Gram-Schmidt pass reads an FP16 copy of the basis
+    const bool half1 = dtype == BBL_FP32 && b == 8 && o.half_first_pass != 0;
     {
         size_t freeb = 0, totalb = 0;
         BBL_CUDA(cudaMemGetInfo(&freeb, &totalb));
@@ -316,7 +318,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         BBL_CUDA(cudaGetDevice(&dev));
         freeb += pool_idle_bytes(dev);  // cached bases are available to this call
         // float-float blocks also keep an FP32 copy (first Gram-Schmidt pass)
-        const size_t per_block = (size_t)n * b * (s + (dtype == kDF32 ? sizeof(float) : 0));
+        const size_t per_block = (size_t)n * b * (s + (dtype == kDF32 ? sizeof(float) : 0) + (half1 ? 2 : 0));
         const size_t reserve = (size_t)(2ull << 30) + 8 * (size_t)n * b * 8;
         if (freeb > reserve) {
             const int fit = (int)std::min<size_t>((freeb - reserve) / per_block, (size_t)1 << 30);
@@ -334,6 +336,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     PoolBuf shadow;
     DevBuf whi;
     BBL_TRY(basis.alloc((size_t)J_max * n * b * s, st));
+    if (half1) BBL_TRY(shadow.alloc((size_t)J_max * n * b * 2, st));
     if (dtype == kDF32) {
         BBL_TRY(shadow.alloc((size_t)J_max * n * b * sizeof(float), st));
         BBL_TRY(whi.alloc((size_t)n * b * sizeof(float)));
@@ -410,7 +413,11 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     BBL_CUDA(cudaStreamSynchronize(st));
     if (h_ndefl[0] > 0) BBL_TRY(replace_deflated(0, blockp(0), d_mask));
     auto shadow_block = [&](int jb) -> bbl_status {
-        if (dtype != kDF32 || jb >= J_max) return BBL_OK;
+        if (jb >= J_max) return BBL_OK;
+        if (half1)
+            return to_half(n * b, reinterpret_cast<const float*>(blockp(jb)), shadow.as<char>() + (size_t)jb * n * b * 2,
+                           st);
+        if (dtype != kDF32) return BBL_OK;
         df32_hi_kernel<<<cg, 256, 0, st>>>(n * b, reinterpret_cast<const df32*>(blockp(jb)),
                                            shadow.as<float>() + (size_t)jb * n * b);
         BBL_LAUNCH_CHECK();
@@ -529,6 +536,10 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         // V_{j+1} there (Gram-Schmidt only reads blocks 0..j)
         if (dtype == kDF32) BBL_TRY(spmm_df32(A, b, Vj, Wn, st));
         else BBL_TRY(spmm_dispatch(A, b, Vj, Wn, f64_spmm, st));
+        // ritz_overlap = 2: the Gram-Schmidt passes wait for the Ritz solve in
+        // flight, which then shares the GPU with this SpMM only (the wait is
+        // counted in the SpMM phase)
+        if (o.ritz_overlap == 2 && pending >= 0) BBL_CUDA(cudaStreamWaitEvent(st, ev_r1[pending & 1], 0));
         BBL_CUDA(cudaEventRecord(tm.ev[1], st));
         double* C1 = coeff.as<double>();
         double* C2 = C1 + (size_t)m_max * b;
@@ -537,18 +548,21 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             df32_hi_kernel<<<cg, 256, 0, st>>>(n * b, reinterpret_cast<const df32*>(Wn), whi.as<float>());
             BBL_LAUNCH_CHECK();
             BBL_TRY(gram(n, b, j + 1, BBL_FP32, shadow.p, whi.p, C1, partials, st));
+        } else if (half1) {
+            BBL_TRY(gram_half(n, j + 1, shadow.p, reinterpret_cast<const float*>(Wn), C1, partials, st));
         } else {
             BBL_TRY(gram(n, b, j + 1, dtype, basis.p, Wn, C1, partials, st));
         }
         BBL_CUDA(cudaEventRecord(tm.ev[5], st));
         BBL_TRY(update(n, b, j + 1, dtype, basis.p, C1, Wn, st));
-        if (dtype != kDF32) {
+        const bool two_pass_A = dtype == kDF32 || half1;  // A_j from both passes' coefficients
+        if (!two_pass_A) {
             fill_A_kernel<<<1, 256, 0, st>>>(j, b, C1, Tb.as<double>());
             BBL_LAUNCH_CHECK();
         }
         BBL_TRY(gram(n, b, j + 1, dtype, basis.p, Wn, C2, partials, st));
         BBL_TRY(update(n, b, j + 1, dtype, basis.p, C2, Wn, st));
-        if (dtype == kDF32) {
+        if (two_pass_A) {
             fill_A2_kernel<<<1, 256, 0, st>>>(j, b, C1, C2, Tb.as<double>());
             BBL_LAUNCH_CHECK();
         }
@@ -564,14 +578,16 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         out.t_reorth += tm.ms(1, 2);
         out.t_chol += tm.ms(2, 3);
         out.t_gram += tm.ms(4, 5);
-        out.gram_bytes += ((double)n * (j + 1) * b + (double)n * b) * (double)s;
+        out.gram_bytes += half1 ? (double)n * (j + 1) * b * 2.0 + (double)n * b * 4.0
+                                : ((double)n * (j + 1) * b + (double)n * b) * (double)s;
         ++out.gram_calls;
         {
             const int m = (j + 1) * b;
             const double sx = (double)s;
             const double sv = (A->storage == BBL_FP64 || (dtype != kDF32 && f64_spmm && A->val64.p)) ? 8.0 : 4.0;
             out.spmm_bytes += (double)A->nnz * (sv + 4.0) + (double)(n + 1) * 8.0 + 2.0 * (double)n * b * sx;
-            out.reorth_bytes += 2.0 * (2.0 * (double)n * m * sx + 3.0 * (double)n * b * sx);
+            // two passes of Gram + update; an FP16 first-pass Gram reads 2 bytes per basis element
+            out.reorth_bytes += (half1 ? 3.5 : 4.0) * (double)n * m * sx + 6.0 * (double)n * b * sx;
         }
         out.spmm_calls = j + 1;
         const bool last = (j == J_max - 1);
@@ -636,6 +652,7 @@ bbl_status solve_impl(const bbl_matrix* A, int nev, int b, const double* pivot, 
         return set_error(BBL_ERR_INVALID_ARG, "solve: options.storage (%d) must match the matrix storage (%d)", o.storage,
                          A->storage);
     if (o.criterion != 0 && o.criterion != 1) return set_error(BBL_ERR_INVALID_ARG, "solve: bad criterion");
+    if (o.ritz_overlap < 0 || o.ritz_overlap > 2) return set_error(BBL_ERR_INVALID_ARG, "solve: ritz_overlap must be 0, 1 or 2");
     cudaStream_t st = as_stream(o.stream);
     const int64_t n = A->n;
     if (nev > n || b > n) return set_error(BBL_ERR_INVALID_ARG, "solve: nev or b larger than n");
@@ -800,6 +817,20 @@ extern "C" bbl_status bbl_pivot_rr_residual(const bbl_matrix* A, int b, const do
         for (int blk = 0; blk < kRedBlocks; ++blk) s += hp[(size_t)blk * b + i];
         resid_out[i] = std::sqrt(s);
     }
+    return BBL_OK;
+}
+
+// C = Q16^T W, b = 8: the FP16 first-pass Gram of the FP32 stage on its own.
+extern "C" bbl_status bbl_block_gram_f16(int64_t n, int nblocks, const void* basis16, const float* W, double* C,
+                                         void* stream) {
+    using namespace bbl;
+    if (n < 1 || nblocks < 1 || !basis16 || !W || !C) return set_error(BBL_ERR_INVALID_ARG, "block_gram_f16: bad arguments");
+    if (!aligned16(basis16) || !aligned16(W))
+        return set_error(BBL_ERR_INVALID_ARG, "block_gram_f16: pointers must be 16-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    DevBuf partials;
+    BBL_TRY(gram_half(n, nblocks, basis16, W, C, partials, st));
+    BBL_CUDA(cudaStreamSynchronize(st));
     return BBL_OK;
 }
 

@@ -130,6 +130,53 @@ def test_block_reorth_matches_oracle_cgs2(dtype, b, nb):
         np.testing.assert_allclose(Wg, W2, atol=2e-5 * np.abs(W0s).max())
 
 
+@pytest.mark.parametrize("n,nb", [(1024, 1), (3001, 5), (70_001, 40), (400_003, 3)])
+def test_block_gram_f16_matches_fp64_product_of_the_fp16_basis(n, nb):
+    """The FP16 first-pass Gram C = Q16^T W (b = 8) against the FP64 product
+    of the same FP16-rounded basis and FP32 W.  Products and sums over a
+    chunk in FP32 (at most 32 rows per lane, then 32 lanes), chunks in FP64:
+    entrywise |C - C_ref| <= 64 eps32 (|Q16|^T |W|).  The sizes cover one
+    exact chunk, a ragged last chunk, many blocks, and more chunks than
+    persistent CTAs (several chunks per CTA from the ticket counter)."""
+    import ctypes as C
+    torch, bbl = need_gpu()
+    from paper_2210_15763_gb300 import _lib
+    lib = _lib.load()
+    rng = np.random.default_rng(n + nb)
+    Q = (rng.standard_normal((nb, n, 8)) / np.sqrt(n)).astype(np.float16)
+    W = rng.standard_normal((n, 8)).astype(np.float32)
+    Qd = torch.from_numpy(Q).cuda()
+    Wd = torch.from_numpy(W).cuda()
+    Cd = torch.empty((nb * 8, 8), dtype=torch.float64, device="cuda")
+    st = lib.bbl_block_gram_f16(n, nb, C.c_void_p(Qd.data_ptr()), C.c_void_p(Wd.data_ptr()),
+                                C.c_void_p(Cd.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0, lib.bbl_last_error()
+    Qh = Q.astype(np.float64)
+    Wh = W.astype(np.float64)
+    ref = np.concatenate([Qh[j].T @ Wh for j in range(nb)])
+    bound = np.concatenate([np.abs(Qh[j]).T @ np.abs(Wh) for j in range(nb)])
+    assert np.all(np.abs(Cd.cpu().numpy() - ref) <= 64 * EPS32 * bound)
+
+
+def test_fp16_first_pass_keeps_the_fp32_stage_and_the_result():
+    """The FP32 stage with the FP16 first Gram-Schmidt pass (default) and with
+    two FP32 passes reach the same eigenvalues; after the polish both agree
+    to the FP64 level."""
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4", scale=0.6)
+    M = bbl.Matrix(H, storage="fp32")
+    piv = OR.normal_block(9, H.n, 8)
+    r1 = bbl.solve(M, 8, 8, pivot=piv, tol=2e-6, polish=0, max_vectors=800, half_first_pass=1)
+    r0 = bbl.solve(M, 8, 8, pivot=piv, tol=2e-6, polish=0, max_vectors=800, half_first_pass=0)
+    assert r1.converged and r0.converged
+    assert abs(r1.stats["iters"] - r0.stats["iters"]) <= 2
+    np.testing.assert_allclose(r1.evals, r0.evals, rtol=2e-6)
+    p1 = bbl.solve(M, 8, 8, pivot=piv, tol=1e-9, max_vectors=800, half_first_pass=1)
+    p0 = bbl.solve(M, 8, 8, pivot=piv, tol=1e-9, max_vectors=800, half_first_pass=0)
+    assert p1.converged and p0.converged
+    np.testing.assert_allclose(p1.evals, p0.evals, rtol=1e-11)
+
+
 @pytest.mark.parametrize("dtype", ["fp64", "fp32"])
 @pytest.mark.parametrize("b", [1, 2, 4, 6, 8, 16])
 def test_cholqr2_matches_oracle(dtype, b):
