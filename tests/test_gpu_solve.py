@@ -86,18 +86,23 @@ def test_solve_random_pivot_null_uses_the_published_generator():
 
 def test_ritz_solve_in_line_matches_the_side_stream():
     """ritz_overlap = 0 runs each Ritz solve on the caller's stream before the
-    next block; it reports the same block, eigenvalues and vectors."""
+    next block, 2 on the side stream with the next Gram-Schmidt waiting for
+    it; all report the same block, eigenvalues and vectors as the default;
+    other values are refused."""
     torch, bbl = need_gpu()
     H = synth.kron_matrix("kron_n2e4", scale=0.5)
     piv = OR.normal_block(12, H.n, 4)
     M = bbl.Matrix(H)
     r1 = bbl.solve(M, 4, 4, pivot=piv, tol=1e-9, check_every=1, ritz_overlap=1)
-    r0 = bbl.solve(M, 4, 4, pivot=piv, tol=1e-9, check_every=1, ritz_overlap=0)
-    assert r0.converged and r1.converged
-    assert r0.stats["iters"] == r1.stats["iters"]
-    np.testing.assert_allclose(r0.evals, r1.evals, rtol=1e-13)
-    X0, X1 = r0.evecs.cpu().numpy(), r1.evecs.cpu().numpy()
-    assert np.abs(X0 - X1).max() < 1e-10
+    for mode in (0, 2):
+        r0 = bbl.solve(M, 4, 4, pivot=piv, tol=1e-9, check_every=1, ritz_overlap=mode)
+        assert r0.converged and r1.converged
+        assert r0.stats["iters"] == r1.stats["iters"]
+        np.testing.assert_allclose(r0.evals, r1.evals, rtol=1e-13)
+        X0, X1 = r0.evecs.cpu().numpy(), r1.evecs.cpu().numpy()
+        assert np.abs(X0 - X1).max() < 1e-10
+    with pytest.raises(RuntimeError, match="ritz_overlap"):
+        bbl.solve(M, 4, 4, pivot=piv, tol=1e-9, ritz_overlap=3)
 
 
 def test_solve_laplacian_1d_closed_form_b1():
