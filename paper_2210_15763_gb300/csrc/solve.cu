@@ -41,19 +41,8 @@ __global__ void convert_kernel(int64_t count, const TI* __restrict__ in, TO* __r
         out[e] = (TO)in[e];
 }
 
-// A_j = sym(C1[j-block]) into the lower band of T
-__global__ void fill_A_kernel(int j, int b, const double* __restrict__ C1, double* __restrict__ Tb) {
-    const int e = threadIdx.x;
-    if (e >= b * b) return;
-    const int r = e / b, c = e % b;
-    if (c > r) return;
-    const int jb = j * b;
-    const double v = 0.5 * (C1[(int64_t)(jb + r) * b + c] + C1[(int64_t)(jb + c) * b + r]);
-    Tb[(int64_t)(jb + r) * (b + 1) + (r - c)] = v;
-}
-
-// A_j = sym(C1[j-block] + C2[j-block]): both Gram-Schmidt passes' own-block
-// coefficients (used when the first pass is computed from FP32 copies)
+// A_j = sym(C1[j-block] + C2[j-block]) into the lower band of T: both
+// Gram-Schmidt passes' own-block coefficients
 __global__ void fill_A2_kernel(int j, int b, const double* __restrict__ C1, const double* __restrict__ C2,
                                double* __restrict__ Tb) {
     const int e = threadIdx.x;
@@ -555,17 +544,13 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         }
         BBL_CUDA(cudaEventRecord(tm.ev[5], st));
         BBL_TRY(update(n, b, j + 1, dtype, basis.p, C1, Wn, st));
-        const bool two_pass_A = dtype == kDF32 || half1;  // A_j from both passes' coefficients
-        if (!two_pass_A) {
-            fill_A_kernel<<<1, 256, 0, st>>>(j, b, C1, Tb.as<double>());
-            BBL_LAUNCH_CHECK();
-        }
         BBL_TRY(gram(n, b, j + 1, dtype, basis.p, Wn, C2, partials, st));
         BBL_TRY(update(n, b, j + 1, dtype, basis.p, C2, Wn, st));
-        if (two_pass_A) {
-            fill_A2_kernel<<<1, 256, 0, st>>>(j, b, C1, C2, Tb.as<double>());
-            BBL_LAUNCH_CHECK();
-        }
+        // A_j = sym(C1 + C2)[j-block]: the second pass's own-block coefficients
+        // are the rounding (or, from a cheaper first pass, the approximation)
+        // the first left in A_j
+        fill_A2_kernel<<<1, 256, 0, st>>>(j, b, C1, C2, Tb.as<double>());
+        BBL_LAUNCH_CHECK();
         BBL_CUDA(cudaEventRecord(tm.ev[2], st));
         BBL_TRY(cholqr2_dev(n, b, dtype, Wn, bj.as<double>(), thresh2, d_ndefl, d_mask, partials, small, st));
         fill_B_kernel<<<1, 256, 0, st>>>(j, b, t_rows, bj.as<double>(), Tb.as<double>());
