@@ -139,7 +139,9 @@ uint64_t bbl_kernel_launches(void);
 /* Workspace cache.  The Lanczos bases (bbl_solve, bbl_pivot_bootstrap,
  * bbl_batch_solve) are device allocations of up to max_vectors * n * s bytes;
  * when a call ends they stay reserved for the next call on the same device
- * instead of being freed (an allocation plus free of 16 GB costs about 10 ms).
+ * instead of being freed (an allocation plus free of 16 GB costs about 10 ms);
+ * a later request reuses an idle buffer of at least its size and at most
+ * 1/16 more (repeated solves of one size reuse theirs exactly).
  * Reuse is ordered by an event on the stream that last used the memory, so
  * calls on different streams may share the cache.  A call whose allocation
  * fails frees the idle buffers and tries once more before reporting

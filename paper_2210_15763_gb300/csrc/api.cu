@@ -70,10 +70,14 @@ bbl_status PoolBuf::alloc(size_t nbytes, cudaStream_t stream) {
     int d = 0;
     BBL_CUDA(cudaGetDevice(&d));
     std::lock_guard<std::mutex> lk(g_pool_mu);
+    // reuse only a buffer at most 1/16 larger than the request: a much larger
+    // one would strand its excess while other idle memory is counted as free
     int best = -1;
     for (size_t i = 0; i < g_idle.size(); ++i) {
         const IdleBuf& e = g_idle[i];
-        if (e.dev == d && e.bytes >= nbytes && (best < 0 || e.bytes < g_idle[(size_t)best].bytes)) best = (int)i;
+        if (e.dev == d && e.bytes >= nbytes && e.bytes - nbytes <= nbytes / 16 &&
+            (best < 0 || e.bytes < g_idle[(size_t)best].bytes))
+            best = (int)i;
     }
     if (best >= 0) {
         const IdleBuf e = g_idle[(size_t)best];

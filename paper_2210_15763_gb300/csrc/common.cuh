@@ -94,8 +94,9 @@ struct DevBuf {
 // Large scratch kept across calls (the Lanczos bases): release() hands the
 // allocation to a per-device idle list with an event recorded on the stream
 // it was used on; alloc() takes the smallest idle allocation of this device
-// that is large enough and makes its own stream wait on that event, so reuse
-// is ordered on the GPU without a host synchronisation.  When cudaMalloc runs
+// that is large enough but at most 1/16 larger, and makes its own stream
+// wait on that event, so reuse is ordered on the GPU without a host
+// synchronisation.  When cudaMalloc runs
 // out of memory the idle allocations of the device are freed and it is tried
 // once more.  bbl_workspace_release() frees every idle allocation.
 struct PoolBuf {
