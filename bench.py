@@ -441,7 +441,9 @@ def run_kernels(args):
         Tb[d:, d] = rng.standard_normal(mT - d)
     Td = torch.from_numpy(Tb).cuda()
     t = timeit(lambda: bbl.ritz_banded(Td, NEV), max(1, args.reps // 2))
-    out["ritz_banded"] = {"ms": t, "m": mT, "p": p, "nev": NEV}
+    out["ritz_banded"] = {"ms": t, "m": mT, "p": p, "nev": NEV,
+                          "matrix": "random N(0,1) band: a dense spectrum, a stress case for bisection and the "
+                                    "cluster step (Lanczos T_j has separated lowest eigenvalues)"}
     print(json.dumps(out))
 
 

@@ -281,7 +281,9 @@ bbl_status bbl_pivot_random(int64_t n, int b, uint64_t seed, double* P, void* st
  * rows with the smallest H_ii (ties: lower index), eigenvectors of the
  * lowest b eigenvalues of H[S,S] (block Lanczos on the GPU to sub_tol, or a
  * dense solve when trunc_dim <= b), zero-padded into P (device FP64 n x b
- * row-major).  If b > trunc_dim the remaining columns are random.       */
+ * row-major).  If b > trunc_dim the remaining columns are random.  The
+ * sub-solve keeps A's FP32 values in FP32 storage (FP32 stage, no polish)
+ * when A is stored in FP32 and sub_tol >= 1e-5, else it runs in FP64.    */
 bbl_status bbl_pivot_bootstrap(const bbl_matrix* A, int64_t trunc_dim, int b, double sub_tol, uint64_t seed,
                                double* P, void* stream);
 

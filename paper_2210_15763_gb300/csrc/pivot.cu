@@ -274,15 +274,21 @@ extern "C" bbl_status bbl_pivot_bootstrap(const bbl_matrix* A, int64_t trunc_dim
                 srp.as<int64_t>(), sci.as<int>(), sva.as<double>());
         BBL_LAUNCH_CHECK();
         BBL_CUDA(cudaStreamSynchronize(st));
-        // 4. lowest b eigenpairs of H[S,S]
+        // 4. lowest b eigenpairs of H[S,S]: a sub-solve to sub_tol >= 1e-5 from
+        // FP32 values runs in FP32 storage without the polish (its tolerance is
+        // far above the FP32 stage's floor, and FP64 arithmetic runs at 1/64 of
+        // the FP32 rate), tighter ones in FP64
+        const bool sub32 = A->storage == BBL_FP32 && sub_tol >= 1e-5;
         bbl_matrix* sub = nullptr;
-        BBL_TRY(bbl_matrix_create(k, acc, srp.as<int64_t>(), sci.as<int>(), sva.p, BBL_FP64, BBL_FP64, BBL_CSR, 0, 0, 0,
-                                  stream, &sub));
+        BBL_TRY(bbl_matrix_create(k, acc, srp.as<int64_t>(), sci.as<int>(), sva.p, BBL_FP64, sub32 ? BBL_FP32 : BBL_FP64,
+                                  BBL_CSR, 0, 0, 0, stream, &sub));
         bbl_options o;
         bbl_options_default(&o);
         o.tol = sub_tol;
         o.seed = seed;
         o.stream = stream;
+        o.storage = sub32 ? BBL_FP32 : BBL_FP64;
+        o.polish = 0;
         const int bs = (int)std::min<int64_t>(b, k);
         o.max_vectors = (int)std::min<int64_t>((k / bs) * bs, 2000);
         DevBuf Y;

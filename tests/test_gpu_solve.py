@@ -208,6 +208,31 @@ def test_bootstrap_pivot_matches_oracle_subspace():
     assert principal_angle_sin(Qg, Po) < 1e-6
 
 
+def test_bootstrap_fp32_sub_solve_gives_an_equally_good_pivot():
+    """From an FP32-stored matrix a sub-solve to sub_tol >= 1e-5 runs in FP32:
+    its pivot lies in the same truncated space, its Rayleigh-Ritz values on
+    H match the FP64 sub-solve's to the sub-solve tolerance, and the main
+    solve from it takes the same number of blocks (+-2)."""
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4", scale=0.6, fp32_values=True)
+    trunc = 1500
+    M32 = bbl.Matrix(H, storage="fp32")
+    M64 = bbl.Matrix(H)
+    S = set(OP.truncated_set(H.diagonal(), trunc).tolist())
+    P32 = bbl.pivot_bootstrap(M32, trunc, 8, sub_tol=1e-4)
+    P64 = bbl.pivot_bootstrap(M64, trunc, 8, sub_tol=1e-4)
+    assert set(np.nonzero(np.abs(P32.cpu().numpy()).sum(axis=1))[0]) <= S
+    th32, _ = bbl.pivot_rr_residual(M64, P32)
+    th64, _ = bbl.pivot_rr_residual(M64, P64)
+    nrm = np.abs(H.to_scipy()).sum(axis=1).max()
+    np.testing.assert_allclose(th32, th64, rtol=0, atol=1e-4 * nrm)
+    r32 = bbl.solve(M32, 8, 8, pivot=P32, tol=1e-8, max_vectors=1200, check_every=1)
+    r64 = bbl.solve(M32, 8, 8, pivot=P64, tol=1e-8, max_vectors=1200, check_every=1)
+    assert r32.converged and r64.converged
+    assert abs(r32.stats["iters"] - r64.stats["iters"]) <= 2
+    np.testing.assert_allclose(r32.evals, r64.evals, rtol=1e-11)
+
+
 def test_bootstrap_pivot_full_space_gives_one_block():
     torch, bbl = need_gpu()
     A = synth.random_sparse_symmetric(200, 6, seed=8)
