@@ -45,7 +45,8 @@ struct IdleBuf {
     cudaEvent_t ready;  // recorded on the last stream that used it
 };
 std::mutex g_pool_mu;
-std::vector<IdleBuf> g_idle;
+std::vector<IdleBuf> g_idle;  // oldest first
+constexpr int kPoolIdleMax = 8;
 
 // frees the idle buffers of device dev; the caller holds g_pool_mu and has
 // dev current
@@ -117,6 +118,19 @@ void PoolBuf::release() {
     if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess && cudaEventRecord(ev, st) == cudaSuccess) {
         std::lock_guard<std::mutex> lk(g_pool_mu);
         g_idle.push_back(IdleBuf{p, bytes, dev, ev});
+        int held = 0;
+        for (const IdleBuf& e : g_idle) held += e.dev == dev;
+        for (size_t i = 0; i < g_idle.size() && held > kPoolIdleMax;) {
+            if (g_idle[i].dev == dev) {  // the oldest of this device (dev is current: it was allocated here)
+                cudaEventSynchronize(g_idle[i].ready);
+                cudaEventDestroy(g_idle[i].ready);
+                cudaFree(g_idle[i].p);
+                g_idle.erase(g_idle.begin() + (std::ptrdiff_t)i);
+                --held;
+            } else {
+                ++i;
+            }
+        }
     } else {
         // reuse cannot be ordered: give it back (cudaFree waits for the device)
         if (ev) cudaEventDestroy(ev);
@@ -125,6 +139,18 @@ void PoolBuf::release() {
     }
     p = nullptr;
     bytes = 0;
+}
+
+bool pool_free_idle_current_device() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    size_t before = g_idle.size();
+    free_idle_locked(d);
+    return g_idle.size() != before;
 }
 
 size_t pool_idle_bytes(int dev) {

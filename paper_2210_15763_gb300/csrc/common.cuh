@@ -61,6 +61,10 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // Is p device-accessible memory the kernels may read directly?
 bool is_device_pointer(const void* p);
 
+// Frees the workspace cache's idle buffers on the current device (see
+// PoolBuf); true if there were any.
+bool pool_free_idle_current_device();
+
 // ------------------------------------------------------------------ device buffers
 // Owning device allocation; frees on destruction.
 struct DevBuf {
@@ -79,6 +83,10 @@ struct DevBuf {
         release();
         if (nbytes == 0) nbytes = 16;
         cudaError_t e = cudaMalloc(&p, nbytes);
+        if (e == cudaErrorMemoryAllocation && pool_free_idle_current_device()) {  // cached bases back, once more
+            (void)cudaGetLastError();
+            e = cudaMalloc(&p, nbytes);
+        }
         if (e != cudaSuccess) {
             p = nullptr;
             (void)cudaGetLastError();
@@ -96,9 +104,10 @@ struct DevBuf {
 // it was used on; alloc() takes the smallest idle allocation of this device
 // that is large enough but at most 1/16 larger, and makes its own stream
 // wait on that event, so reuse is ordered on the GPU without a host
-// synchronisation.  When cudaMalloc runs
-// out of memory the idle allocations of the device are freed and it is tried
-// once more.  bbl_workspace_release() frees every idle allocation.
+// synchronisation.  When cudaMalloc (here or in DevBuf) runs out of memory
+// the idle allocations of the device are freed and it is tried once more;
+// at most kPoolIdleMax allocations per device stay idle (the oldest goes).
+// bbl_workspace_release() frees every idle allocation.
 struct PoolBuf {
     void* p = nullptr;
     size_t bytes = 0;  // capacity
