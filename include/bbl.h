@@ -209,8 +209,10 @@ bbl_status bbl_block_reorth(int64_t n, int b, int nblocks, bbl_dtype dtype, cons
 bbl_status bbl_block_gram(int64_t n, int b, int nblocks, bbl_dtype dtype, const void* basis, const void* W,
                           double* C, void* stream);
 
-/* C ~= Q16^T W for b = 8, the first Gram-Schmidt pass of the FP32 stage
- * (bbl_options.half_first_pass): Q16 the FP16 copy of an FP32 basis.
+/* C ~= Q16^T W for b = 8: the Gram step of the first of the two classical
+ * Gram-Schmidt passes of the full reorthogonalisation (Sec. II.A, Eqs. 7-8)
+ * in the FP32 stage (bbl_options.half_first_pass), from Q16, the FP16 copy
+ * of an FP32 basis; the FP32 second pass removes what its rounding leaves.
  *   basis16 device FP16, nblocks consecutive n x 8 row-major blocks
  *   W       device FP32 n x 8 (not modified)
  *   C       device FP64 (nblocks*8) x 8 row-major
