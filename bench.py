@@ -161,6 +161,12 @@ def oracle_sample(A, iters_gpu: int, budget_blocks: int = 3):
     return float(est), float(time.perf_counter() - t_start), 1
 
 
+def workload_name(A) -> str:
+    """The workload both arms report in config.workload."""
+    return (f"{WORKLOAD}: Kronecker H=Hp(x)I+I(x)Hn+sum_12 Cp(x)Cn, n={A.n}, nnz={A.nnz}, b={B}, nev={NEV}, "
+            f"tol={TOL}")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -177,8 +183,9 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD} (n=2e6, nnz={A.nnz}, b={B}, nev={NEV}, tol={TOL})",
-                   "oracle": "numpy/scipy FP64 block Lanczos"},
+        "config": {"workload": workload_name(A),
+                   "method": "the oracle: numpy/scipy FP64 block Lanczos (CGS2, CholQR2, LAPACK Ritz solve)",
+                   "parallelism": "host cores"},
         "cpu_baseline": {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"the oracle's steps timed once each at full size (SpMM, Gram-Schmidt passes "
                                    f"at two basis sizes, CholQR2, dense eigensolve) and composed into a {iters}-block run"},
@@ -357,11 +364,12 @@ def run_ours(args):
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: Kronecker H=Hp(x)I+I(x)Hn+sum_12 Cp(x)Cn, n={A.n}, nnz={A.nnz}, "
-                               f"b={B}, nev={NEV}, tol={TOL}, bootstrap trunc_dim={TRUNC} sub_tol={args.sub_tol:g}, FP32 stage "
-                               f"({sched['fmt']}, lanes {sched['lanes']}, sigma {sched['sigma']}"
-                               f"{'' if args.stage1_tol is None else f', to {args.stage1_tol:g}'}) + float-float polish, "
-                               f"FP64 residuals",
+        "config": {"workload": workload_name(A),
+                   "method": f"bootstrap trunc_dim={TRUNC} sub_tol={args.sub_tol:g}, FP32 stage "
+                             f"({sched['fmt']}, lanes {sched['lanes']}, sigma {sched['sigma']}"
+                             f"{'' if args.stage1_tol is None else f', to {args.stage1_tol:g}'}"
+                             f"{', FP16 first-pass Gram' if args.half_first_pass else ''}) + float-float polish, "
+                             f"FP64 residuals",
                    "parallelism": "replicas only" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (matrix 4.8 GB)"},
         "converged": ok, "max_resid_rel": resid_rel,
