@@ -292,7 +292,7 @@ bbl_status bbl_pivot_bootstrap(const bbl_matrix* A, int64_t trunc_dim, int b, do
 /* Rayleigh-Ritz on the span of a pivot block P (host or device FP64 n x b):
  * Q = orth(P), the b Ritz values of Q^T H Q (theta, host, ascending) and the
  * residual norms ||H Q s_i - theta_i Q s_i||_2 (resid, host).  This is the
- * cheap one-SpMM judge used to choose between a learned and a bootstrapped
+ * cheap one-SpMM test used to choose between a learned and a bootstrapped
  * pivot (the paper's Sec. II.B condition: the pivot must overlap the wanted
  * eigenvectors).                                                          */
 bbl_status bbl_pivot_rr_residual(const bbl_matrix* A, int b, const double* P, double* theta, double* resid,

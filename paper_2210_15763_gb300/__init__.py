@@ -232,7 +232,7 @@ def block_gram_f16(basis16, W, stream=None):
 
 
 def pivot_rr_residual(A: Matrix, P, stream=None):
-    """Rayleigh-Ritz values and residual norms of span(P) (the pivot judge)."""
+    """Rayleigh-Ritz values and residual norms of span(P) (the test that chooses a pivot)."""
     b = P.shape[1]
     th = np.zeros(b)
     rs = np.zeros(b)

@@ -6,7 +6,7 @@ eigenvectors X(g).  The eigenvectors at `n_basis_g` evenly spaced training
 values are orthonormalised block by block (CGS2 + CholQR2 on the GPU) into
 the stored basis U (FP32, nbasis = n_basis_g * nev columns).  The network
 is trained to map g to the coefficients C(g) = U^T X(g) (FP64 Gram on the
-GPU).  At inference P = U f(g); Lanczos remains the judge: the learned pivot
+GPU).  At inference P = U f(g); Lanczos still decides: the learned pivot
 is used only if the Rayleigh-Ritz residual of its span is below that of
 every bootstrapped pivot seen in training (else the bootstrapped pivot is
 built and the better of the two taken), and a solve that does not converge
@@ -89,7 +89,7 @@ def fit(make_matrix, g_train, nev: int, b: int, trunc_dim: int, n_basis_g: int =
 
 
 def choose_pivot(A: Matrix, P_learned, P_boot, nev: int):
-    """Lanczos judges: keep the learned pivot only if the Rayleigh-Ritz residual
+    """Lanczos decides: keep the learned pivot only if the Rayleigh-Ritz residual
     of its span (max over the nev lowest pairs) is not worse than the bootstrap's."""
     _, rl = pivot_rr_residual(A, P_learned)
     _, rb = pivot_rr_residual(A, P_boot)
@@ -100,7 +100,7 @@ def choose_pivot(A: Matrix, P_learned, P_boot, nev: int):
 
 def solve_with_learned_pivot(A: Matrix, lp: LearnedPivot, g: float, b: int, trunc_dim: int, tol: float = 1e-8,
                              seed: int = 0):
-    """Lanczos judges the learned pivot.  When its Rayleigh-Ritz residual is
+    """Lanczos decides on the learned pivot.  When its Rayleigh-Ritz residual is
     below every bootstrapped pivot's seen in training, it is used at once;
     otherwise the bootstrapped pivot is built and the better of the two is
     taken.  A solve from the learned pivot that does not converge is redone
