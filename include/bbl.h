@@ -228,7 +228,9 @@ bbl_status bbl_block_gram_f16(int64_t n, int nblocks, const void* basis16, const
  * cudaFree or allocating library routine: the per-chunk partial sums live in
  * a fixed 8 MiB file-scope device array that every device loading the
  * library holds until the process exits.
- *   Limit: nblocks*b*b <= 2^20 - 64 (otherwise BBL_ERR_INVALID_ARG with a message);
+ *   Limit: nblocks*b*b <= 2^20 - 2048 (otherwise BBL_ERR_INVALID_ARG with a
+ *   message): the array holds 2048 doubles of chunk tickets (one int per
+ *   group of up to 256 columns) ahead of the partial sums.
  *   b in {1, 2, 4, 8, 16}.  Arguments and layouts as in bbl_block_gram.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call

@@ -698,15 +698,29 @@ int sm_count() {
     return n;
 }
 
+// Column groups of the split-K Gram for m basis columns: each thread of a
+// CTA owns CPT columns, so a group covers up to kThreads * CPT columns, and
+// each group has its own chunk ticket.
+template <int CPT>
+int gram_groups(int m) {
+    const int cols = (m + CPT - 1) / CPT;
+    return (cols + kThreads - 1) / kThreads;
+}
+
 // Launches the persistent split-K Gram and the reduction of its per-worker
-// partials.  partial: room for `cap` doubles; tickets: gy ints (zeroed here).
+// partials.  partial: room for `cap` doubles; tickets: room for `ticket_cap`
+// ints, of which gram_groups<CPT>(m) are zeroed here and used (a request
+// needing more is refused before any launch).
 template <typename T, int B, int CPT>
 bbl_status gram_core(int64_t n, int m, const T* Q, const T* W, double* C, double* partial, int64_t cap, int* tickets,
-                     cudaStream_t st) {
+                     int64_t ticket_cap, cudaStream_t st) {
     int cols = (m + CPT - 1) / CPT;
     int TC = 1;
     while (TC < cols && TC < kThreads) TC <<= 1;
     const int gy = (cols + TC - 1) / TC;
+    if (gy != gram_groups<CPT>(m) || gy > ticket_cap)
+        return set_error(BBL_ERR_INVALID_ARG, "gram: %d column groups exceed the %lld chunk tickets", gy,
+                         (long long)ticket_cap);
     const int RS = kThreads / TC;
     // FP32 data keeps its FP64 running sums in shared memory; FP64 data needs
     // the buffer only for the reduction over row slots
@@ -905,10 +919,13 @@ template <typename T, int B, int CPT>
 bbl_status launch_gram(int64_t n, int m, const T* Q, const T* W, double* C, DevBuf& partials, cudaStream_t st) {
     const int64_t per = (int64_t)m * B;
     const int64_t cap = per * (int64_t)sm_count() * 8;        // enough for any occupancy
-    const size_t need = sizeof(double) * (size_t)cap + 4096;   // + tickets
+    const int64_t gy = gram_groups<CPT>(m);                   // one ticket per column group
+    const size_t ticket_bytes = 256 * (size_t)ceil_div(gy * (int64_t)sizeof(int), 256);
+    const size_t need = sizeof(double) * (size_t)cap + ticket_bytes;
     if (partials.bytes < need) BBL_TRY(partials.alloc(need));
     int* tickets = reinterpret_cast<int*>(partials.as<char>() + sizeof(double) * (size_t)cap);
-    return gram_core<T, B, CPT>(n, m, Q, W, C, partials.as<double>(), cap, tickets, st);
+    return gram_core<T, B, CPT>(n, m, Q, W, C, partials.as<double>(), cap, tickets,
+                                (int64_t)(ticket_bytes / sizeof(int)), st);
 }
 
 template <typename T>
@@ -1675,7 +1692,13 @@ bbl_status bbl_ritz_vectors(int64_t n, int b, int nblocks, bbl_dtype dtype, cons
 namespace bbl {
 namespace {
 
-constexpr int64_t kNoAllocScratchDoubles = int64_t(1) << 20;  // 8 MiB of FP64 partial sums
+constexpr int64_t kNoAllocScratchDoubles = int64_t(1) << 20;  // 8 MiB: chunk tickets + FP64 partial sums
+// The front of the array holds one chunk ticket (int) per column group of the
+// Gram.  2048 doubles hold 4096 tickets, more than any request within the
+// limit below needs (b = 1: m <= 2^20 - 2048 columns in groups of 256 give at
+// most 4088; larger b have fewer groups); the rest holds the partial sums.
+constexpr int64_t kNoAllocTicketDoubles = 2048;
+constexpr int64_t kNoAllocPartialDoubles = kNoAllocScratchDoubles - kNoAllocTicketDoubles;
 __device__ __align__(256) double g_noalloc_gram_scratch[kNoAllocScratchDoubles];
 
 constexpr int kMaxDevices = 64;
@@ -1703,15 +1726,16 @@ bbl_status noalloc_scratch(double** out) {
 
 template <typename T, int B, int CPT>
 bbl_status launch_gram_fixed(int64_t n, int m, const T* Q, const T* W, double* C, double* scratch, cudaStream_t st) {
-    // the first 64 doubles of the array hold the chunk tickets (zeroed by
-    // every call), the rest the per-worker partial sums
-    const int64_t per_chunk = (int64_t)m * B;
-    if (per_chunk > kNoAllocScratchDoubles - 64)
+    // the front of the array holds the chunk tickets (the ones a call uses
+    // are zeroed by that call), the rest the per-worker partial sums
+    const int64_t per_worker = (int64_t)m * B;
+    if (per_worker > kNoAllocPartialDoubles)
         return set_error(BBL_ERR_INVALID_ARG,
                          "block_gram_noalloc: nblocks*b*b = %lld exceeds the fixed scratch of %lld doubles",
-                         (long long)per_chunk, (long long)(kNoAllocScratchDoubles - 64));
-    return gram_core<T, B, CPT>(n, m, Q, W, C, scratch + 64, kNoAllocScratchDoubles - 64,
-                                reinterpret_cast<int*>(scratch), st);
+                         (long long)per_worker, (long long)kNoAllocPartialDoubles);
+    return gram_core<T, B, CPT>(n, m, Q, W, C, scratch + kNoAllocTicketDoubles, kNoAllocPartialDoubles,
+                                reinterpret_cast<int*>(scratch),
+                                kNoAllocTicketDoubles * (int64_t)(sizeof(double) / sizeof(int)), st);
 }
 
 template <typename T>
