@@ -28,7 +28,9 @@ Readings of garbled or silent passages (each also listed in the design notes):
   * Breakdown / near-singular overlap ("easy to locate and remove", Sec. II.B):
     a column whose orthogonal part has norm below defl_tol * ||H||_inf is
     replaced by a splitmix64 uniform vector orthogonalised against the basis,
-    and the matching part of B_n is set to zero.
+    and the matching part of B_n is set to zero.  In the spectral normaliser
+    an eigenvalue of the overlap O also counts as near-singular at or below
+    1e-14 times O's largest (the eigensolve of O resolves no finer).
 """
 from __future__ import annotations
 
@@ -40,6 +42,9 @@ from . import rng as _rng
 from .spmm import norm_inf, spmm
 
 DEFLATION_SEED_XOR = 0x5DEECE66D
+# eigenvalues of the overlap matrix O (Eq. 9) below this fraction of its
+# largest are numerically zero (about 50 times the FP64 machine epsilon)
+NEAR_SINGULAR_REL = 1e-14
 
 
 # --------------------------------------------------------------------------
@@ -121,17 +126,22 @@ def cholqr2(W: np.ndarray, thresh2: float, basis: np.ndarray | None = None, repl
 
 def spectral_normalise(W: np.ndarray, thresh2: float, basis: np.ndarray | None = None, replace=None):
     """The paper's normaliser (Eqs. 9-11): O = W'^T W' = U Lambda U^T,
-    B = Lambda^{1/2} U^T, V_{n+1} = W' U Lambda^{-1/2}; eigenvalues of O at or
-    below thresh2 are removed (their rows of B are zero and their columns of
-    V_{n+1} are replaced by vectors orthogonal to everything else)."""
+    B = Lambda^{1/2} U^T, V_{n+1} = W' U Lambda^{-1/2}; near-singular
+    eigenvalues of O (Sec. II.B) are removed: their rows of B are zero and
+    their columns of V_{n+1} are replaced by vectors orthogonal to everything
+    else.  An eigenvalue counts as near-singular at or below thresh2, or at or
+    below NEAR_SINGULAR_REL * lambda_max: the eigenvalues of O are only known
+    to about machine epsilon times lambda_max, so a direction that W' lacks
+    exactly can come out of the eigensolve anywhere below that level."""
     O = W.T @ W                                   # Eq. 9
     lam, U = np.linalg.eigh(O)
     b = W.shape[1]
     B = np.zeros((b, b))
     V = np.zeros_like(W)
     removed = []
+    cut = max(thresh2, NEAR_SINGULAR_REL * max(float(lam[-1]), 0.0))
     for c in range(b):
-        if lam[c] > thresh2:
+        if lam[c] > cut:
             B[c, :] = np.sqrt(lam[c]) * U[:, c]       # Eq. 10 read as Lambda^{1/2} U^T
             V[:, c] = (W @ U[:, c]) / np.sqrt(lam[c])  # Eq. 11
         else:

@@ -194,6 +194,49 @@ def test_cholqr2_deflates_dependent_column():
     assert np.allclose(np.tril(B, -1), 0.0)
 
 
+def test_spectral_normalise_deflates_dependent_column():
+    """Eqs. 9-11 with a near-singular overlap (Sec. II.B: such directions are
+    removed): an exactly dependent column of W' gives one zero eigenvalue of
+    O = W'^T W'; its row of B is zero, its column of V_{n+1} is a unit vector
+    orthogonal to the basis and to the kept columns, and V_{n+1} B = W' still
+    holds because W' has no component along the removed direction."""
+    rng = np.random.default_rng(4)
+    basis, _ = np.linalg.qr(rng.standard_normal((300, 5)))
+    W = rng.standard_normal((300, 4))
+    W -= basis @ (basis.T @ W)
+    W[:, 2] = 2.0 * W[:, 0] - W[:, 1]          # exactly dependent column
+    V, B, removed = L.spectral_normalise(W, 1e-20, basis, lambda i: L.deflation_vector(0, 1, i, 300))
+    assert removed == [0]                      # eigh orders the overlap's eigenvalues ascending
+    assert np.max(np.abs(V.T @ V - np.eye(4))) < 1e-13
+    assert np.max(np.abs(basis.T @ V)) < 1e-13
+    assert np.all(B[0] == 0.0)
+    np.testing.assert_allclose(V @ B, W, atol=1e-12)
+    np.testing.assert_allclose(B.T @ B, W.T @ W, atol=1e-11)   # Eq. 10 read as Lambda^{1/2} U^T
+    # the kept columns span exactly the column space of W'
+    P = V[:, 1:] @ V[:, 1:].T
+    np.testing.assert_allclose(P @ W, W, atol=1e-12)
+
+
+@pytest.mark.parametrize("normaliser", ["spectral", "cholqr2"])
+def test_block_lanczos_deflation_branch_reaches_the_dense_spectrum(normaliser):
+    """A pivot holding an exact eigenvector: its column of W' vanishes after
+    the reorthogonalisation of the first block, so both normalisers take
+    their deflation branch there (a replacement direction enters the Krylov
+    space), and both still converge to the dense eigenvalues."""
+    A = synth.random_sparse_symmetric(150, 6, seed=21)
+    w, U = np.linalg.eigh(A.to_dense())
+    piv = R.normal_block(8, A.n, 4)
+    piv[:, 0] = U[:, 0]
+    r = L.block_lanczos(A, 4, 4, piv, tol=1e-11, max_vectors=150, normaliser=normaliser)
+    assert r.deflations >= 1
+    assert r.converged
+    np.testing.assert_allclose(r.evals, w[:4], rtol=1e-10)
+    # with a deflation the method has the same Ritz values under either normaliser
+    other = L.block_lanczos(A, 4, 4, piv, tol=1e-11, max_vectors=150,
+                            normaliser="cholqr2" if normaliser == "spectral" else "spectral")
+    np.testing.assert_allclose(r.evals, other.evals, rtol=1e-10)
+
+
 def test_block_tridiagonal_layout():
     A = [np.full((2, 2), 1.0), np.full((2, 2), 2.0)]
     B = [np.array([[3.0, 4.0], [0.0, 5.0]])]
