@@ -69,6 +69,30 @@ def test_fullsize_mixed_precision_matches_oracle(kron_n2e6):
     assert rel.max() <= 1e-6, rel
 
 
+@pytest.mark.parametrize("fmt,sigma", [("sell", 1024), ("csr", 0)])
+def test_fullsize_headline_step_matches_oracle(kron_n2e6, fmt, sigma):
+    """The benchmark's timed step exactly: the bootstrapped pivot (20,000
+    lowest-diagonal rows, truncated-space sub-solve to 1e-4 in FP32 storage),
+    the FP32 stage to 3e-7 with the FP16 first-pass Gram, the float-float
+    polish and the FP64 residuals, on the FP32-stored matrix in either format
+    the SpMM autotuner may pick (SELL-C-sigma with sigma = 1024, or CSR).
+    The eight eigenvalues agree with the FP64 oracle's to relative 1e-10."""
+    import bench
+    torch, bbl = need_gpu()
+    ref = _golden("kron_n2e6")
+    A = kron_n2e6
+    M = bbl.Matrix(A, storage="fp32", fmt=fmt, sell_sigma=sigma)
+    P = bench.headline_pivot(bbl, M)
+    r = bench.headline_solve(bbl, M, P, evecs=None)
+    M.close()
+    assert r.converged
+    rel = np.abs(r.evals - np.array(ref["evals"])) / np.abs(ref["evals"])
+    print(f"headline step ({fmt}) relative eigenvalue errors vs the FP64 oracle:", " ".join(f"{x:.2e}" for x in rel))
+    assert rel.max() <= 1e-10, rel
+    assert bench.oracle_eval_error(r.evals) == pytest.approx(rel.max())
+    assert np.all(r.resid <= ref["tol"] * ref["norm_inf"] * 1.01)
+
+
 def test_fullsize_c3_family_mixed_precision_error_table():
     """The ~200 nonzeros-per-row family (K = 12, c = 3.9) at n = 2e6: the
     FP32 stage's per-eigenvalue error against the FP64 oracle (<= 1e-6) and

@@ -30,7 +30,7 @@ def _check_eigs(res, ref_evals, H, tol, rel=1e-10):
     return X
 
 
-@pytest.mark.parametrize("b", [1, 2, 4, 8])
+@pytest.mark.parametrize("b", [1, 2, 4, 8, 16])
 def test_solve_fp64_kron_small_vs_oracle(b):
     torch, bbl = need_gpu()
     H = synth.kron_matrix("kron_n2e4", scale=0.3)  # n = 60 x 30
@@ -182,6 +182,20 @@ def test_float_float_polish_agrees_with_fp64_polish(fmt):
     np.testing.assert_allclose(r1.evals, r2.evals, rtol=1e-12)
     assert r1.stats["iters"] == r2.stats["iters"]
     assert abs(r1.stats["polish_iters"] - r2.stats["polish_iters"]) <= 1
+
+
+@pytest.mark.parametrize("nev", [8, 16])
+def test_solve_mixed_precision_b16_matches_fp64_oracle(nev):
+    """Block size 16 in the mixed-precision form (FP32 stage + float-float
+    polish) against the oracle's block Lanczos at b = 16."""
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4", scale=0.5)
+    piv = OR.normal_block(17, H.n, 16)
+    ref = OL.block_lanczos(H, nev, 16, piv, tol=1e-8)
+    M = bbl.Matrix(H, storage="fp32", fmt="sell", sell_sigma=256)
+    res = bbl.solve(M, nev, 16, pivot=piv, tol=1e-8)
+    assert res.converged
+    _check_eigs(res, ref.evals, H, 1e-8)
 
 
 def test_solve_mixed_precision_stage1_error_below_1e6():
