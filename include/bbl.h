@@ -51,7 +51,7 @@ typedef enum {
 } bbl_status;
 
 typedef enum { BBL_FP64 = 0, BBL_FP32 = 1 } bbl_dtype;
-typedef enum { BBL_CSR = 0, BBL_SELL = 1 } bbl_format;
+typedef enum { BBL_CSR = 0, BBL_SELL = 1, BBL_KRON = 2 } bbl_format;
 
 typedef struct bbl_matrix bbl_matrix;   /* opaque, library-owned device copy of H */
 
@@ -176,6 +176,36 @@ void bbl_matrix_destroy(bbl_matrix* A);
 /* n, nnz, ||H||_inf, device bytes held, stored format and precision.  Any output may be NULL. */
 bbl_status bbl_matrix_info(const bbl_matrix* A, int64_t* n, int64_t* nnz, double* norm_inf,
                            int64_t* device_bytes, int* fmt, int* storage, int64_t* padded_nnz);
+
+/* A matrix kept as Kronecker factors (fmt BBL_KRON) and applied without
+ * storing its entries: the paper's on-the-fly rebuilding of the matrix
+ * elements from factors shared by every vector of a block (Sec. I,
+ * Sec. III.A, Appendix A), for
+ *     H = Hp (x) I_nN + I_nP (x) Hn + sum_{k<K} Cp_k (x) Cn_k,
+ * row r = p*nN + q, (A (x) B)[p*nN+q, p'*nN+q'] = A[p,p'] B[q,q'].
+ * Factors (host or device arrays, copied): 2 + 2K square CSR matrices in
+ * the order Hp, Hn, Cp_0, Cn_0, ..., Cp_{K-1}, Cn_{K-1} (Hp, Cp_k: nP x nP;
+ * Hn, Cn_k: nN x nN), packed into fptr (int32 row pointers, factor f's
+ * nP+1 or nN+1 of them from ptr_off[f], each starting at 0), fcol (int32,
+ * strictly increasing per row) and fval (FP64; with storage BBL_FP32 the
+ * operator's factors are their FP32 roundings), factor f's entries from
+ * nz_off[f] (host int64 arrays of 2 + 2K offsets).
+ *   nP*nN < 2^31; K <= 30; check_symmetry: every factor must be symmetric
+ *   (BBL_ERR_NOT_SYMMETRIC), which makes H symmetric.
+ * The matrix is the exact Kronecker sum: each entry is the FP64 sum of its
+ * factor products (no rounding to the storage type).  diag(H), ||H||_inf
+ * and the number of nonzeros of the expansion are computed at creation.
+ * SpMM: FP32 blocks in FP32 arithmetic (storage BBL_FP32), FP64 blocks in
+ * FP64 (bbl_spmm_f64, or storage BBL_FP64), float-float blocks in the
+ * polish; one CTA forms one nN-row slab of W, staging one slab-sized tile
+ * in shared memory, so nN * min(b, 16) * 4 bytes (FP32) must fit in about
+ * 200 KB (narrower column groups are used for larger nN; beyond
+ * nN ~ 4000 * 16 / (element bytes) the SpMM reports BBL_ERR_UNSUPPORTED).
+ * bbl_pivot_bootstrap extracts H[S,S] from the factors.  Not accepted by
+ * bbl_batch_create.                                                        */
+bbl_status bbl_matrix_create_kron(int64_t nP, int64_t nN, int K, const int32_t* fptr, const int32_t* fcol,
+                                  const double* fval, const int64_t* ptr_off, const int64_t* nz_off,
+                                  bbl_dtype storage, int check_symmetry, void* stream, bbl_matrix** out);
 
 /* SpMM schedule for the CSR path chosen by an autotuner: lanes per row (a
  * power of two <= 32; 0 restores the built-in rule).  Used by bbl_spmm and by

@@ -16,7 +16,7 @@ import numpy as np
 from . import _lib
 from ._lib import BBLError, CSR, FP32, FP64, SELL, Options, Stats
 
-__all__ = ["Matrix", "spmm", "spmm_f64", "block_reorth", "cholqr2", "ritz_banded", "ritz_vectors", "pivot_random",
+__all__ = ["Matrix", "KronMatrix", "spmm", "spmm_f64", "block_reorth", "cholqr2", "ritz_banded", "ritz_vectors", "pivot_random",
            "pivot_bootstrap", "solve", "SolveResult", "BBLError", "options", "FP32", "FP64", "CSR", "SELL"]
 
 
@@ -129,6 +129,45 @@ class Matrix:
             self.close()
         except Exception:
             pass
+
+
+def pack_kron_factors(factors):
+    """Layout conversion for bbl_matrix_create_kron: the factors (objects with
+    n, row_ptr, col, val) in the order Hp, Hn, Cp_0, Cn_0, ... packed into
+    (fptr int32, fcol int32, fval FP64, ptr_off int64, nz_off int64)."""
+    facs = [factors.Hp, factors.Hn]
+    for a, b in zip(factors.Cp, factors.Cn):
+        facs += [a, b]
+    ptr_off = np.cumsum([0] + [f.n + 1 for f in facs[:-1]]).astype(np.int64)
+    nz_off = np.cumsum([0] + [int(f.row_ptr[-1]) for f in facs[:-1]]).astype(np.int64)
+    fptr = np.concatenate([np.asarray(f.row_ptr, dtype=np.int32) for f in facs])
+    fcol = np.concatenate([np.asarray(f.col, dtype=np.int32) for f in facs])
+    fval = np.concatenate([np.asarray(f.val, dtype=np.float64) for f in facs])
+    return fptr, fcol, fval, ptr_off, nz_off
+
+
+class KronMatrix(Matrix):
+    """A matrix kept as its Kronecker factors and applied without storing its
+    entries (bbl_matrix_create_kron): H = Hp (x) I + I (x) Hn + sum_k Cp_k (x) Cn_k.
+    `factors` has Hp, Hn (CSR-like objects) and the lists Cp, Cn."""
+
+    def __init__(self, factors, storage: str = "fp32", check_symmetry: bool = False, stream=None):
+        lib = _lib.load()
+        self._lib = lib
+        fptr, fcol, fval, ptr_off, nz_off = pack_kron_factors(factors)
+        h = C.c_void_p()
+        st = lib.bbl_matrix_create_kron(int(factors.Hp.n), int(factors.Hn.n), len(factors.Cp), _ptr(fptr), _ptr(fcol),
+                                        _ptr(fval), _ptr(ptr_off), _ptr(nz_off), FP32 if storage == "fp32" else FP64,
+                                        int(check_symmetry), _stream(stream), C.byref(h))
+        _lib.check(st)
+        self.handle = h
+        self.storage = storage
+        self.fmt = "kron"
+        n, nnz, nb, fm, sto, pnz = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int(), C.c_int(), C.c_int64()
+        norm = C.c_double()
+        _lib.check(lib.bbl_matrix_info(h, C.byref(n), C.byref(nnz), C.byref(norm), C.byref(nb), C.byref(fm),
+                                       C.byref(sto), C.byref(pnz)))
+        self.n, self.nnz, self.norm_inf, self.device_bytes, self.padded_nnz = n.value, nnz.value, norm.value, nb.value, pnz.value
 
 
 def spmm(A: Matrix, V, W=None, stream=None, lanes_per_row: int | None = None):

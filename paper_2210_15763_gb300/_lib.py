@@ -10,7 +10,7 @@ BBL_OK = 0
 STATUS = {0: "BBL_OK", 1: "BBL_ERR_INVALID_ARG", 2: "BBL_ERR_NOT_SYMMETRIC", 3: "BBL_ERR_OOM", 4: "BBL_ERR_CUDA",
           5: "BBL_ERR_NOT_CONVERGED", 6: "BBL_ERR_NUMERICAL", 7: "BBL_ERR_TIMEOUT", 8: "BBL_ERR_UNSUPPORTED"}
 FP64, FP32 = 0, 1
-CSR, SELL = 0, 1
+CSR, SELL, KRON = 0, 1, 2
 
 
 class Options(C.Structure):
@@ -49,6 +49,7 @@ SIGNATURES = {
     "bbl_workspace_bytes": (C.c_size_t, []),
     "bbl_workspace_release": (ST, []),
     "bbl_matrix_create": (ST, [I64, I64, P, P, P, I32, I32, I32, I32, I32, I32, P, C.POINTER(P)]),
+    "bbl_matrix_create_kron": (ST, [I64, I64, I32, P, P, P, P, P, I32, I32, P, C.POINTER(P)]),
     "bbl_matrix_destroy": (None, [P]),
     "bbl_matrix_info": (ST, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(D), C.POINTER(I64), C.POINTER(I32),
                              C.POINTER(I32), C.POINTER(I64)]),

@@ -16,6 +16,8 @@ namespace bbl {
 constexpr int kWarp = 32;
 constexpr int kSellC = 32;     // rows per SELL slice
 constexpr int kMaxB = 16;      // largest block size
+constexpr int kKronMaxK = 30;  // coupling terms of a Kronecker-factored operator
+constexpr int kKronMaxFactors = 2 + 2 * kKronMaxK;
 
 // ------------------------------------------------------------------ errors
 bbl_status set_error(bbl_status s, const char* fmt, ...);
@@ -172,9 +174,21 @@ struct bbl_matrix {
     bbl::DevBuf perm;      // int32 [nslices*32] original row of each slot (-1 past n)
     // diagonal, FP64 [n]
     bbl::DevBuf diag;
+    // Kronecker-factored operator (fmt == BBL_KRON): H = Hp (x) I + I (x) Hn +
+    // sum_k Cp_k (x) Cn_k kept as its factors (Hp, Hn, Cp_0, Cn_0, ...),
+    // packed: factor f's row pointers (int32) start at kf_ptr_off[f], its
+    // columns (int32) and values (FP32 and FP64 copies) at kf_nz_off[f]
+    int64_t kron_nP = 0, kron_nN = 0;
+    int kron_K = 0;
+    int kron_prow_cap = 0;  // most entries of one row p over Hp and all Cp_k
+    int kron_row_cap = 0;   // power of two >= the most term contributions of one row of H
+    bbl::DevBuf kf_ptr, kf_col, kf_val32, kf_val64;
+    int64_t kf_ptr_off[bbl::kKronMaxFactors] = {};
+    int64_t kf_nz_off[bbl::kKronMaxFactors] = {};
     int64_t device_bytes() const {
         return (int64_t)(row_ptr.bytes + col.bytes + val.bytes + val64.bytes + slice_ptr.bytes + sell_col.bytes +
-                         sell_val.bytes + sell_len.bytes + perm.bytes + diag.bytes);
+                         sell_val.bytes + sell_len.bytes + perm.bytes + diag.bytes + kf_ptr.bytes + kf_col.bytes +
+                         kf_val32.bytes + kf_val64.bytes);
     }
 };
 
@@ -184,6 +198,14 @@ bbl_status spmm_dispatch(const bbl_matrix* A, int b, const void* V, void* W, boo
                          int rows_per_warp_hint = 0);
 // W = H V with float-float blocks V, W (n x b pairs) and FP32 matrix values
 bbl_status spmm_df32(const bbl_matrix* A, int b, const void* V, void* W, cudaStream_t st);
+// kron.cu: W = H V from the factors of a BBL_KRON matrix; dt = element type
+// of V and W (BBL_FP32, BBL_FP64 or kDF32)
+bbl_status kron_spmm(const bbl_matrix* A, int b, int dt, const void* V, void* W, cudaStream_t st);
+// the principal submatrix H[S,S] of a BBL_KRON matrix as CSR (FP64 values):
+// S device int32 [k] ascending rows, pos device int32 [n] (position in S or
+// -1); row_ptr (int64 [k+1]), col, val allocated here
+bbl_status kron_submatrix(const bbl_matrix* A, int64_t k, const int* S, const int* pos, DevBuf& row_ptr,
+                          DevBuf& col, DevBuf& val, int64_t* nnz, cudaStream_t st);
 // block.cu
 struct BlockWork;  // scratch for Gram/reorth/CholQR2
 bbl_status gram(int64_t n, int b, int nblocks, int dtype, const void* Q, const void* W, double* C,

@@ -187,7 +187,8 @@ extern "C" bbl_status bbl_pivot_bootstrap(const bbl_matrix* A, int64_t trunc_dim
     using namespace bbl;
     if (!A || !P || b < 1 || b > kMaxB || trunc_dim < 1 || !(sub_tol > 0))
         return set_error(BBL_ERR_INVALID_ARG, "pivot_bootstrap: bad arguments");
-    if (!A->has_csr) return set_error(BBL_ERR_UNSUPPORTED, "pivot_bootstrap: needs the CSR copy of H");
+    if (!A->has_csr && A->fmt != BBL_KRON)
+        return set_error(BBL_ERR_UNSUPPORTED, "pivot_bootstrap: needs the CSR copy of H");
     cudaStream_t st = as_stream(stream);
     const int64_t n = A->n;
     const int64_t k = std::min(trunc_dim, n);
@@ -243,8 +244,12 @@ extern "C" bbl_status bbl_pivot_bootstrap(const bbl_matrix* A, int64_t trunc_dim
         unit_embed_kernel<<<(unsigned)ceil_div(k, 256), 256, 0, st>>>(k, b, Sidx.as<int>(), P);
         BBL_LAUNCH_CHECK();
     } else {
-        // 3. H[S,S] as CSR
+        // 3. H[S,S] as CSR (of a factored matrix: from its expanded rows)
         DevBuf len, srp, sci, sva;
+        int64_t acc = 0;
+        if (A->fmt == BBL_KRON) {
+            BBL_TRY(kron_submatrix(A, k, Sidx.as<int>(), pos.as<int>(), srp, sci, sva, &acc, st));
+        } else {
         BBL_TRY(len.alloc(sizeof(int64_t) * (k + 1)));
         sub_rowlen_kernel<<<(unsigned)ceil_div(k * 32, 256), 256, 0, st>>>(k, Sidx.as<int>(), pos.as<int>(),
                                                                            A->row_ptr.as<int64_t>(), A->col.as<int>(),
@@ -253,7 +258,6 @@ extern "C" bbl_status bbl_pivot_bootstrap(const bbl_matrix* A, int64_t trunc_dim
         std::vector<int64_t> h(k + 1);
         BBL_CUDA(cudaMemcpyAsync(h.data(), len.p, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, st));
         BBL_CUDA(cudaStreamSynchronize(st));
-        int64_t acc = 0;
         for (int64_t s = 0; s < k; ++s) {
             const int64_t t = h[s];
             h[s] = acc;
@@ -274,6 +278,7 @@ extern "C" bbl_status bbl_pivot_bootstrap(const bbl_matrix* A, int64_t trunc_dim
                 srp.as<int64_t>(), sci.as<int>(), sva.as<double>());
         BBL_LAUNCH_CHECK();
         BBL_CUDA(cudaStreamSynchronize(st));
+        }
         // 4. lowest b eigenpairs of H[S,S]: a sub-solve to sub_tol >= 1e-5 from
         // FP32 values runs in FP32 storage without the polish (its tolerance is
         // far above the FP32 stage's floor, and FP64 arithmetic runs at 1/64 of

@@ -52,7 +52,7 @@ def _load():
             lib = ctypes.CDLL(_LIB)
             f = lib.kron_assemble
             f.restype = ctypes.c_int64
-            f.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int] + [ctypes.c_void_p] * 9
+            f.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int] + [ctypes.c_void_p] * 9 + [ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -167,12 +167,17 @@ def kron_factors(nP: int, nN: int, K: int, c: float, seed: int, d_off: float = 1
 
 
 def assemble(f: KronFactors, fp32_values: bool = False, extra_scale: float | None = None,
-             extra: KronFactors | None = None) -> CSR:
+             extra: KronFactors | None = None, exact: bool = False) -> CSR:
     """Expands the Kronecker sum into CSR.
 
     With ``extra`` given, its coupling terms are appended with their Cp values
     multiplied by ``extra_scale`` (used for the family H(g) = H0 + g V).
+    ``exact`` keeps every entry as the FP64 sum of its factor products (no
+    FP32 rounding): the matrix that an operator applying the factors
+    themselves applies (FP64 values only).
     """
+    if exact and fp32_values:
+        raise ValueError("exact entries are FP64 sums of factor products")
     cp, cn = list(f.Cp), list(f.Cn)
     if extra is not None:
         s = 1.0 if extra_scale is None else float(extra_scale)
@@ -192,19 +197,20 @@ def assemble(f: KronFactors, fp32_values: bool = False, extra_scale: float | Non
     lib = _load()
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    r32 = 0 if exact else 1
     nnz = lib.kron_assemble(nP, nN, K, p(ptrs), p(idxs), p(vals), p(offs_ptr), p(offs_nz),
-                            p(row_ptr), None, None, None)
+                            p(row_ptr), None, None, None, r32)
     if nnz < 0:
         raise MemoryError("kron_assemble: out of memory (pass 1)")
     col = np.empty(nnz, dtype=np.int32)
     if fp32_values:
         val = np.empty(nnz, dtype=np.float32)
         r = lib.kron_assemble(nP, nN, K, p(ptrs), p(idxs), p(vals), p(offs_ptr), p(offs_nz),
-                              p(row_ptr), p(col), None, p(val))
+                              p(row_ptr), p(col), None, p(val), r32)
     else:
         val = np.empty(nnz, dtype=np.float64)
         r = lib.kron_assemble(nP, nN, K, p(ptrs), p(idxs), p(vals), p(offs_ptr), p(offs_nz),
-                              p(row_ptr), p(col), p(val), None)
+                              p(row_ptr), p(col), p(val), None, r32)
     if r < 0:
         raise MemoryError("kron_assemble: out of memory (pass 2)")
     return CSR(n, row_ptr, col, val)
@@ -234,12 +240,21 @@ def kron_config(name: str, scale: float = 1.0) -> dict:
     return cfg
 
 
-def kron_matrix(name: str, scale: float = 1.0, fp32_values: bool = False, K: int | None = None) -> CSR:
+def named_factors(name: str, scale: float = 1.0, K: int | None = None) -> KronFactors:
+    """The factor matrices of a named workload."""
     cfg = kron_config(name, scale)
     if K is not None:
         cfg["K"] = K
-    f = kron_factors(cfg["nP"], cfg["nN"], cfg["K"], cfg["c"], cfg["seed"])
-    return assemble(f, fp32_values=fp32_values)
+    return kron_factors(cfg["nP"], cfg["nN"], cfg["K"], cfg["c"], cfg["seed"])
+
+
+def kron_matrix(name: str, scale: float = 1.0, fp32_values: bool = False, K: int | None = None,
+                exact: bool = False) -> CSR:
+    """A named workload assembled into CSR (entries rounded to FP32 unless
+    ``exact``; a name ending in "_exact" asks for the exact entries)."""
+    if name.endswith("_exact"):
+        name, exact = name[:-len("_exact")], True
+    return assemble(named_factors(name, scale, K), fp32_values=fp32_values, exact=exact)
 
 
 def learned_family(scale: float = 1.0, seed: int = 20221032):

@@ -3,7 +3,9 @@
  *
  *     H = Hp (x) I_nN  +  I_nP (x) Hn  +  sum_k Cp_k (x) Cn_k
  *
- * into CSR (int64 row pointers, int32 column indices, values rounded to FP32).
+ * into CSR (int64 row pointers, int32 column indices, values rounded to FP32,
+ * or kept as the FP64 sums of the factor products: the "exact" Kronecker sum
+ * that an operator applying the factors directly, without storing H, applies).
  * The factor matrices are small sparse symmetric CSR matrices drawn by
  * synth/kron.py; this file only expands the Kronecker sum row by row.
  *
@@ -75,8 +77,8 @@ static int64_t row_terms(int64_t p, int64_t q, int64_t nN, fcsr Hp, fcsr Hn, int
 }
 
 /* Sorts and merges the contributions; returns the merged count.  Merged
- * values are the FP64 sums in term order, rounded to FP32. */
-static int64_t merge_terms(entry* buf, int64_t t) {
+ * values are the FP64 sums in term order, rounded to FP32 when round32. */
+static int64_t merge_terms(entry* buf, int64_t t, int round32) {
     qsort(buf, (size_t)t, sizeof(entry), cmp_entry);
     int64_t out = 0;
     for (int64_t i = 0; i < t;) {
@@ -84,7 +86,7 @@ static int64_t merge_terms(entry* buf, int64_t t) {
         double s = 0.0;
         while (j < t && buf[j].col == buf[i].col) { s += buf[j].v; ++j; }
         buf[out].col = buf[i].col;
-        buf[out].v = (double)(float)s;
+        buf[out].v = round32 ? (double)(float)s : s;
         ++out;
         i = j;
     }
@@ -112,12 +114,14 @@ static void unpack(const int64_t* ptrs, const int32_t* idxs, const double* vals,
  * Pass 1 (row_ptr != NULL, col == NULL): writes the CSR row pointer (n+1).
  * Pass 2 (col != NULL): fills col / val (val64 or val32, whichever is non-NULL)
  *                       using the row pointer from pass 1.
+ * round32: 1 rounds every merged entry to FP32 once (both solvers then see
+ * the same FP32-exact matrix); 0 keeps the FP64 sums (requires val64).
  * Returns the number of nonzeros, or -1 on allocation failure.
  */
 int64_t kron_assemble(int64_t nP, int64_t nN, int K,
                       const int64_t* ptrs, const int32_t* idxs, const double* vals,
                       const int64_t* offs_ptr, const int64_t* offs_nz,
-                      int64_t* row_ptr, int32_t* col, double* val64, float* val32) {
+                      int64_t* row_ptr, int32_t* col, double* val64, float* val32, int round32) {
     fcsr Hp, Hn;
     fcsr* Cp = (fcsr*)malloc(sizeof(fcsr) * (K > 0 ? K : 1));
     fcsr* Cn = (fcsr*)malloc(sizeof(fcsr) * (K > 0 ? K : 1));
@@ -145,7 +149,7 @@ int64_t kron_assemble(int64_t nP, int64_t nN, int K,
                 for (int64_t p = 0; p < nP; ++p) {
                     for (int64_t q = 0; q < nN; ++q) {
                         int64_t t = row_terms(p, q, nN, Hp, Hn, K, Cp, Cn, buf);
-                        row_ptr[p * nN + q + 1] = merge_terms(buf, t);
+                        row_ptr[p * nN + q + 1] = merge_terms(buf, t, round32);
                     }
                 }
             }
@@ -165,7 +169,7 @@ int64_t kron_assemble(int64_t nP, int64_t nN, int K,
                 for (int64_t p = 0; p < nP; ++p) {
                     for (int64_t q = 0; q < nN; ++q) {
                         const int64_t r = p * nN + q;
-                        int64_t t = merge_terms(buf, row_terms(p, q, nN, Hp, Hn, K, Cp, Cn, buf));
+                        int64_t t = merge_terms(buf, row_terms(p, q, nN, Hp, Hn, K, Cp, Cn, buf), round32);
                         int64_t base = row_ptr[r];
                         for (int64_t e = 0; e < t; ++e) {
                             col[base + e] = (int32_t)buf[e].col;

@@ -5,7 +5,10 @@ block Lanczos (b = 8, random pivot from the splitmix64 generator, residual
 1e-8 * ||H||_inf), then the 8 lowest Ritz values, their true residuals and the
 block count.  The GPU tests compare against these files at full size.
 
-    python tests/golden/make_reference_evals.py kron_n2e6 kron_n2e6_c3
+    python tests/golden/make_reference_evals.py kron_n2e6 kron_n2e6_c3 kron_n2e6_exact
+
+A name ending in "_exact" is the same workload with unrounded entries (the
+FP64 sums of the factor products: the matrix the factored operator applies).
 """
 import json
 import os
