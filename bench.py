@@ -77,11 +77,11 @@ def headline_solve(bbl, M, P, evecs="device", **opts):
     return bbl.solve(M, NEV, B, pivot=P, tol=TOL, evecs=evecs, max_vectors=2000, **kw)
 
 
-def oracle_eval_error(evals):
+def oracle_eval_error(evals, path=None):
     """Largest relative difference from the stored FP64 oracle eigenvalues
     (None when the file is absent)."""
     try:
-        with open(ORACLE_EVALS) as f:
+        with open(path or ORACLE_EVALS) as f:
             ref = np.array(json.load(f)["evals"])
     except (OSError, KeyError, ValueError):
         return None
@@ -354,6 +354,11 @@ def run_ours(args):
                 "per_kernel": {k: {kk: (round(vv, 3) if isinstance(vv, float) else vv) for kk, vv in v.items()}
                                for k, v in kernels.items()}}
 
+    # overlap of the bootstrapped pivot with each converged eigenvector (Sec. II.B)
+    P_last = headline_pivot(bbl, M32, args.sub_tol)
+    overlaps = bbl.pivot_overlap(P_last, r.evecs)
+    del P_last
+
     # plain FP64 random-pivot block Lanczos (the comparison named by the metric)
     plain = None
     if not args.skip_plain:
@@ -366,8 +371,16 @@ def run_ours(args):
         p1.record(st)
         torch.cuda.synchronize()
         t_plain = p0.elapsed_time(p1) / 1e3
-        plain = {"time_s": t_plain, "iters": rp.stats["iters"], "converged": rp.converged,
-                 "spmm_gbs": rp.stats["spmm_gbs"], "dfma_bound": True,
+        # is the FP64 SpMM limited by FP64 arithmetic or by memory?  Its
+        # flop rate against the measured FP64 FMA rate, its bytes against HBM
+        f64_rate = bbl.probe_fma_rate("fp64")
+        sp = rp.stats
+        flop_rate = 2.0 * A.nnz * B * sp["spmm_calls"] / (sp["t_spmm_ms"] * 1e-3)
+        plain = {"time_s": t_plain, "iters": sp["iters"], "converged": rp.converged,
+                 "spmm_gbs": sp["spmm_gbs"], "spmm_tflops": flop_rate / 1e12,
+                 "fp64_fma_tflops_measured": f64_rate / 1e12,
+                 "spmm_frac_of_fp64_fma": flop_rate / f64_rate, "spmm_frac_of_hbm": sp["spmm_gbs"] / hbm,
+                 "dfma_bound": bool(flop_rate / f64_rate > sp["spmm_gbs"] / hbm),
                  "max_abs_eval_diff_vs_mixed": float(np.max(np.abs(rp.evals - r.evals)))}
         del M64
         torch.cuda.empty_cache()
@@ -408,6 +421,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (matrix 4.8 GB)"},
         "converged": ok, "max_resid_rel": resid_rel,
         "max_rel_err_vs_oracle": oracle_eval_error(r.evals),
+        "pivot_overlap": [round(float(x), 4) for x in overlaps],
         "iters": r.stats["iters"], "polish_iters": r.stats["polish_iters"], "ritz_solves": r.stats["ritz_solves"],
         "vec_equiv_iters": r.stats["vec_equiv_iters"],
         "spmm_gbs": round(spmm_gbs, 1), "reorth_gbs": round(reorth_gbs, 1), "phases_ms": phases,
@@ -454,7 +468,8 @@ def run_kernels(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    out = {"n": n, "nnz": A.nnz, "b": B, "basis_blocks": nb}
+    out = {"n": n, "nnz": A.nnz, "b": B, "basis_blocks": nb,
+           "fma_tflops": {"fp32": bbl.probe_fma_rate("fp32") / 1e12, "fp64": bbl.probe_fma_rate("fp64") / 1e12}}
     t = timeit(lambda: bbl.spmm(M, V, W), args.reps)
     by = A.nnz * 8 + (n + 1) * 8 + 2 * n * B * 4
     out["spmm_sell_fp32"] = {"ms": t, "GBs": by / t / 1e6}
@@ -671,9 +686,135 @@ def run_c3(args):
     print(json.dumps(out))
 
 
+def run_kron(args):
+    """The same step on the Kronecker-factored operator: H is never stored;
+    every SpMM rebuilds it from Hp, Hn, Cp_k, Cn_k (the paper's on-the-fly
+    matrix elements, Sec. I, Sec. III.A, Appendix A).  The matrix is the exact
+    Kronecker sum of the kron_n2e6 factors (entries not rounded to FP32), so
+    the eigenvalues are compared with the oracle's for that matrix.  Reported
+    beside it: the factored SpMM per launch (its own CUDA events inside the
+    solver), the bytes it streams through L2 per launch, and the plain FP64
+    random-pivot solve of the same exact matrix stored as FP64 CSR."""
+    import torch
+    import synth
+    import paper_2210_15763_gb300 as bbl
+    st = torch.cuda.current_stream()
+    f = synth.named_factors(WORKLOAD)
+    t0 = time.perf_counter()
+    M = bbl.KronMatrix(f, storage="fp32")
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    solve_opts = {"stage1_tol": args.stage1_tol, "half_first_pass": args.half_first_pass}
+    stats_log = []
+
+    def step():
+        P = headline_pivot(bbl, M, args.sub_tol)
+        r = headline_solve(bbl, M, P, **solve_opts)
+        stats_log.append(r.stats)
+        return r
+
+    for _ in range(args.warmup):
+        step()
+    stats_log.clear()
+    sampler = ClockSampler(0)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    results = [step() for _ in range(args.steps)]
+    e1.record(st)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    r = results[-1]
+    # SpMM of the FP32 stage: one launch per phase event
+    calls = sum(s["spmm_calls"] for s in stats_log)
+    spmm_ms = sum(s["spmm_bytes"] * s["spmm_calls"] / (s["spmm_gbs"] * 1e9) * 1e3 for s in stats_log) / calls
+    # bytes a launch streams: every output slab p reads the slabs of row p of
+    # Hp and of each Cp_k, and its own slab once (b = 8 FP32 columns)
+    lens = np.diff(f.Hp.row_ptr) + 1 + sum(np.diff(c.row_ptr) for c in f.Cp)
+    stream_bytes = float(lens.sum()) * f.Hn.n * B * 4
+    plain = None
+    if not args.skip_plain:
+        Hx = synth.assemble(f, exact=True)
+        M64 = bbl.Matrix(Hx, storage="fp64", fmt="csr")
+        del Hx
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(st)
+        rp = bbl.solve(M64, NEV, B, pivot=None, seed=PIVOT_SEED, tol=TOL, evecs=None, max_vectors=2000)
+        p1.record(st)
+        torch.cuda.synchronize()
+        plain = {"time_s": p0.elapsed_time(p1) / 1e3, "iters": rp.stats["iters"], "converged": rp.converged,
+                 "max_abs_eval_diff_vs_factored": float(np.max(np.abs(rp.evals - r.evals)))}
+        del M64
+        torch.cuda.empty_cache()
+    exact = os.path.join(ROOT, "tests", "golden", f"{WORKLOAD}_exact_fp64_oracle_evals.json")
+    out = {"mode": "kron", "metric": METRIC, "value": ms / 1e3, "unit": "s", "steps": args.steps,
+           "warmup": args.warmup, "higher_is_better": False,
+           "config": {"workload": f"{WORKLOAD} factored: Hp 2000x2000, Hn 1000x1000, 12 coupling terms, n={M.n}, "
+                                  f"nnz of the expansion={M.nnz} (never stored), b={B}, nev={NEV}, tol={TOL}",
+                      "method": "bootstrap + FP32 stage + float-float polish on the factored operator"},
+           "converged": all(x.converged for x in results), "iters": r.stats["iters"],
+           "polish_iters": r.stats["polish_iters"], "max_resid_rel": float(np.max(r.resid) / M.norm_inf),
+           "max_rel_err_vs_oracle": oracle_eval_error(r.evals, exact),
+           "kron_spmm_ms_per_launch": spmm_ms, "kron_spmm_launches": calls,
+           "stream_bytes_per_launch": stream_bytes, "stream_gbs": stream_bytes / (spmm_ms * 1e-3) / 1e9,
+           "hbm_alg_bytes_per_launch": r.stats["spmm_bytes"],
+           "matrix_device_bytes": int(M.device_bytes), "create_s": t_create,
+           "phases_ms": {k: sum(s[k] for s in stats_log) / args.steps
+                         for k in ("t_spmm_ms", "t_reorth_ms", "t_cholqr_ms", "t_ritz_ms", "t_total_ms")},
+           "plain_fp64_stored_exact": plain, "clocks": clocks}
+    print(json.dumps(out))
+
+
+def run_c2(args):
+    """The b sweep of the plain FP64 configuration at n = 2,000,000 (the
+    paper's Tables I-II: time per operation and vector-equivalent iterations
+    against the block size): b in {1, 4, 8, 16}, 8 lowest eigenpairs to
+    residual 1e-8, FP64 CSR, random pivot vs the pivot bootstrapped from the
+    20,000 lowest-diagonal rows (its FP64 sub-solve to sub_tol).  Per run:
+    blocks, vector-equivalent iterations, time-to-solve (including the
+    bootstrap), SpMM ms per call, ns per operation t_SpMM / (nnz * b), and
+    the largest relative eigenvalue error against the stored oracle values."""
+    import torch
+    import paper_2210_15763_gb300 as bbl
+    A, tgen = build_matrix()
+    M = bbl.Matrix(A, storage="fp64", fmt="csr")
+    del A
+    st = torch.cuda.current_stream()
+    rows = []
+    for b in [int(x) for x in args.c2_blocks.split(",")]:
+        for pivot in ("random", "bootstrap"):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            eb = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            P = None if pivot == "random" else bbl.pivot_bootstrap(M, TRUNC, b, sub_tol=args.sub_tol, seed=PIVOT_SEED)
+            eb.record(st)
+            r = bbl.solve(M, NEV, b, pivot=P, seed=PIVOT_SEED, tol=TOL, evecs=None, max_vectors=2000)
+            e1.record(st)
+            torch.cuda.synchronize()
+            s = r.stats
+            t_call = s["t_spmm_ms"] / max(s["spmm_calls"], 1)
+            rows.append({"b": b, "pivot": pivot, "converged": r.converged, "blocks": s["iters"],
+                         "vec_equiv_iters": s["iters"] * b, "time_s": e0.elapsed_time(e1) / 1e3,
+                         "bootstrap_s": e0.elapsed_time(eb) / 1e3, "spmm_ms_per_call": t_call,
+                         "ns_per_op": t_call * 1e6 / (M.nnz * b), "spmm_gbs": s["spmm_gbs"],
+                         "reorth_ms": s["t_reorth_ms"], "ritz_ms": s["t_ritz_ms"],
+                         "max_rel_err_vs_oracle": oracle_eval_error(r.evals)})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"mode": "c2", "workload": f"{WORKLOAD} (n={M.n}, nnz={M.nnz}), FP64 CSR, nev={NEV}, tol={TOL}",
+                      "runs": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--mode", default="solve", choices=["solve", "kernels", "batched", "learned", "c3"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "kernels", "batched", "learned", "c3", "kron", "c2"])
+    ap.add_argument("--c2-blocks", default="1,4,8,16")
     ap.add_argument("--c3-vectors", type=int, default=300)
     ap.add_argument("--c3-fp64", action="store_true")
     ap.add_argument("--ritz-overlap", type=int, default=None)
@@ -707,6 +848,10 @@ def main():
         run_learned(args)
     elif args.mode == "c3":
         run_c3(args)
+    elif args.mode == "kron":
+        run_kron(args)
+    elif args.mode == "c2":
+        run_c2(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

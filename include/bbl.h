@@ -134,6 +134,12 @@ void bbl_options_default(bbl_options* opt);
 const char* bbl_last_error(void);
 const char* bbl_status_string(bbl_status s);
 int bbl_version(void);
+/* Measured fused multiply-add rate of the current GPU in FLOP/s (2 per
+ * FMA) for BBL_FP32 or BBL_FP64 arithmetic: independent FMA chains on every
+ * SM, best of three timed launches.  No counterpart in the paper: it backs
+ * the precision choices (FP64 arithmetic runs at a small fraction of the
+ * FP32 rate on this GPU).  Synchronises `stream`.                         */
+bbl_status bbl_probe_fma_rate(bbl_dtype dtype, double* flops_per_s, void* stream);
 /* Number of kernels this library has launched in the process so far. */
 uint64_t bbl_kernel_launches(void);
 /* Workspace cache.  The Lanczos bases (bbl_solve, bbl_pivot_bootstrap,
@@ -329,6 +335,18 @@ bbl_status bbl_pivot_bootstrap(const bbl_matrix* A, int64_t trunc_dim, int b, do
  * eigenvectors).                                                          */
 bbl_status bbl_pivot_rr_residual(const bbl_matrix* A, int b, const double* P, double* theta, double* resid,
                                  void* stream);
+
+/* Pivot-eigenvector overlap (Sec. II.B: block Lanczos only reaches the
+ * eigenvectors its pivot overlaps; Sec. III.A: states the pivot misses
+ * converge late, after higher "intruder" states).  For each of k vectors
+ * x_i (unit eigenvectors, e.g. bbl_solve's), overlap[i] = ||Q^T x_i||_2 with
+ * Q = orth(P) (CholQR2 in FP64; a pivot column dependent on the others to
+ * 1e-10 of the largest column norm is dropped): 1 when x_i lies in span(P),
+ * 0 when it is orthogonal to it.
+ *   P        host or device FP64 n x b row-major;  X host or device FP64
+ *            n x k row-major;  overlap host FP64 [k];  b, k in 1..16.   */
+bbl_status bbl_pivot_overlap(int64_t n, int b, const double* P, int k, const double* X, double* overlap,
+                             void* stream);
 
 /* ---------------------------------------------------------------- learned pivot (MLP)
  * A small network g -> y = f(g) (1 -> H -> H -> O, exact-erf GELU), FP32

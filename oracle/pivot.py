@@ -2,6 +2,9 @@
 
 random_pivot     i.i.d. N(0,1) block ("randomly constructed pivot", Sec. III),
                  from the splitmix64 counter generator.
+pivot_overlap    Sec. II.B / III.A: the share of each eigenvector inside the
+                 span of the pivot, ||Q^T x|| with Q an orthonormal basis of
+                 span(P) (Householder QR).
 bootstrap_pivot  Sec. II.B (bootstrapping) and Sec. III: approximate lowest
                  eigenvectors computed in a truncated space, projected into
                  the full space.  The truncated space is the set S of the
@@ -44,3 +47,13 @@ def bootstrap_pivot(H, trunc_dim: int, b: int, seed: int = 0):
     if k < b:
         P[:, k:] = _rng.normal_block(seed, n, b - k)
     return P, S, theta[:k]
+
+
+def pivot_overlap(P: np.ndarray, X: np.ndarray, rank_tol: float = 1e-10) -> np.ndarray:
+    """||Q^T x_i||_2 for each column of X, Q an orthonormal basis of span(P)
+    (Householder QR; directions with |R_ii| below rank_tol * max |R_jj| are
+    dropped)."""
+    Q, R = np.linalg.qr(np.asarray(P, dtype=np.float64))
+    d = np.abs(np.diag(R))
+    Q = Q[:, d > rank_tol * d.max()] if d.size and d.max() > 0 else Q[:, :0]
+    return np.linalg.norm(Q.T @ np.asarray(X, dtype=np.float64), axis=0)

@@ -281,6 +281,26 @@ def pivot_rr_residual(A: Matrix, P, stream=None):
     return th, rs
 
 
+def pivot_overlap(P, X, stream=None):
+    """||orth(P)^T x_i|| for each column x_i of X (host or device FP64)."""
+    n, b = P.shape
+    k = X.shape[1]
+    if isinstance(P, np.ndarray):
+        P = np.ascontiguousarray(P, dtype=np.float64)
+    if isinstance(X, np.ndarray):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+    out = np.zeros(k)
+    _lib.check(_lib.load().bbl_pivot_overlap(n, b, _ptr(P), k, _ptr(X), _ptr(out), _stream(stream)))
+    return out
+
+
+def probe_fma_rate(dtype: str = "fp64", stream=None) -> float:
+    """Measured FMA throughput of the GPU in FLOP/s (FP32 or FP64)."""
+    out = C.c_double()
+    _lib.check(_lib.load().bbl_probe_fma_rate(FP64 if dtype == "fp64" else FP32, C.byref(out), _stream(stream)))
+    return out.value
+
+
 def workspace_bytes() -> int:
     """Bytes of Lanczos bases the library keeps idle for reuse on this device."""
     return int(_lib.load().bbl_workspace_bytes())

@@ -46,6 +46,7 @@ SIGNATURES = {
     "bbl_status_string": (C.c_char_p, [ST]),
     "bbl_version": (C.c_int, []),
     "bbl_kernel_launches": (C.c_uint64, []),
+    "bbl_probe_fma_rate": (ST, [I32, C.POINTER(D), P]),
     "bbl_workspace_bytes": (C.c_size_t, []),
     "bbl_workspace_release": (ST, []),
     "bbl_matrix_create": (ST, [I64, I64, P, P, P, I32, I32, I32, I32, I32, I32, P, C.POINTER(P)]),
@@ -69,6 +70,7 @@ SIGNATURES = {
     "bbl_block_gram_noalloc": (ST, [I64, I32, I32, I32, P, P, P, P]),
     "bbl_block_gram_f16": (ST, [I64, I32, P, P, P, P]),
     "bbl_pivot_rr_residual": (ST, [P, I32, P, P, P, P]),
+    "bbl_pivot_overlap": (ST, [I64, I32, P, I32, P, P, P]),
     "bbl_mlp_create": (ST, [I32, I32, C.POINTER(P)]),
     "bbl_mlp_destroy": (None, [P]),
     "bbl_mlp_num_params": (C.c_int, [P]),

@@ -16,7 +16,9 @@
 //  cholqr2  G = W^T W -> R = chol(G) (one thread, b <= 16) -> W <- W R^{-1},
 //           twice; B = R2 R1 (Sec. II.B normalisation, CholQR2 form).
 #include <algorithm>
+#include <cmath>
 #include <mutex>
+#include <vector>
 
 #include <cuda_fp16.h>
 
@@ -1775,5 +1777,85 @@ extern "C" bbl_status bbl_block_gram_noalloc(int64_t n, int b, int nblocks, bbl_
         BBL_TRY(gram_fixed_typed<float>(n, b, m, static_cast<const float*>(basis), static_cast<const float*>(W), C,
                                         scratch, st));
     BBL_CUDA(cudaStreamSynchronize(st));
+    return BBL_OK;
+}
+
+// -------------------------------------------------------------------- pivot overlap diagnostic
+// How much of each converged eigenvector lies in the span of the pivot block
+// (Sec. II.B: the pivot must overlap the wanted eigenvectors; Sec. III.A:
+// states the pivot misses come late or as intruders).
+namespace bbl {
+namespace {
+
+constexpr int kOvRows = 64;
+
+// partial[cta][a*k + i] = sum over the CTA's rows r of Q[r][a] X[r][i]
+// (thread t < b*k owns the pair a = t / k, i = t % k; row tiles of Q and X
+// are staged in shared memory).
+__global__ void __launch_bounds__(256) cross_gram_kernel(int64_t n, int b, int k, const double* __restrict__ Q,
+                                                         const double* __restrict__ X, double* __restrict__ partial) {
+    __shared__ double qs[kOvRows * kMaxB];
+    __shared__ double xs[kOvRows * kMaxB];
+    const int t = threadIdx.x;
+    const int a = t / k, i = t - (t / k) * k;
+    double s = 0.0;
+    for (int64_t r0 = (int64_t)blockIdx.x * kOvRows; r0 < n; r0 += (int64_t)gridDim.x * kOvRows) {
+        const int rows = (int)min((int64_t)kOvRows, n - r0);
+        __syncthreads();
+        for (int e = t; e < rows * b; e += blockDim.x) qs[e] = Q[r0 * b + e];
+        for (int e = t; e < rows * k; e += blockDim.x) xs[e] = X[r0 * k + e];
+        __syncthreads();
+        if (t < b * k)
+            for (int r = 0; r < rows; ++r) s = fma(qs[r * b + a], xs[r * k + i], s);
+    }
+    if (t < b * k) partial[(int64_t)blockIdx.x * b * k + t] = s;
+}
+
+}  // namespace
+}  // namespace bbl
+
+extern "C" bbl_status bbl_pivot_overlap(int64_t n, int b, const double* P, int k, const double* X, double* overlap,
+                                        void* stream) {
+    using namespace bbl;
+    if (n < 1 || b < 1 || b > kMaxB || k < 1 || k > kMaxB || !P || !X || !overlap)
+        return set_error(BBL_ERR_INVALID_ARG, "pivot_overlap: bad arguments (b, k in 1..%d)", kMaxB);
+    cudaStream_t st = as_stream(stream);
+    DevBuf Q, Xd, partials, small, cnt, part, C;
+    BBL_TRY(Q.alloc(sizeof(double) * n * b));
+    BBL_CUDA(cudaMemcpyAsync(Q.p, P, sizeof(double) * n * b, cudaMemcpyDefault, st));
+    const double* Xp = X;
+    if (!is_device_pointer(X)) {
+        BBL_TRY(Xd.alloc(sizeof(double) * n * k));
+        BBL_CUDA(cudaMemcpyAsync(Xd.p, X, sizeof(double) * n * k, cudaMemcpyHostToDevice, st));
+        Xp = Xd.as<double>();
+    }
+    // Q = orth(P) by CholQR2; a column dependent on the others to 1e-10 of
+    // the largest column norm is dropped (a zero column of Q)
+    BBL_TRY(cnt.alloc(sizeof(int)));
+    BBL_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int), st));
+    BBL_TRY(small.alloc(sizeof(double) * 8 * kMaxB * kMaxB + sizeof(int) * 4 * kMaxB));
+    BBL_CUDA(cudaMemsetAsync(small.p, 0, small.bytes, st));
+    DevBuf Bm;
+    BBL_TRY(Bm.alloc(sizeof(double) * kMaxB * kMaxB));
+    BBL_TRY(cholqr2_dev(n, b, BBL_FP64, Q.p, Bm.as<double>(), -1e-20, cnt.as<int>(), nullptr, partials, small, st));
+    const int grid = (int)std::min<int64_t>(152 * 4, ceil_div(n, kOvRows));
+    BBL_TRY(part.alloc(sizeof(double) * (size_t)grid * b * k));
+    BBL_TRY(C.alloc(sizeof(double) * b * k));
+    cross_gram_kernel<<<grid, 256, 0, st>>>(n, b, k, Q.as<double>(), Xp, part.as<double>());
+    BBL_LAUNCH_CHECK();
+    launch_reduce((int64_t)b * k, grid, part.as<double>(), C.as<double>(), st);
+    BBL_LAUNCH_CHECK();
+    std::vector<double> h(b * k);
+    int bad = 0;
+    BBL_CUDA(cudaMemcpyAsync(h.data(), C.p, sizeof(double) * b * k, cudaMemcpyDeviceToHost, st));
+    BBL_CUDA(cudaMemcpyAsync(&bad, reinterpret_cast<char*>(small.p) + sizeof(double) * 8 * kMaxB * kMaxB, sizeof(int),
+                             cudaMemcpyDeviceToHost, st));
+    BBL_CUDA(cudaStreamSynchronize(st));
+    if (bad) return set_error(BBL_ERR_NUMERICAL, "pivot_overlap: non-finite pivot Gram matrix");
+    for (int i = 0; i < k; ++i) {
+        double s = 0.0;
+        for (int a = 0; a < b; ++a) s += h[a * k + i] * h[a * k + i];
+        overlap[i] = std::sqrt(s);
+    }
     return BBL_OK;
 }

@@ -198,6 +198,16 @@ bbl_status spmm_dispatch(const bbl_matrix* A, int b, const void* V, void* W, boo
                          int rows_per_warp_hint = 0);
 // W = H V with float-float blocks V, W (n x b pairs) and FP32 matrix values
 bbl_status spmm_df32(const bbl_matrix* A, int b, const void* V, void* W, cudaStream_t st);
+// Algorithmic bytes of one SpMM with b columns: the stored matrix (values of
+// sv bytes, int32 columns, int64 row pointers) read once, V read once and W
+// written once (sx bytes per block element); a factored matrix stores no
+// entries, so only the factors (int32 columns and row pointers, FP32 and
+// FP64 values) and the two blocks count.
+inline double spmm_alg_bytes(const bbl_matrix* A, int b, double sv, double sx) {
+    const double blocks = 2.0 * (double)A->n * b * sx;
+    if (A->fmt == BBL_KRON) return (double)(A->kf_ptr.bytes + A->kf_col.bytes + A->kf_val32.bytes) + blocks;
+    return (double)A->nnz * (sv + 4.0) + (double)(A->n + 1) * 8.0 + blocks;
+}
 // kron.cu: W = H V from the factors of a BBL_KRON matrix; dt = element type
 // of V and W (BBL_FP32, BBL_FP64 or kDF32)
 bbl_status kron_spmm(const bbl_matrix* A, int b, int dt, const void* V, void* W, cudaStream_t st);

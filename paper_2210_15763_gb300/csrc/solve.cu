@@ -570,7 +570,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             const int m = (j + 1) * b;
             const double sx = (double)s;
             const double sv = (A->storage == BBL_FP64 || (dtype != kDF32 && f64_spmm && A->val64.p)) ? 8.0 : 4.0;
-            out.spmm_bytes += (double)A->nnz * (sv + 4.0) + (double)(n + 1) * 8.0 + 2.0 * (double)n * b * sx;
+            out.spmm_bytes += spmm_alg_bytes(A, b, sv, sx);
             // two passes of Gram + update; an FP16 first-pass Gram reads 2 bytes per basis element
             out.reorth_bytes += (half1 ? 3.5 : 4.0) * (double)n * m * sx + 6.0 * (double)n * b * sx;
         }
@@ -717,7 +717,7 @@ bbl_status solve_impl(const bbl_matrix* A, int nev, int b, const double* pivot, 
         cudaEventElapsedTime(&tt, t0, t1);
         stats->t_total_ms = tt;
         const double sv = mixed ? 4.0 : 8.0;
-        stats->spmm_bytes = (double)A->nnz * (sv + 4.0) + (double)(n + 1) * 8.0 + 2.0 * (double)n * b * sv;
+        stats->spmm_bytes = spmm_alg_bytes(A, b, sv, sv);
         stats->spmm_gbs = s1.t_spmm > 0 ? s1.spmm_bytes / (s1.t_spmm * 1e-3) / 1e9 : 0.0;
         stats->ns_per_op = s1.t_spmm > 0 ? s1.t_spmm * 1e6 / ((double)A->nnz * b * s1.spmm_calls) : 0.0;
         stats->spmm_bytes_total = s1.spmm_bytes + s2.spmm_bytes;

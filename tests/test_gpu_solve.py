@@ -268,6 +268,38 @@ def test_bootstrap_small_truncation_pads_random_columns():
     np.testing.assert_allclose(P[:, 2:], OR.normal_block(5, H.n, 4)[:, 2:], rtol=1e-12, atol=1e-14)
 
 
+def test_pivot_overlap_matches_oracle_and_flags_the_missing_sector():
+    """bbl_pivot_overlap against the oracle's Householder-QR overlap (host and
+    device inputs, a rank-deficient pivot), then the diagnostic on the
+    symmetry-sector case: the even pivot's overlap with the true odd-sector
+    eigenvectors is zero, and the eigenvectors the solve converges to from
+    that pivot all overlap it."""
+    import scipy.sparse as sp
+    torch, bbl = need_gpu()
+    rng = np.random.default_rng(12)
+    n = 5000
+    P = rng.standard_normal((n, 4))
+    P[:, 3] = P[:, 0] - 2.0 * P[:, 1]
+    X, _ = np.linalg.qr(rng.standard_normal((n, 8)))
+    X[:, 0] = np.linalg.qr(P[:, :1])[0][:, 0]
+    want = OP.pivot_overlap(P, X)
+    np.testing.assert_allclose(bbl.pivot_overlap(P, X), want, atol=1e-12)
+    np.testing.assert_allclose(bbl.pivot_overlap(to_dev(torch, P), to_dev(torch, X)), want, atol=1e-12)
+    assert abs(want[0] - 1.0) < 1e-12
+    n = 120
+    A = synth.random_sparse_symmetric(n, 6, seed=5).to_scipy()
+    J = sp.csr_matrix((np.ones(n), (np.arange(n), np.arange(n)[::-1])), shape=(n, n))
+    H = synth.csr_from_scipy(A + J @ A @ J)
+    w, U = np.linalg.eigh(H.to_dense())
+    parity = np.sign(np.sum(U * U[::-1], axis=0))
+    p = OR.normal_block(3, n, 2)
+    even = 0.5 * (p + p[::-1])
+    o_true = bbl.pivot_overlap(even, U[:, :6].copy())
+    assert np.all(o_true[parity[:6] < 0] < 1e-12) and np.all(o_true[parity[:6] > 0] > 1e-3)
+    res = bbl.solve(bbl.Matrix(H), 3, 2, pivot=even, tol=1e-9, max_vectors=60)
+    assert np.all(bbl.pivot_overlap(even, res.evecs) > 1e-3)
+
+
 # ----------------------------------------------------------------- errors
 def test_invalid_csr_is_rejected_before_solving():
     torch, bbl = need_gpu()

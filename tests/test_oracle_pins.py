@@ -15,6 +15,7 @@ import synth
 from oracle import lanczos as L
 from oracle import mlp as M
 from oracle import pivot as P
+from oracle import pivot as P_
 from oracle import rng as R
 from oracle.spmm import norm_inf, spmm, spmm_loops
 
@@ -285,6 +286,37 @@ def test_bootstrap_pivot_on_full_space_is_exact():
     np.testing.assert_allclose(th, w[:3], rtol=1e-12)
     r = L.block_lanczos(A, 3, 3, piv, tol=1e-10)
     assert r.iters == 1
+
+
+def test_pivot_overlap_closed_forms():
+    """The overlap of a unit vector with span(P): 1 inside, 0 orthogonal, and
+    cos(t) for a pivot column cos(t) x + sin(t) y with y orthogonal to x; a
+    dependent pivot column changes nothing; scaling P changes nothing."""
+    rng = np.random.default_rng(9)
+    Qf, _ = np.linalg.qr(rng.standard_normal((200, 6)))
+    x, y, z, w = Qf[:, 0], Qf[:, 1], Qf[:, 2], Qf[:, 3]
+    t = 0.3
+    P = np.stack([np.cos(t) * x + np.sin(t) * y, z, 2.0 * z + 0.0 * x], axis=1) * 7.0
+    o = P_.pivot_overlap(P, np.stack([x, y, z, w], axis=1))
+    np.testing.assert_allclose(o, [np.cos(t), np.sin(t), 1.0, 0.0], atol=1e-12)
+
+
+def test_pivot_overlap_flags_the_missing_symmetry_sector():
+    """The paper's intruder case: an even-sector pivot has no overlap with the
+    odd-sector eigenvectors (their overlap is zero to rounding) and a
+    positive one with the even-sector eigenvectors."""
+    import scipy.sparse as sp
+    n = 120
+    A = synth.random_sparse_symmetric(n, 6, seed=5).to_scipy()
+    J = sp.csr_matrix((np.ones(n), (np.arange(n), np.arange(n)[::-1])), shape=(n, n))
+    H = (A + J @ A @ J).toarray()
+    w, U = np.linalg.eigh(H)
+    parity = np.sign(np.sum(U * U[::-1], axis=0))
+    p = R.normal_block(3, n, 2)
+    even = 0.5 * (p + p[::-1])
+    o = P_.pivot_overlap(even, U[:, :6])
+    assert np.all(o[parity[:6] < 0] < 1e-12)
+    assert np.all(o[parity[:6] > 0] > 1e-3)
 
 
 def test_truncated_set_ties_take_lower_index():
