@@ -5,6 +5,13 @@ large-dimension eigenvalue problems" (arXiv 2210.15763):
 
   vector_lanczos   Algorithm 1 (steps 1-6) with full reorthogonalisation of
                    each new vector against all previous ones (Sec. II.A).
+  block_lanczos_thick  the same iteration with thick restart (the remedy
+                   Sec. II.A names for the storage of all vectors): when the
+                   basis is full, keep the `keep` lowest Ritz vectors and the
+                   newest block, and go on.  The projected matrix is then an
+                   arrowhead: the kept Ritz values on the diagonal, coupled
+                   to the newest block only (by B_J times the last block row
+                   of the kept Ritz vectors' coordinates).
   block_lanczos    Eqs. 4-12 (Sec. II.B): W = H V_n; A_n; subtraction;
                    full reorthogonalisation; normalisation into V_{n+1} and
                    B_n, either by the paper's spectral decomposition of the
@@ -299,4 +306,100 @@ def block_lanczos(H, nev: int, b: int, pivot: np.ndarray, tol: float = 1e-8, max
                                  A, B, basis if keep_basis else None, ndefl)
         Vs.append(Vn)
         B.append(Bj)
+    raise AssertionError("unreachable")
+
+
+# --------------------------------------------------------------------------
+# Block Lanczos with thick restart (Sec. II.A names thick restart as the
+# remedy for storing every Lanczos vector)
+# --------------------------------------------------------------------------
+def restarted_projection(theta_kept: np.ndarray, C: np.ndarray, A: list, B: list) -> np.ndarray:
+    """The projected matrix Q^T H Q of a restarted basis Q = [X, V_0, V_1, ...]:
+    diag(theta_kept) for the kept Ritz vectors X, coupled to the first new
+    block V_0 by C (b x keep, block (V_0, X)); then Eq. 12 for the new blocks."""
+    k = theta_kept.size
+    J = len(A)
+    b = A[0].shape[0]
+    T = np.zeros((k + J * b, k + J * b))
+    T[:k, :k] = np.diag(theta_kept)
+    T[k:k + b, :k] = C
+    T[:k, k:k + b] = C.T
+    T[k:, k:] = block_tridiagonal(A, B)
+    return T
+
+
+def block_lanczos_thick(H, nev: int, b: int, pivot: np.ndarray, tol: float = 1e-8, max_vectors: int = 2000,
+                        keep: int = 0, max_blocks: int = 100000, normaliser: str = "cholqr2",
+                        reorth_passes: int = 2, defl_tol: float = 1e-10, seed: int = 0,
+                        keep_basis: bool = False) -> LanczosResult:
+    """Block Lanczos for the nev lowest eigenpairs with thick restart.
+
+    The block step is block_lanczos's (Eqs. 4-12, both Gram-Schmidt passes
+    against every stored vector).  When the stored vectors (kept Ritz vectors
+    plus blocks) could not take one more block, the restart keeps
+    X = Q S[:, :keep] (the keep lowest Ritz vectors), their Ritz values theta
+    and the newest block V_{J+1}: since H Q = Q T + V_{J+1} B_J E_J^T, the
+    new basis [X, V_{J+1}] has the projection
+        [[diag(theta), C^T], [C, A']],   C = B_J E_J^T S[:, :keep],
+    and the next block's subtraction (Eq. 8) includes X C^T.  `iters`
+    counts every block (SpMM) over all restarts; the run stops after
+    max_blocks blocks.  keep = 0: no restart (as block_lanczos)."""
+    n = pivot.shape[0]
+    nrm = norm_inf(H)
+    thresh2 = (defl_tol * nrm) ** 2
+    norm_fn = {"cholqr2": cholqr2, "spectral": spectral_normalise}[normaliser]
+    if keep and (keep < nev or keep + 2 * b > max_vectors):
+        raise ValueError("thick restart needs nev <= keep and keep + 2b <= max_vectors")
+    P = np.asarray(pivot, dtype=np.float64)
+    pthresh = (1e-10 * max(1e-300, float(np.max(np.linalg.norm(P, axis=0))))) ** 2
+    V1, _, d0 = norm_fn(P, pthresh, None, lambda i: deflation_vector(seed, 0, i, n))
+    X = np.zeros((n, 0))
+    theta_kept = np.zeros(0)
+    C = np.zeros((b, 0))
+    Vs = [V1]
+    A, B = [], []
+    hist = []
+    ndefl = len(d0)
+    restarts = 0
+    for blocks in range(1, max_blocks + 1):
+        j = len(Vs) - 1
+        W = spmm(H, Vs[j])                                     # Eq. 4
+        Aj = Vs[j].T @ W                                       # Eq. 7 (read)
+        Aj = 0.5 * (Aj + Aj.T)
+        W = W - Vs[j] @ Aj                                     # Eq. 8
+        if j > 0:
+            W = W - Vs[j - 1] @ B[j - 1].T
+        elif X.shape[1]:
+            W = W - X @ C.T                                    # the restart coupling
+        basis = np.hstack([X] + Vs)
+        for _ in range(reorth_passes):                         # full reorthogonalisation
+            W = cgs_pass(W, basis)
+        Vn, Bj, d = norm_fn(W, thresh2, basis, lambda i: deflation_vector(seed, blocks, i, n))
+        ndefl += len(d)
+        A.append(Aj)
+        T = restarted_projection(theta_kept, C, A, B) if X.shape[1] else block_tridiagonal(A, B)
+        theta, S = np.linalg.eigh(T)
+        hist.append(theta.copy())
+        m = T.shape[0]
+        k = min(nev, m)
+        est = np.linalg.norm(Bj @ S[m - b:, :k], axis=0)
+        done = k == nev and bool(np.all(est <= tol * nrm))
+        full = X.shape[1] + (j + 2) * b > max_vectors
+        if done or blocks == max_blocks or (full and not keep):
+            Xr = sign_normalise(basis @ S[:, :k])
+            R = spmm(H, Xr) - Xr * theta[:k]
+            res = LanczosResult(theta[:k], Xr, np.linalg.norm(R, axis=0), est, blocks, bool(done), hist, T,
+                                A, B, basis if keep_basis else None, ndefl)
+            res.restarts = restarts
+            return res
+        if full:                                               # thick restart
+            Sk = S[:, :keep]
+            X = basis @ Sk
+            theta_kept = theta[:keep].copy()
+            C = Bj @ Sk[m - b:, :]
+            Vs, A, B = [Vn], [], []
+            restarts += 1
+        else:
+            Vs.append(Vn)
+            B.append(Bj)
     raise AssertionError("unreachable")

@@ -76,3 +76,20 @@ def test_wrong_sign_in_gram_schmidt_is_caught(monkeypatch):
 def test_dropped_reorthogonalisation_is_caught(monkeypatch):
     monkeypatch.setattr(L, "cgs_pass", lambda W, Q: W)
     assert _fails(_orthonormality_error, 1e-12)
+
+
+def test_thick_restart_without_the_coupling_is_caught(monkeypatch):
+    # the restart's coupling C between the kept Ritz vectors and the newest
+    # block dropped from the projected matrix: the restarted runs no longer
+    # reach the dense spectrum
+    A = synth.random_sparse_symmetric(300, 6, seed=34)
+    want = np.linalg.eigvalsh(A.to_dense())[:4]
+    orig = L.restarted_projection
+    monkeypatch.setattr(L, "restarted_projection", lambda th, C, As, Bs: orig(th, 0.0 * C, As, Bs))
+
+    def err():
+        r = L.block_lanczos_thick(A, 4, 4, R.normal_block(2, A.n, 4), tol=1e-10, max_vectors=24, keep=8,
+                                  max_blocks=400)
+        return np.max(np.abs(r.evals - want) / np.abs(want)) if r.converged else np.inf
+
+    assert _fails(err, 1e-10)

@@ -238,6 +238,56 @@ def test_block_lanczos_deflation_branch_reaches_the_dense_spectrum(normaliser):
     np.testing.assert_allclose(r.evals, other.evals, rtol=1e-10)
 
 
+# ----------------------------------------------------------------- thick restart
+def test_thick_restart_off_is_block_lanczos():
+    A = synth.random_sparse_symmetric(300, 6, seed=33)
+    piv = R.normal_block(1, A.n, 4)
+    a = L.block_lanczos(A, 4, 4, piv, tol=1e-10)
+    t = L.block_lanczos_thick(A, 4, 4, piv, tol=1e-10, keep=0)
+    assert t.iters == a.iters and t.restarts == 0
+    np.testing.assert_allclose(t.evals, a.evals, rtol=1e-13)
+
+
+@pytest.mark.parametrize("b,keep,mv", [(4, 8, 24), (4, 12, 32), (2, 6, 16), (1, 4, 10)])
+def test_thick_restart_reaches_the_dense_spectrum(b, keep, mv):
+    A = synth.random_sparse_symmetric(300, 6, seed=34)
+    w = np.linalg.eigvalsh(A.to_dense())[:4]
+    r = L.block_lanczos_thick(A, 4, b, R.normal_block(2, A.n, b), tol=1e-10, max_vectors=mv, keep=keep)
+    assert r.converged and r.restarts >= 1
+    np.testing.assert_allclose(r.evals, w, rtol=1e-10)
+    assert np.all(r.resid <= 1e-10 * norm_inf(A) * 1.01)
+
+
+def test_thick_restart_laplacian_closed_form():
+    n = 400
+    H = synth.laplacian_1d(n)
+    r = L.block_lanczos_thick(H, 3, 2, R.normal_block(3, n, 2), tol=1e-10, max_vectors=40, keep=8, max_blocks=20000)
+    assert r.converged and r.restarts >= 1
+    np.testing.assert_allclose(r.evals, lap1d_eigs(n)[:3], rtol=1e-9)
+
+
+def test_thick_restart_keeps_an_orthonormal_basis_and_its_projection():
+    """After restarts the stored basis Q = [X, V_0, ...] is orthonormal and
+    Q^T H Q is the arrowhead-plus-Eq.-12 matrix the method solves."""
+    A = synth.kron_matrix("kron_n2e4", scale=0.3)
+    r = L.block_lanczos_thick(A, 4, 4, R.normal_block(4, A.n, 4), tol=1e-30, max_vectors=40, keep=8,
+                              max_blocks=30, keep_basis=True)
+    assert r.restarts >= 2
+    Q = r.V
+    assert np.max(np.abs(Q.T @ Q - np.eye(Q.shape[1]))) < 1e-12
+    np.testing.assert_allclose(Q.T @ spmm(A, Q), r.T, atol=1e-9 * norm_inf(A))
+
+
+def test_thick_restart_ritz_values_never_increase():
+    """The kept Ritz vectors span a subspace of every later basis, so by the
+    minimax principle each of the lowest Ritz values can only decrease."""
+    A = synth.random_sparse_symmetric(300, 6, seed=35)
+    r = L.block_lanczos_thick(A, 4, 4, R.normal_block(5, A.n, 4), tol=1e-12, max_vectors=24, keep=8)
+    assert r.restarts >= 2
+    low = np.array([h[:4] for h in r.theta_history if h.size >= 4])
+    assert np.all(np.diff(low, axis=0) <= 1e-12 * norm_inf(A))
+
+
 def test_block_tridiagonal_layout():
     A = [np.full((2, 2), 1.0), np.full((2, 2), 2.0)]
     B = [np.array([[3.0, 4.0], [0.0, 5.0]])]
