@@ -105,10 +105,24 @@ typedef struct {
                                    the bulk; the FP32 second pass removes the
                                    rest and A_j sums both passes' coefficients);
                                    0: both passes read the FP32 basis             */
+    int restart_keep;           /* thick restart (Sec. II.A: the remedy for storing
+                                   every Lanczos vector).  0 (default): none -- a
+                                   stage that fills max_vectors stops with
+                                   BBL_ERR_NOT_CONVERGED.  k > 0: when the basis is
+                                   full, keep the k lowest Ritz vectors and the
+                                   newest block and go on (k a multiple of b,
+                                   nev <= k <= 16, k + 2b <= max_vectors; the
+                                   polish stage, of block size nev, keeps
+                                   k rounded up to a multiple of nev).  The kept
+                                   vectors are rotated so that the projected
+                                   matrix stays block tridiagonal.              */
+    int max_blocks;             /* with restart_keep: cap on the blocks (SpMM
+                                   calls) of a stage; 0 (default) = 10000        */
 } bbl_options;
 
 typedef struct {
-    int iters;                  /* block iterations (SpMM calls) in the main stage */
+    int iters;                  /* block iterations (SpMM calls) in the main stage,
+                                   over all thick restarts                        */
     int vec_equiv_iters;        /* iters * b (Sec. III.A's vector-equivalent count) */
     int polish_iters;           /* FP64 block iterations of the polish stage       */
     int deflations;
@@ -128,6 +142,7 @@ typedef struct {
     double gram_bytes_total;    /* their algorithmic bytes: (n*m + n*b)*s each
                                    (n*m*2 + n*b*4 when read from the FP16 copy)    */
     int spmm_calls;             /* main stage SpMM launches (spmm_gbs is over them) */
+    int restarts;               /* thick restarts of all stages                   */
 } bbl_stats;
 
 void bbl_options_default(bbl_options* opt);

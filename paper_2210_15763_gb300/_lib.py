@@ -17,7 +17,8 @@ class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_vectors", C.c_int), ("criterion", C.c_int), ("rms_tol", C.c_double),
                 ("seed", C.c_uint64), ("defl_tol", C.c_double), ("storage", C.c_int), ("polish", C.c_int),
                 ("stage1_tol", C.c_double), ("check_every", C.c_int), ("stream", C.c_void_p),
-                ("ritz_overlap", C.c_int), ("half_first_pass", C.c_int)]
+                ("ritz_overlap", C.c_int), ("half_first_pass", C.c_int), ("restart_keep", C.c_int),
+                ("max_blocks", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -27,7 +28,8 @@ class Stats(C.Structure):
                 ("t_total_ms", C.c_double), ("spmm_bytes", C.c_double), ("spmm_gbs", C.c_double),
                 ("ns_per_op", C.c_double), ("ortho_err", C.c_double), ("spmm_bytes_total", C.c_double),
                 ("reorth_bytes_total", C.c_double), ("ritz_solves", C.c_int), ("gram_calls", C.c_int),
-                ("t_gram_ms", C.c_double), ("gram_bytes_total", C.c_double), ("spmm_calls", C.c_int)]
+                ("t_gram_ms", C.c_double), ("gram_bytes_total", C.c_double), ("spmm_calls", C.c_int),
+                ("restarts", C.c_int)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -160,6 +160,148 @@ __global__ void scale_cols_kernel(int64_t n, int k, const double* __restrict__ s
 
 constexpr int kRedBlocks = 304;
 
+// ------------------------------------------------------------------ thick restart
+// When the basis Q of J blocks is full: H Q = Q T + V_{J+1} B_J E_J^T.  The
+// k lowest Ritz pairs (theta, S) of T give X = Q S_k with
+// H X = X diag(theta) + V_{J+1} C, C = B_J E_J^T S_k (b x k): in the basis
+// [X, V_{J+1}] the projection is an arrowhead.  A small block Lanczos on
+// diag(theta) started from C^T turns X into blocks Y_1..Y_r (r = k/b) whose
+// projection is block tridiagonal with the coupling to V_{J+1} on the last
+// one only; ordering them Y_r, ..., Y_1, V_{J+1} keeps T banded, so the
+// Lanczos recurrence and the banded Ritz solve go on unchanged.  Each block
+// of the small Lanczos is normalised "QL"-style (the QR of its columns in
+// reverse order), which makes every coupling block of the reversed order
+// upper triangular, as the band storage wants.
+constexpr int kRestartMaxK = 16;
+
+// One CTA.  theta[k], S (m x k row-major): the k lowest Ritz pairs of the
+// band Tb (m rows; B_J in rows m..m+b-1).  Out: G (m x k row-major), the
+// coordinates of the new blocks in Q (block t = columns t*b..t*b+b-1), and
+// band rows 0..k+b-1 of the restarted T (the diagonal block of V_{J+1},
+// rows k..k+b-1, is left zero for the next Gram-Schmidt pass to fill).
+// status: bit 0 set if a value is not finite.
+__global__ void __launch_bounds__(256) restart_kernel(int m, int b, int k, const double* __restrict__ theta,
+                                                      const double* __restrict__ S, double* __restrict__ Tb,
+                                                      double* __restrict__ G, int* __restrict__ status) {
+    __shared__ double th[kRestartMaxK];
+    __shared__ double C[kMaxB * kRestartMaxK];          // b x k
+    __shared__ double Z[kRestartMaxK * kRestartMaxK];   // column c of the new basis at Z[c * k + i]
+    __shared__ double M[kRestartMaxK * kRestartMaxK];   // Z^T diag(theta) Z
+    __shared__ double U[kMaxB * kMaxB];                 // C times the last new block (b x b)
+    const int t = threadIdx.x;
+    const int r = k / b;
+    if (t < k) th[t] = theta[t];
+    // C[x][i] = sum_{c >= x} B_J[x][c] S[m - b + c][i]; B_J[x][c] at band row m + x, d = b + x - c
+    for (int e = t; e < b * k; e += blockDim.x) {
+        const int x = e / k, i = e % k;
+        double s = 0.0;
+        for (int c = x; c < b; ++c) s += Tb[(int64_t)(m + x) * (b + 1) + (b + x - c)] * S[(int64_t)(m - b + c) * k + i];
+        C[e] = s;
+    }
+    __syncthreads();
+    if (t == 0) {
+        // Q columns of the small Lanczos in creation order; block i (0-based)
+        // holds columns i*b .. i*b+b-1 of Qc, already in reversed ("QL") order
+        double Qc[kRestartMaxK * kRestartMaxK];
+        int nz = 0;
+        for (int blk = 0; blk < r; ++blk) {
+            double Wc[kMaxB * kRestartMaxK];  // b columns of length k, reversed column order
+            for (int c = 0; c < b; ++c)
+                for (int i = 0; i < k; ++i) {
+                    const int src = b - 1 - c;
+                    Wc[c * k + i] = blk == 0 ? C[src * k + i] : th[i] * Qc[((blk - 1) * b + src) * k + i];
+                }
+            for (int c = 0; c < b; ++c) {
+                double* v = Wc + c * k;
+                double orig = 0.0;
+                for (int i = 0; i < k; ++i) orig += v[i] * v[i];
+                orig = sqrt(orig);
+                for (int pass = 0; pass < 2; ++pass)
+                    for (int l = 0; l < nz; ++l) {
+                        double dt = 0.0;
+                        for (int i = 0; i < k; ++i) dt += Qc[l * k + i] * v[i];
+                        for (int i = 0; i < k; ++i) v[i] -= dt * Qc[l * k + i];
+                    }
+                double nrm = 0.0;
+                for (int i = 0; i < k; ++i) nrm += v[i] * v[i];
+                nrm = sqrt(nrm);
+                if (!(orig > 0.0) || !(nrm > 1e-10 * orig)) {
+                    // dependent: the first unit vector left with half its length
+                    // after two passes against the columns so far
+                    for (int u = 0; u < k; ++u) {
+                        for (int i = 0; i < k; ++i) v[i] = (i == u) ? 1.0 : 0.0;
+                        for (int pass = 0; pass < 2; ++pass)
+                            for (int l = 0; l < nz; ++l) {
+                                double dt = 0.0;
+                                for (int i = 0; i < k; ++i) dt += Qc[l * k + i] * v[i];
+                                for (int i = 0; i < k; ++i) v[i] -= dt * Qc[l * k + i];
+                            }
+                        nrm = 0.0;
+                        for (int i = 0; i < k; ++i) nrm += v[i] * v[i];
+                        nrm = sqrt(nrm);
+                        if (nrm > 0.5) break;
+                    }
+                }
+                for (int i = 0; i < k; ++i) Qc[nz * k + i] = v[i] / nrm;
+                ++nz;
+            }
+            // un-reverse: block blk's columns in natural order
+            for (int c = 0; c < b / 2; ++c)
+                for (int i = 0; i < k; ++i) {
+                    const double a = Qc[(blk * b + c) * k + i];
+                    Qc[(blk * b + c) * k + i] = Qc[(blk * b + b - 1 - c) * k + i];
+                    Qc[(blk * b + b - 1 - c) * k + i] = a;
+                }
+        }
+        // new block t = small-Lanczos block r - 1 - t (the one coupled to V_{J+1} last)
+        for (int tt = 0; tt < r; ++tt)
+            for (int c = 0; c < b; ++c)
+                for (int i = 0; i < k; ++i) Z[(tt * b + c) * k + i] = Qc[((r - 1 - tt) * b + c) * k + i];
+    }
+    __syncthreads();
+    for (int e = t; e < k * k; e += blockDim.x) {
+        const int x = e / k, y = e % k;
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s += Z[x * k + i] * th[i] * Z[y * k + i];
+        M[e] = s;
+    }
+    for (int e = t; e < b * b; e += blockDim.x) {
+        const int x = e / b, y = e % b;
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s += C[x * k + i] * Z[((r - 1) * b + y) * k + i];
+        U[e] = s;
+    }
+    __syncthreads();
+    for (int64_t e = t; e < (int64_t)m * k; e += blockDim.x) {
+        const int64_t row = e / k;
+        const int col = (int)(e % k);
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s += S[row * k + i] * Z[col * k + i];
+        G[e] = s;
+        if (!isfinite(s)) atomicOr(status, 1);
+    }
+    for (int e = t; e < (k + b) * (b + 1); e += blockDim.x) {
+        const int row = e / (b + 1), d = e % (b + 1);
+        const int col = row - d;
+        double v = 0.0;
+        if (col >= 0) {
+            if (row < k) v = M[row * k + col];
+            else if (col < k) v = U[(row - k) * b + (col - (r - 1) * b)];
+        }
+        Tb[e] = v;
+    }
+}
+
+// the kept vectors Y (n x k FP64, row-major) into basis blocks 0..k/b-1
+template <typename T>
+__global__ void restart_store_kernel(int64_t n, int b, int k, const double* __restrict__ Y, T* __restrict__ basis) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / k;
+        const int c = (int)(e % k);
+        basis[(int64_t)(c / b) * n * b + i * b + (c % b)] = T(Y[e]);
+    }
+}
+
 struct Timer {
     cudaEvent_t ev[6] = {};
     bool ok = false;
@@ -187,6 +329,7 @@ struct StageOut {
     double spmm_bytes = 0, reorth_bytes = 0;
     double t_gram = 0, gram_bytes = 0;  // the first Gram-Schmidt pass's Gram (kernel + partial reduction)
     int gram_calls = 0;
+    int restarts = 0;
 };
 
 // Normalise columns of X (FP64, n x k) to the sign convention and compute the
@@ -293,7 +436,7 @@ struct CheckPlan {
 // FP64 n x nev_eff) holds the Ritz vectors, theta_dev the Ritz values.
 bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivot_dev, int dtype, bool f64_spmm,
                          double tol, const bbl_options& o, cudaStream_t st, double* X, double* theta_dev,
-                         StageOut& out) {
+                         StageOut& out, int keep = 0) {
     const int64_t n = A->n;
     const size_t s = dtype_size(dtype);
     const double nrm = A->norm_inf > 0 ? A->norm_inf : 1.0;
@@ -316,6 +459,14 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     }
     const int m_max = J_max * b;
     if (nev > m_max) return set_error(BBL_ERR_INVALID_ARG, "solve: nev=%d exceeds the basis capacity %d", nev, m_max);
+    // thick restart: keep/b blocks of kept Ritz vectors + the newest block
+    const bool restart_on = keep > 0;
+    const int r_keep = restart_on ? keep / b : 0;
+    if (restart_on && (keep % b != 0 || keep < nev || keep > kRestartMaxK || r_keep + 2 > J_max))
+        return set_error(BBL_ERR_INVALID_ARG,
+                         "solve: restart_keep=%d must be a multiple of b=%d, >= nev=%d, <= %d, with room for %d more "
+                         "blocks (basis capacity %d blocks)", keep, b, nev, kRestartMaxK, 2, J_max);
+    const int max_total = restart_on ? (o.max_blocks > 0 ? o.max_blocks : 10000) : J_max;
     DevBuf Z, coeff, partials, small, Tb, S, rwork, flags, bj;
     PoolBuf basis;
     // float-float blocks: FP32 copies of the basis (high parts) and of W for
@@ -458,10 +609,10 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     int final_k = 0;
     CheckPlan plan;
     plan.every = (o.check_every > 0 || o.criterion == 1) ? std::max(1, o.check_every) : 0;
-    auto launch_ritz = [&](int jj) -> bbl_status {
+    auto launch_ritz = [&](int jj, int tt) -> bbl_status {
         const int m = (jj + 1) * b;
         const int k = std::min(nev, m);
-        const int slot = jj & 1;
+        const int slot = tt & 1;
         BBL_CUDA(cudaStreamWaitEvent(side, ev_main[slot], 0));
         BBL_CUDA(cudaEventRecord(ev_r0[slot], side));
         double* th = theta2.as<double>() + 64 * slot;
@@ -479,11 +630,13 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         BBL_CUDA(cudaEventRecord(ev_r1[slot], side));
         return BBL_OK;
     };
-    // waits for the report of block jj; returns 1 when converged
-    auto check_ritz = [&](int jj, bool* done) -> bbl_status {
+    // waits for the report of block jj (basis position; tt: its index over
+    // all restarts); returns 1 when converged
+    int final_t = -1;
+    auto check_ritz = [&](int jj, int tt, bool* done) -> bbl_status {
         const int m = (jj + 1) * b;
         const int k = std::min(nev, m);
-        const int slot = jj & 1;
+        const int slot = tt & 1;
         BBL_CUDA(cudaEventSynchronize(ev_r1[slot]));
         out.t_ritz += [&] { float t = 0.f; cudaEventElapsedTime(&t, ev_r0[slot], ev_r1[slot]); return (double)t; }();
         const double* ht = h_theta + 32 * slot;
@@ -498,7 +651,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         if (k == nev) {
             double rho = 0.0;
             for (int i = 0; i < nev; ++i) rho = std::max(rho, he[i] / (tol * nrm));
-            plan.report(jj, rho);
+            plan.report(tt, rho);
             if (o.criterion == 1) {
                 if (prev_theta.size() == (size_t)nev) {
                     double ss = 0.0;
@@ -512,12 +665,51 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         }
         prev_theta.assign(ht, ht + k);
         final_j = jj;
+        final_t = tt;
         final_k = k;
         return BBL_OK;
     };
-    int j = 0;
+    // thick restart at the full block jf (its report checked, not converged;
+    // V_{J+1} normalised in Wn): blocks 0..r_keep-1 <- Q G, block r_keep <- Wn,
+    // band rows 0..keep+b-1 rebuilt
+    DevBuf th_r, S_r, G_r, Y_r, st_r;
+    auto thick_restart = [&](int jf, const char* Wn) -> bbl_status {
+        const int m = (jf + 1) * b;
+        if (!th_r.p) {
+            BBL_TRY(th_r.alloc(sizeof(double) * 64));
+            BBL_TRY(S_r.alloc(sizeof(double) * (size_t)m_max * keep));
+            BBL_TRY(G_r.alloc(sizeof(double) * (size_t)m_max * keep));
+            BBL_TRY(Y_r.alloc(sizeof(double) * (size_t)n * keep));
+            BBL_TRY(st_r.alloc(sizeof(int) * 4));
+        }
+        BBL_CUDA(cudaStreamSynchronize(side));
+        BBL_CUDA(cudaMemsetAsync(st_r.p, 0, sizeof(int) * 4, st));
+        BBL_TRY(ritz_dev(m, b, keep, Tb.as<double>(), th_r.as<double>(), S_r.as<double>(), rwork, st));
+        restart_kernel<<<1, 256, 0, st>>>(m, b, keep, th_r.as<double>(), S_r.as<double>(), Tb.as<double>(),
+                                          G_r.as<double>(), st_r.as<int>());
+        BBL_LAUNCH_CHECK();
+        BBL_TRY(ritz_vectors(n, b, jf + 1, dtype, basis.p, keep, G_r.as<double>(), Y_r.as<double>(), st));
+        if (dtype == BBL_FP64)
+            restart_store_kernel<double><<<cg, 256, 0, st>>>(n, b, keep, Y_r.as<double>(), basis.as<double>());
+        else if (dtype == kDF32)
+            restart_store_kernel<df32><<<cg, 256, 0, st>>>(n, b, keep, Y_r.as<double>(), basis.as<df32>());
+        else
+            restart_store_kernel<float><<<cg, 256, 0, st>>>(n, b, keep, Y_r.as<double>(), basis.as<float>());
+        BBL_LAUNCH_CHECK();
+        BBL_CUDA(cudaMemcpyAsync(blockp(r_keep), Wn, (size_t)n * b * s, cudaMemcpyDeviceToDevice, st));
+        for (int q = 0; q <= r_keep; ++q) BBL_TRY(shadow_block(q));
+        int hs = 0;
+        BBL_CUDA(cudaMemcpyAsync(&hs, st_r.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BBL_CUDA(cudaStreamSynchronize(st));
+        if (hs) return set_error(BBL_ERR_NUMERICAL, "solve: non-finite values in the thick restart");
+        ++out.restarts;
+        return BBL_OK;
+    };
+    int j = 0;        // basis position of the current block
+    int tb = 0;       // its index over all restarts (SpMM calls so far)
+    int pending_t = -1;
     bool stop = false;
-    for (j = 0; j < J_max && !stop; ++j) {
+    while (!stop) {
         char* Vj = blockp(j);
         char* Wn = (j + 1 < J_max) ? blockp(j + 1) : Z.as<char>();
         BBL_CUDA(cudaEventRecord(tm.ev[0], st));
@@ -528,7 +720,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         // ritz_overlap = 2: the Gram-Schmidt passes wait for the Ritz solve in
         // flight, which then shares the GPU with this SpMM only (the wait is
         // counted in the SpMM phase)
-        if (o.ritz_overlap == 2 && pending >= 0) BBL_CUDA(cudaStreamWaitEvent(st, ev_r1[pending & 1], 0));
+        if (o.ritz_overlap == 2 && pending >= 0) BBL_CUDA(cudaStreamWaitEvent(st, ev_r1[pending_t & 1], 0));
         BBL_CUDA(cudaEventRecord(tm.ev[1], st));
         double* C1 = coeff.as<double>();
         double* C2 = C1 + (size_t)m_max * b;
@@ -556,7 +748,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         fill_B_kernel<<<1, 256, 0, st>>>(j, b, t_rows, bj.as<double>(), Tb.as<double>());
         BBL_LAUNCH_CHECK();
         BBL_CUDA(cudaEventRecord(tm.ev[3], st));
-        BBL_CUDA(cudaEventRecord(ev_main[j & 1], st));
+        BBL_CUDA(cudaEventRecord(ev_main[tb & 1], st));
         BBL_CUDA(cudaMemcpyAsync(h_ndefl, d_ndefl, sizeof(int), cudaMemcpyDeviceToHost, st));
         BBL_CUDA(cudaStreamSynchronize(st));
         out.t_spmm += tm.ms(0, 1);
@@ -574,17 +766,21 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             // two passes of Gram + update; an FP16 first-pass Gram reads 2 bytes per basis element
             out.reorth_bytes += (half1 ? 3.5 : 4.0) * (double)n * m * sx + 6.0 * (double)n * b * sx;
         }
-        out.spmm_calls = j + 1;
-        const bool last = (j == J_max - 1);
-        const bool want = plan.want(j) || last || (j + 1) * b < nev;
+        out.spmm_calls = tb + 1;
+        const bool full = (j == J_max - 1);
+        const bool last = (tb == max_total - 1) || (full && !restart_on);
+        const bool want = plan.want(tb) || last || full || (j + 1) * b < nev;
         if (want) {
             // a new Ritz solve may reuse the buffers of block j-2 only: the one of block j-1 is pending
-            BBL_TRY(launch_ritz(j));
+            BBL_TRY(launch_ritz(j, tb));
         }
-        if (serial && want) pending = j;  // read this block's report now
+        if (serial && want) {  // read this block's report now
+            pending = j;
+            pending_t = tb;
+        }
         if (pending >= 0) {
             bool done = false;
-            BBL_TRY(check_ritz(pending, &done));
+            BBL_TRY(check_ritz(pending, pending_t, &done));
             pending = -1;
             if (done) {
                 out.converged = true;
@@ -592,31 +788,54 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
                 break;
             }
         }
-        if (want && !serial) pending = j;
+        if (want && !serial) {
+            pending = j;
+            pending_t = tb;
+        }
         if (last) break;
         if (h_ndefl[0] > last_defl) {
             BBL_TRY(replace_deflated(j + 1, Wn, d_mask));
             last_defl = h_ndefl[0];
             if (exhausted) break;  // no direction left to extend the basis with
         }
+        if (full) {
+            // the basis is full: this block's report decides between stopping
+            // and a thick restart
+            if (pending >= 0) {  // (in line, ritz_overlap = 0, it was read above)
+                bool done = false;
+                BBL_TRY(check_ritz(pending, pending_t, &done));
+                pending = -1;
+                if (done) {
+                    out.converged = true;
+                    break;
+                }
+            }
+            BBL_TRY(thick_restart(j, Wn));
+            j = r_keep;
+            ++tb;
+            continue;
+        }
         BBL_TRY(shadow_block(j + 1));
+        ++j;
+        ++tb;
     }
     if (pending >= 0 && !stop) {
         bool done = false;
-        BBL_TRY(check_ritz(pending, &done));
+        BBL_TRY(check_ritz(pending, pending_t, &done));
         out.converged = done;
     }
     BBL_CUDA(cudaStreamSynchronize(side));
     out.deflations = last_defl;
     if (final_j < 0) return set_error(BBL_ERR_NUMERICAL, "solve: no Ritz solve completed");
-    out.iters = final_j + 1;
+    out.iters = final_t + 1;
     out.nev_eff = final_k;
-    const int slot = final_j & 1;
+    const int slot = final_t & 1;
     BBL_CUDA(cudaMemcpyAsync(theta_dev, theta2.as<double>() + 64 * slot, sizeof(double) * final_k,
                              cudaMemcpyDeviceToDevice, st));
     // Ritz vectors X = Q S (k columns) from the blocks of the returned T
     BBL_CUDA(cudaEventRecord(tm.ev[0], st));
-    BBL_TRY(ritz_vectors(n, b, out.iters, dtype, basis.p, final_k, S2.as<double>() + (size_t)slot * m_max * nev, X, st));
+    BBL_TRY(ritz_vectors(n, b, final_j + 1, dtype, basis.p, final_k, S2.as<double>() + (size_t)slot * m_max * nev, X,
+                         st));
     BBL_CUDA(cudaEventRecord(tm.ev[1], st));
     BBL_CUDA(cudaStreamSynchronize(st));
     out.t_other += tm.ms(0, 1);
@@ -660,11 +879,11 @@ bbl_status solve_impl(const bbl_matrix* A, int nev, int b, const double* pivot, 
     std::vector<double> res(nev, 0.0);
     if (!mixed) {
         BBL_TRY(lanczos_stage(A, nev, b, piv.as<double>(), BBL_FP64, false, o.tol, o, st, X.as<double>(),
-                              theta.as<double>(), s1));
+                              theta.as<double>(), s1, o.restart_keep));
     } else {
         const double t1tol = o.polish ? std::max(o.tol, o.stage1_tol) : o.tol;
         BBL_TRY(lanczos_stage(A, nev, b, piv.as<double>(), BBL_FP32, false, t1tol, o, st, X.as<double>(),
-                              theta.as<double>(), s1));
+                              theta.as<double>(), s1, o.restart_keep));
     }
     int k = s1.nev_eff;
     // before a polish the stage-1 residuals only decide whether it runs
@@ -682,8 +901,10 @@ bbl_status solve_impl(const bbl_matrix* A, int nev, int b, const double* pivot, 
             // polish 1: float-float blocks and products (FP32 pipes, ~48-bit);
             // polish 2: FP64 blocks and FP64 arithmetic
             const int pdt = o.polish == 2 ? BBL_FP64 : kDF32;
+            // the polish's block size is k: its restart keeps a multiple of k
+            const int keep2 = o.restart_keep > 0 ? std::min(kRestartMaxK, (int)ceil_div(o.restart_keep, k) * k) : 0;
             BBL_TRY(lanczos_stage(A, nev, k, piv.as<double>(), pdt, true, o.tol, o2, st, X.as<double>(),
-                                  theta.as<double>(), s2));
+                                  theta.as<double>(), s2, keep2));
             k = s2.nev_eff;
             BBL_TRY(finish_vectors(A, k, X.as<double>(), theta.as<double>(), res.data(), scratch, st));
             ok = s2.converged && k == nev;
@@ -727,6 +948,7 @@ bbl_status solve_impl(const bbl_matrix* A, int nev, int b, const double* pivot, 
         stats->t_gram_ms = s1.t_gram;
         stats->gram_bytes_total = s1.gram_bytes;
         stats->spmm_calls = s1.spmm_calls;
+        stats->restarts = s1.restarts + s2.restarts;
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
