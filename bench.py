@@ -565,7 +565,8 @@ def run_batched(args):
            "iters_max": int(it.max()), "iters_mean": float(it.mean()), "iters_single_mean": float(np.mean(its1)) if its1 else None,
            "max_resid_rel": float(np.max(rs.max(axis=1) / nrm)),
            "schedule": {k: best[k] for k in ("fmt", "lanes", "sigma", "ms", "class")},
-           "graph_kernels_per_iteration": stats["polish_iters"], "graph": graph, "generate_s": tgen}
+           "polish_iters_max": stats["polish_iters"],
+           "graph_kernels_per_iteration": stats["graph_kernels"], "graph": graph, "generate_s": tgen}
     print(json.dumps(out))
 
 

@@ -143,6 +143,8 @@ typedef struct {
                                    (n*m*2 + n*b*4 when read from the FP16 copy)    */
     int spmm_calls;             /* main stage SpMM launches (spmm_gbs is over them) */
     int restarts;               /* thick restarts of all stages                   */
+    int graph_kernels;          /* batched form: kernels in one captured block
+                                   iteration                                      */
 } bbl_stats;
 
 void bbl_options_default(bbl_options* opt);
@@ -414,9 +416,15 @@ bbl_status bbl_batch_set_schedule(bbl_batch* B, int lanes_per_row);
  * with use_graph = 0 the host drives the same sequence.  Each problem stops
  * when its nev estimates ||B_j s_i[last b]|| are <= tol*||H_s||_inf, tested
  * on opt->check_every's schedule (0: adaptive, per problem, as in
- * bbl_solve); random pivots (opt->seed).  Outputs (host): evals, resid [count x nev] (true FP64
- * residuals), iters [count], status [count] (BBL_OK, BBL_ERR_NOT_CONVERGED,
- * BBL_ERR_NUMERICAL for a breakdown).  b in {1, 2, 4, 8, 16}, nev <= 16.
+ * bbl_solve); random pivots (opt->seed).  FP32 storage with opt->polish
+ * (default on) and nev in {1, 2, 4, 8, 16}: the problems whose true FP64
+ * residuals miss tol after the FP32 run go on from their FP32 Ritz vectors
+ * (block size nev) with FP64 blocks and FP64 arithmetic on the FP32 values,
+ * in a second lock-step run over those problems only.  Outputs (host):
+ * evals, resid [count x nev] (true FP64 residuals), iters [count] (blocks of
+ * both runs), status [count] (BBL_OK when the true residuals meet tol,
+ * BBL_ERR_NOT_CONVERGED, BBL_ERR_NUMERICAL for a breakdown).
+ * b in {1, 2, 4, 8, 16}, nev <= 16.
  * Returns BBL_OK when every problem converged.                           */
 bbl_status bbl_batch_solve(bbl_batch* B, int nev, int b, const bbl_options* opt, int use_graph, double* evals,
                            double* resid, int* iters, int* status, bbl_stats* stats);

@@ -29,7 +29,7 @@ class Stats(C.Structure):
                 ("ns_per_op", C.c_double), ("ortho_err", C.c_double), ("spmm_bytes_total", C.c_double),
                 ("reorth_bytes_total", C.c_double), ("ritz_solves", C.c_int), ("gram_calls", C.c_int),
                 ("t_gram_ms", C.c_double), ("gram_bytes_total", C.c_double), ("spmm_calls", C.c_int),
-                ("restarts", C.c_int)]
+                ("restarts", C.c_int), ("graph_kernels", C.c_int)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -19,6 +19,7 @@
 // its estimate ||B_j s_i[last b]|| <= tol * ||H_s||_inf).
 #include <algorithm>
 #include <cmath>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -317,19 +318,28 @@ bbl_status bbl_batch_set_schedule(bbl_batch* Bt, int lanes_per_row) {
     return BBL_OK;
 }
 
-bbl_status bbl_batch_solve(bbl_batch* Bt, int nev, int b, const bbl_options* opt, int use_graph, double* evals,
-                           double* resid, int* iters, int* status, bbl_stats* stats) {
-    using namespace bbl;
-    if (!Bt || !evals || b < 1 || b > kMaxB || nev < 1 || nev > kMaxB)
-        return set_error(BBL_ERR_INVALID_ARG, "batch_solve: bad arguments");
-    if (b != 1 && b != 2 && b != 4 && b != 8 && b != 16)
-        return set_error(BBL_ERR_UNSUPPORTED, "batch_solve: b must be 1, 2, 4, 8 or 16");
-    bbl_options o;
-    if (opt) o = *opt;
-    else bbl_options_default(&o);
+}  // extern "C"
+
+namespace bbl {
+namespace {
+
+struct BatchStageOut {
+    std::vector<int> fin, status;         // per segment: last block, status
+    std::vector<double> theta, resid;     // nseg x nev
+    float t_loop = 0.f;
+    int launches = 0;                     // kernels in one captured iteration
+};
+
+// One lock-step block Lanczos run over the segments flagged in init_active
+// (all when NULL).  dtype: block storage (the matrix's, or FP64 for the
+// polish with FP64 arithmetic on FP32 values, f64_spmm); pivot: device FP64
+// n x b, or NULL for the random pivot.  X: device FP64 n x nev, the Ritz
+// vectors of the segments that ran; out: their Ritz values, true FP64
+// residuals, last block and status.
+bbl_status batch_stage(bbl_batch* Bt, int nev, int b, const bbl_options& o, int use_graph, int dtype, bool f64_spmm,
+                       const double* pivot, const int* init_active, double* X_out, BatchStageOut& bout) {
     const int nseg = Bt->nseg;
     const int64_t n = Bt->n_tot;
-    const int dtype = Bt->A->storage;
     const size_t sz = dtype_size(dtype);
     int64_t nmin = Bt->off[1] - Bt->off[0];
     for (int s = 1; s < nseg; ++s) nmin = std::min(nmin, Bt->off[s + 1] - Bt->off[s]);
@@ -427,7 +437,7 @@ bbl_status bbl_batch_solve(bbl_batch* Bt, int nev, int b, const bbl_options* opt
         h[0] = 0;
         h[1] = b;
         h[2] = b;
-        for (int s = 0; s < nseg; ++s) h[8 + s] = 1;  // active
+        for (int s = 0; s < nseg; ++s) h[8 + s] = init_active ? (init_active[s] != 0) : 1;  // active
         for (int s = 0; s < nseg; ++s) h[8 + 2 * nseg + s] = BBL_ERR_NOT_CONVERGED;
         for (int s = 0; s < nseg; ++s) h[8 + (size_t)nseg * (7 + b) + s] = -1;  // jprev: no test yet
         BBL_CUDA(cudaMemcpyAsync(ints.p, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice, st));
@@ -439,9 +449,10 @@ bbl_status bbl_batch_solve(bbl_batch* Bt, int nev, int b, const bbl_options* opt
         }
         BBL_CUDA(cudaMemcpyAsync(thr.p, th.data(), sizeof(double) * th.size(), cudaMemcpyHostToDevice, st));
     }
-    // ---- pivot: random N(0,1) per row (splitmix64), orthonormalised per segment ----
+    // ---- pivot: given, or random N(0,1) per row (splitmix64); orthonormalised per segment ----
     BBL_TRY(piv.alloc(sizeof(double) * (size_t)n * b));
-    BBL_TRY(fill_normal(n, b, o.seed, 0, piv.as<double>(), st));
+    if (pivot) BBL_CUDA(cudaMemcpyAsync(piv.p, pivot, sizeof(double) * (size_t)n * b, cudaMemcpyDeviceToDevice, st));
+    else BBL_TRY(fill_normal(n, b, o.seed, 0, piv.as<double>(), st));
     char* bp = basis.as<char>();
     const unsigned cg = 152 * 8;
     if (dtype == BBL_FP64)
@@ -493,8 +504,23 @@ bbl_status bbl_batch_solve(bbl_batch* Bt, int nev, int b, const bbl_options* opt
     }
     // ---- one block iteration (all segments), reading j and m from device memory ----
     cudaGraphConditionalHandle handle = 0;
+    // a run over a subset of the problems (the polish) multiplies only their
+    // rows: maximal runs of consecutive flagged segments
+    std::vector<std::pair<int64_t, int64_t>> row_runs;
+    if (init_active && f64_spmm && Bt->A->has_csr) {
+        for (int s = 0; s < nseg; ++s) {
+            if (!init_active[s]) continue;
+            if (!row_runs.empty() && row_runs.back().second == Bt->off[s]) row_runs.back().second = Bt->off[s + 1];
+            else row_runs.push_back({Bt->off[s], Bt->off[s + 1]});
+        }
+    }
     auto iteration = [&]() -> bbl_status {
-        BBL_TRY(spmm_dispatch(Bt->A, b, Vfix.p, Wfix.p, false, st, Bt->spmm_lanes));
+        if (!row_runs.empty()) {
+            for (const auto& rr : row_runs)
+                BBL_TRY(spmm_rows_f64(Bt->A, b, Vfix.as<double>(), Wfix.as<double>(), rr.first, rr.second, st));
+        } else {
+            BBL_TRY(spmm_dispatch(Bt->A, b, Vfix.p, Wfix.p, f64_spmm, st, Bt->spmm_lanes));
+        }
         BBL_TRY(gram_seg(n, b, m_max, d_m, dtype, basis.p, Wfix.p, CH, nchunks, CP, nseg, active, partial.as<double>(),
                          C1.as<double>(), st));
         BBL_TRY(apply_seg(n, b, b, d_m, 0, dtype, basis.p, C1.as<double>(), (int64_t)m_max * b, Wfix.p, true, false, CT,
@@ -592,51 +618,120 @@ bbl_status bbl_batch_solve(bbl_batch* Bt, int nev, int b, const bbl_options* opt
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     // ---- results: per-segment Ritz vectors X_s = Q_s S_s and FP64 residuals ----
-    std::vector<int> hfin(nseg), hstat(nseg);
-    BBL_CUDA(cudaMemcpyAsync(hfin.data(), final_j, sizeof(int) * nseg, cudaMemcpyDeviceToHost, st));
-    BBL_CUDA(cudaMemcpyAsync(hstat.data(), seg_status, sizeof(int) * nseg, cudaMemcpyDeviceToHost, st));
+    bout.fin.assign(nseg, 0);
+    bout.status.assign(nseg, 0);
+    BBL_CUDA(cudaMemcpyAsync(bout.fin.data(), final_j, sizeof(int) * nseg, cudaMemcpyDeviceToHost, st));
+    BBL_CUDA(cudaMemcpyAsync(bout.status.data(), seg_status, sizeof(int) * nseg, cudaMemcpyDeviceToHost, st));
     BBL_CUDA(cudaStreamSynchronize(st));
-    std::vector<int> hms(nseg);
-    for (int s = 0; s < nseg; ++s) hms[s] = (hfin[s] + 1) * b;
-    std::vector<int> ones(nseg, 1);
+    std::vector<int> hms(nseg), ran(nseg, 1);
+    for (int s = 0; s < nseg; ++s) {
+        hms[s] = (bout.fin[s] + 1) * b;
+        if (init_active) ran[s] = init_active[s] != 0;
+    }
     BBL_CUDA(cudaMemcpyAsync(ms, hms.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice, st));
-    BBL_CUDA(cudaMemcpyAsync(active, ones.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice, st));
-    BBL_TRY(X.alloc(sizeof(double) * (size_t)n * nev));
+    BBL_CUDA(cudaMemcpyAsync(active, ran.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice, st));
+    BBL_CUDA(cudaMemsetAsync(X_out, 0, sizeof(double) * (size_t)n * nev, st));
     BBL_TRY(Y.alloc(sizeof(double) * (size_t)n * nev));
-    BBL_TRY(apply_seg(n, b, nev, ms, 1, dtype, basis.p, S.as<double>(), (int64_t)m_max * nev, X.p, false, true, CT, nctas,
-                      active, st));
-    BBL_TRY(spmm_dispatch(Bt->A, nev, X.p, Y.p, true, st, 0));
+    BBL_TRY(apply_seg(n, b, nev, ms, 1, dtype, basis.p, S.as<double>(), (int64_t)m_max * nev, X_out, false, true, CT,
+                      nctas, active, st));
+    BBL_TRY(spmm_dispatch(Bt->A, nev, X_out, Y.p, true, st, 0));
     BBL_TRY(rpart.alloc(sizeof(double) * (size_t)nctas * nev));
-    resid_seg_kernel<<<nctas, 256, 0, st>>>(nev, CT, Y.as<double>(), X.as<double>(), theta.as<double>(), nev,
+    resid_seg_kernel<<<nctas, 256, 0, st>>>(nev, CT, Y.as<double>(), X_out, theta.as<double>(), nev,
                                             rpart.as<double>());
     BBL_LAUNCH_CHECK();
-    std::vector<double> hp((size_t)nctas * nev), hth((size_t)nseg * nev);
+    std::vector<double> hp((size_t)nctas * nev);
+    bout.theta.assign((size_t)nseg * nev, 0.0);
     BBL_CUDA(cudaMemcpyAsync(hp.data(), rpart.p, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st));
-    BBL_CUDA(cudaMemcpyAsync(hth.data(), theta.p, sizeof(double) * hth.size(), cudaMemcpyDeviceToHost, st));
+    BBL_CUDA(cudaMemcpyAsync(bout.theta.data(), theta.p, sizeof(double) * bout.theta.size(), cudaMemcpyDeviceToHost, st));
     BBL_CUDA(cudaStreamSynchronize(st));
     std::vector<double> r2((size_t)nseg * nev, 0.0);
     for (int c = 0; c < nctas; ++c) {
-        const int s = (int)ctas[3 * (size_t)c];
-        for (int i = 0; i < nev; ++i) r2[(size_t)s * nev + i] += hp[(size_t)c * nev + i];
+        const int sg = (int)ctas[3 * (size_t)c];
+        for (int i = 0; i < nev; ++i) r2[(size_t)sg * nev + i] += hp[(size_t)c * nev + i];
     }
-    int nconv = 0, maxit = 0;
-    for (int s = 0; s < nseg; ++s) {
-        for (int i = 0; i < nev; ++i) {
-            evals[(size_t)s * nev + i] = hth[(size_t)s * nev + i];
-            if (resid) resid[(size_t)s * nev + i] = std::sqrt(r2[(size_t)s * nev + i]);
+    bout.resid.assign((size_t)nseg * nev, 0.0);
+    for (size_t e = 0; e < r2.size(); ++e) bout.resid[e] = std::sqrt(r2[e]);
+    bout.t_loop = t_loop;
+    bout.launches = launches_in_graph;
+    return BBL_OK;
+}
+
+}  // namespace
+}  // namespace bbl
+
+extern "C" {
+
+bbl_status bbl_batch_solve(bbl_batch* Bt, int nev, int b, const bbl_options* opt, int use_graph, double* evals,
+                           double* resid, int* iters, int* status, bbl_stats* stats) {
+    using namespace bbl;
+    if (!Bt || !evals || b < 1 || b > kMaxB || nev < 1 || nev > kMaxB)
+        return set_error(BBL_ERR_INVALID_ARG, "batch_solve: bad arguments");
+    if (b != 1 && b != 2 && b != 4 && b != 8 && b != 16)
+        return set_error(BBL_ERR_UNSUPPORTED, "batch_solve: b must be 1, 2, 4, 8 or 16");
+    bbl_options o;
+    if (opt) o = *opt;
+    else bbl_options_default(&o);
+    const int nseg = Bt->nseg;
+    const int64_t n = Bt->n_tot;
+    const int storage = Bt->A->storage;
+    DevBuf X;
+    BBL_TRY(X.alloc(sizeof(double) * (size_t)n * nev));
+    BatchStageOut s1, s2;
+    BBL_TRY(batch_stage(Bt, nev, b, o, use_graph, storage, false, nullptr, nullptr, X.as<double>(), s1));
+    std::vector<int> polished(nseg, 0), piters(nseg, 0);
+    const bool pow2 = nev == 1 || nev == 2 || nev == 4 || nev == 8 || nev == 16;
+    if (storage == BBL_FP32 && o.polish && pow2) {
+        // polish: the segments whose FP64 residuals miss tol go on from their
+        // FP32 Ritz vectors (block size nev) with FP64 blocks and FP64
+        // arithmetic on the FP32 values, in one more lock-step run
+        int need = 0;
+        for (int s = 0; s < nseg; ++s) {
+            for (int i = 0; i < nev; ++i)
+                if (!(s1.resid[(size_t)s * nev + i] <= o.tol * Bt->norm[s])) polished[s] = 1;
+            need += polished[s];
         }
-        if (iters) iters[s] = hfin[s] + 1;
-        if (status) status[s] = hstat[s];
-        nconv += hstat[s] == BBL_OK;
-        maxit = std::max(maxit, hfin[s] + 1);
+        if (need > 0) {
+            DevBuf X2;
+            BBL_TRY(X2.alloc(sizeof(double) * (size_t)n * nev));
+            bbl_options o2 = o;
+            o2.check_every = 0;
+            BBL_TRY(batch_stage(Bt, nev, nev, o2, use_graph, BBL_FP64, true, X.as<double>(), polished.data(),
+                                X2.as<double>(), s2));
+            for (int s = 0; s < nseg; ++s) {
+                if (!polished[s]) continue;
+                for (int i = 0; i < nev; ++i) {
+                    s1.theta[(size_t)s * nev + i] = s2.theta[(size_t)s * nev + i];
+                    s1.resid[(size_t)s * nev + i] = s2.resid[(size_t)s * nev + i];
+                }
+                s1.status[s] = s2.status[s];
+                piters[s] = s2.fin[s] + 1;
+            }
+        }
+    }
+    int nconv = 0, maxit = 0, maxp = 0;
+    for (int s = 0; s < nseg; ++s) {
+        bool ok = s1.status[s] == BBL_OK;
+        for (int i = 0; i < nev; ++i) {
+            evals[(size_t)s * nev + i] = s1.theta[(size_t)s * nev + i];
+            if (resid) resid[(size_t)s * nev + i] = s1.resid[(size_t)s * nev + i];
+            // a segment counts as converged when its true FP64 residuals meet tol
+            ok = ok && s1.resid[(size_t)s * nev + i] <= o.tol * Bt->norm[s] * (1.0 + 1e-6);
+        }
+        if (!ok && s1.status[s] == BBL_OK) s1.status[s] = BBL_ERR_NOT_CONVERGED;
+        if (iters) iters[s] = s1.fin[s] + 1 + piters[s];
+        if (status) status[s] = s1.status[s];
+        nconv += s1.status[s] == BBL_OK;
+        maxit = std::max(maxit, s1.fin[s] + 1);
+        maxp = std::max(maxp, piters[s]);
     }
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
         stats->iters = maxit;
         stats->vec_equiv_iters = maxit * b;
+        stats->polish_iters = maxp;
         stats->converged = nconv;
-        stats->t_total_ms = t_loop;
-        stats->polish_iters = launches_in_graph;
+        stats->t_total_ms = s1.t_loop + s2.t_loop;
+        stats->graph_kernels = s1.launches;
     }
     return nconv == nseg ? BBL_OK : BBL_ERR_NOT_CONVERGED;
 }

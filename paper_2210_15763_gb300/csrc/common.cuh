@@ -198,6 +198,9 @@ bbl_status spmm_dispatch(const bbl_matrix* A, int b, const void* V, void* W, boo
                          int rows_per_warp_hint = 0);
 // W = H V with float-float blocks V, W (n x b pairs) and FP32 matrix values
 bbl_status spmm_df32(const bbl_matrix* A, int b, const void* V, void* W, cudaStream_t st);
+// rows [r0, r1) of W = H V in FP64 arithmetic from the CSR copy (other rows of W untouched)
+bbl_status spmm_rows_f64(const bbl_matrix* A, int b, const double* V, double* W, int64_t r0, int64_t r1,
+                         cudaStream_t st);
 // Algorithmic bytes of one SpMM with b columns: the stored matrix (values of
 // sv bytes, int32 columns, int64 row pointers) read once, V read once and W
 // written once (sx bytes per block element); a factored matrix stores no

@@ -279,27 +279,34 @@ __global__ void __launch_bounds__(256) spmm_sell_generic(int64_t nslices, int b,
     }
 }
 
+// rows [r0, r0 + nr) of the CSR matrix (the whole matrix: r0 = 0, nr = n)
+struct CsrRows {
+    int64_t nr;
+    const int64_t* rp;  // row pointers from row r0
+    const int* ci;
+    int64_t r0;
+};
+
 template <typename TM, typename TX, int B, int G>
-void launch_csr(const bbl_matrix* A, const TM* val, const TX* V, TX* W, cudaStream_t st) {
-    const int64_t threads = A->n * G;
+void launch_csr(const CsrRows& R, const TM* val, const TX* V, TX* W, cudaStream_t st) {
+    const int64_t threads = R.nr * G;
     const int64_t blocks = ceil_div(threads, 256);
-    spmm_csr_kernel<TM, TX, B, G><<<(unsigned)blocks, 256, 0, st>>>(A->n, A->row_ptr.as<int64_t>(), A->col.as<int>(),
-                                                                    val, V, W);
+    spmm_csr_kernel<TM, TX, B, G><<<(unsigned)blocks, 256, 0, st>>>(R.nr, R.rp, R.ci, val, V, W + R.r0 * B);
 }
 
 template <typename TM, typename TX, int B>
-void launch_csr_g(const bbl_matrix* A, const TM* val, const TX* V, TX* W, int G, cudaStream_t st) {
+void launch_csr_g(const CsrRows& R, const TM* val, const TX* V, TX* W, int G, cudaStream_t st) {
     constexpr int LPN = VecLayout<TX, B>::LPN;
     if (G < LPN) G = LPN;
     switch (G) {
-        case 1: if constexpr (LPN <= 1) { launch_csr<TM, TX, B, 1>(A, val, V, W, st); return; } break;
-        case 2: if constexpr (LPN <= 2) { launch_csr<TM, TX, B, 2>(A, val, V, W, st); return; } break;
-        case 4: if constexpr (LPN <= 4) { launch_csr<TM, TX, B, 4>(A, val, V, W, st); return; } break;
-        case 8: if constexpr (LPN <= 8) { launch_csr<TM, TX, B, 8>(A, val, V, W, st); return; } break;
-        case 16: launch_csr<TM, TX, B, 16>(A, val, V, W, st); return;
+        case 1: if constexpr (LPN <= 1) { launch_csr<TM, TX, B, 1>(R, val, V, W, st); return; } break;
+        case 2: if constexpr (LPN <= 2) { launch_csr<TM, TX, B, 2>(R, val, V, W, st); return; } break;
+        case 4: if constexpr (LPN <= 4) { launch_csr<TM, TX, B, 4>(R, val, V, W, st); return; } break;
+        case 8: if constexpr (LPN <= 8) { launch_csr<TM, TX, B, 8>(R, val, V, W, st); return; } break;
+        case 16: launch_csr<TM, TX, B, 16>(R, val, V, W, st); return;
         default: break;
     }
-    launch_csr<TM, TX, B, 32>(A, val, V, W, st);
+    launch_csr<TM, TX, B, 32>(R, val, V, W, st);
 }
 
 // Lanes per row: about the average row length / 2, clamped to [LPN, 32].
@@ -314,10 +321,12 @@ int default_group(const bbl_matrix* A) {
 
 template <typename TM, typename TX>
 bbl_status spmm_typed(const bbl_matrix* A, int b, const TM* csr_val, const TM* sell_val, const TX* V, TX* W,
-                      cudaStream_t st, int G) {
+                      cudaStream_t st, int G, int64_t r0 = 0, int64_t r1 = -1) {
     if (G <= 0) G = A->spmm_lanes > 0 ? A->spmm_lanes : default_group(A);
     const bool pow2 = (b == 1 || b == 2 || b == 4 || b == 8 || b == 16);
-    if (A->fmt == BBL_SELL && sell_val) {
+    const bool ranged = r1 >= 0;  // rows [r0, r1) only, from the CSR copy
+    if (r1 < 0) r1 = A->n;
+    if (A->fmt == BBL_SELL && sell_val && !ranged) {
         const int64_t blocks = ceil_div(A->nslices * 32, 256);
         auto sp = A->slice_ptr.as<int64_t>();
         auto sc = A->sell_col.as<int>();
@@ -337,16 +346,17 @@ bbl_status spmm_typed(const bbl_matrix* A, int b, const TM* csr_val, const TM* s
         return BBL_OK;
     }
     if (!A->has_csr || !csr_val) return set_error(BBL_ERR_UNSUPPORTED, "spmm: matrix holds no CSR values of this type");
+    const CsrRows R{r1 - r0, A->row_ptr.as<int64_t>() + r0, A->col.as<int>(), r0};
+    if (R.nr <= 0) return BBL_OK;
     switch (pow2 ? b : 0) {
-        case 1: launch_csr_g<TM, TX, 1>(A, csr_val, V, W, G, st); break;
-        case 2: launch_csr_g<TM, TX, 2>(A, csr_val, V, W, G, st); break;
-        case 4: launch_csr_g<TM, TX, 4>(A, csr_val, V, W, G, st); break;
-        case 8: launch_csr_g<TM, TX, 8>(A, csr_val, V, W, G, st); break;
-        case 16: launch_csr_g<TM, TX, 16>(A, csr_val, V, W, G, st); break;
+        case 1: launch_csr_g<TM, TX, 1>(R, csr_val, V, W, G, st); break;
+        case 2: launch_csr_g<TM, TX, 2>(R, csr_val, V, W, G, st); break;
+        case 4: launch_csr_g<TM, TX, 4>(R, csr_val, V, W, G, st); break;
+        case 8: launch_csr_g<TM, TX, 8>(R, csr_val, V, W, G, st); break;
+        case 16: launch_csr_g<TM, TX, 16>(R, csr_val, V, W, G, st); break;
         default: {
-            const int64_t blocks = ceil_div(A->n * 32, 256);
-            spmm_csr_generic<TM, TX><<<(unsigned)blocks, 256, 0, st>>>(A->n, b, A->row_ptr.as<int64_t>(),
-                                                                      A->col.as<int>(), csr_val, V, W);
+            const int64_t blocks = ceil_div(R.nr * 32, 256);
+            spmm_csr_generic<TM, TX><<<(unsigned)blocks, 256, 0, st>>>(R.nr, b, R.rp, R.ci, csr_val, V, W + r0 * b);
         }
     }
     BBL_LAUNCH_CHECK();
@@ -377,6 +387,16 @@ bbl_status spmm_dispatch(const bbl_matrix* A, int b, const void* V, void* W, boo
     return spmm_typed<float, double>(A, b, A->has_csr ? A->val.as<float>() : nullptr,
                                      A->fmt == BBL_SELL ? A->sell_val.as<float>() : nullptr,
                                      static_cast<const double*>(V), static_cast<double*>(W), st, G);
+}
+
+bbl_status spmm_rows_f64(const bbl_matrix* A, int b, const double* V, double* W, int64_t r0, int64_t r1,
+                         cudaStream_t st) {
+    if (A->fmt == BBL_KRON || !A->has_csr)
+        return set_error(BBL_ERR_UNSUPPORTED, "spmm: a row range needs the CSR copy of the matrix");
+    if (r0 < 0 || r1 > A->n || r0 > r1) return set_error(BBL_ERR_INVALID_ARG, "spmm: bad row range");
+    if (A->storage == BBL_FP64)
+        return spmm_typed<double, double>(A, b, A->val.as<double>(), nullptr, V, W, st, 0, r0, r1);
+    return spmm_typed<float, double>(A, b, A->val.as<float>(), nullptr, V, W, st, 0, r0, r1);
 }
 
 bbl_status spmm_df32(const bbl_matrix* A, int b, const void* V, void* W, cudaStream_t st) {

@@ -97,6 +97,28 @@ def test_batched_segment_equals_single_solve_with_the_same_pivot():
         assert abs(int(it[s]) - r.stats["iters"]) <= 1
 
 
+def test_batched_fp32_polish_reaches_the_fp64_tolerance():
+    """FP32 blocks alone stop at their floor, far above 1e-10; with the
+    polish (default) the problems that miss the tolerance go on from their
+    FP32 Ritz vectors with FP64 blocks, and every problem then matches the
+    dense eigenvalues to 1e-10 with true FP64 residuals <= tol * ||H_s||."""
+    torch, bbl = need_gpu()
+    mats = _family(count=6, seed=9)
+    B = bbl.Batch(mats, storage="fp32")
+    tol = 1e-10
+    e0, r0, i0, s0, _ = B.solve(4, 4, tol=tol, max_vectors=400, seed=3, polish=0)
+    assert np.any(s0 != 0)
+    ev, rs, it, st, stats = B.solve(4, 4, tol=tol, max_vectors=400, seed=3)
+    assert np.all(st == 0), st
+    assert stats["polish_iters"] >= 1
+    nrm = np.array([np.abs(A.to_dense()).sum(axis=1).max() for A in mats])
+    for s, A in enumerate(mats):
+        want = np.linalg.eigvalsh(A.to_dense())[:4]
+        np.testing.assert_allclose(ev[s], want, rtol=1e-10, atol=1e-10 * np.abs(want).max())
+        assert np.all(rs[s] <= tol * nrm[s] * (1 + 1e-6))
+    assert np.all(it >= i0)
+
+
 def test_batched_rejects_coupled_segments():
     torch, bbl = need_gpu()
     a = synth.random_sparse_symmetric(40, 4, seed=1)
