@@ -158,12 +158,43 @@ def build_matrix():
 
 
 # ---------------------------------------------------------------------------- reference arm: the oracle
-def oracle_sample(A, iters_gpu: int, budget_blocks: int = 3):
-    """Times the CPU oracle's own steps once each at full size and composes
-    the cost of a block Lanczos run of `iters_gpu` blocks: per block one SpMM
-    (Eq. 3), two classical Gram-Schmidt passes against (j+1)*b columns (cost
-    linear in the columns, timed at two basis sizes), the CholQR2 normaliser
-    and the dense eigensolve of T (cost cubic in its order, timed once)."""
+def oracle_measured(scale: float = 0.2):
+    """The oracle's whole block Lanczos run (random pivot, b = 8, nev = 8,
+    residual 1e-8) on the same family at a reduced size, timed end to end,
+    beside the composition of oracle_sample at that size and block count:
+    the check of the composition used at full size."""
+    import synth
+    from oracle import lanczos as OL
+    from oracle import rng as OR
+    A = synth.kron_matrix(WORKLOAD, scale=scale)
+    H = A.to_scipy()
+    piv = OR.normal_block(PIVOT_SEED, A.n, B)
+    t0 = time.perf_counter()
+    r = OL.block_lanczos(H, NEV, B, piv, tol=TOL, max_vectors=2000)
+    measured = time.perf_counter() - t0
+    composed, _, _ = oracle_sample(A, r.iters)
+    return {"n": A.n, "nnz": A.nnz, "blocks": r.iters, "converged": bool(r.converged), "measured_s": measured,
+            "composed_s": composed, "measured_over_composed": measured / composed}
+
+
+def oracle_blocks_full_size(default: int = 110) -> int:
+    """The oracle's own block count on the full workload (random pivot), as
+    stored beside its eigenvalues."""
+    try:
+        with open(ORACLE_EVALS) as f:
+            return int(json.load(f)["blocks"])
+    except (OSError, KeyError, ValueError):
+        return default
+
+
+def oracle_sample(A, iters_gpu: int, budget_blocks: int = 3, k1: int = 8, k2: int = 32):
+    """Times the CPU oracle's own steps and composes the cost of a block
+    Lanczos run of `iters_gpu` blocks.  Per block: one SpMM (Eq. 3); the
+    stacking of the basis and the two classical Gram-Schmidt passes against
+    (j+1)*b columns (cost linear in the columns, timed together at two basis
+    sizes); the CholQR2 normaliser; the assembly of T (Eq. 12, quadratic in
+    its order) and its dense eigensolve (cubic), timed at one order and
+    scaled."""
     from oracle import lanczos as OL
     from oracle import rng as OR
     from oracle.spmm import spmm as ospmm
@@ -177,14 +208,24 @@ def oracle_sample(A, iters_gpu: int, budget_blocks: int = 3):
         return time.perf_counter() - t0
 
     t_spmm = tm(lambda: ospmm(H, V))
-    m1, m2 = 4 * B, 16 * B
-    Q = OR.normal_block(7, A.n, m2) / np.sqrt(A.n)
-    t1 = tm(lambda: OL.cgs_pass(V, Q[:, :m1]))
-    t2 = tm(lambda: OL.cgs_pass(V, Q))
-    c_col = max((t2 - t1) / (m2 - m1), 0.0)
-    a_pass = max(t1 - c_col * m1, 0.0)
+    Q = OR.normal_block(7, A.n, k2 * B) / np.sqrt(A.n)
+    blocks = [Q[:, i * B:(i + 1) * B] for i in range(k2)]
+
+    def gs(k):
+        basis = np.hstack(blocks[:k])
+        return OL.cgs_pass(OL.cgs_pass(V, basis), basis)
+
+    t1 = tm(lambda: gs(k1))
+    t2 = tm(lambda: gs(k2))
+    del Q, blocks
+    c_col = max((t2 - t1) / ((k2 - k1) * B), 0.0)
+    a_gs = max(t1 - c_col * k1 * B, 0.0)
     t_norm = tm(lambda: OL.cholqr2(V, 0.0))
-    me = 256
+    ke = 32
+    As = [np.eye(B) for _ in range(ke)]
+    Bs = [np.eye(B) for _ in range(ke - 1)]
+    me = ke * B
+    t_asm = tm(lambda: OL.block_tridiagonal(As, Bs))
     Te = np.random.default_rng(0).standard_normal((me, me))
     Te = Te + Te.T
     t_eig = tm(lambda: np.linalg.eigh(Te))
@@ -192,7 +233,7 @@ def oracle_sample(A, iters_gpu: int, budget_blocks: int = 3):
     est = 0.0
     for j in range(J):
         m = (j + 1) * B
-        est += t_spmm + 2.0 * (a_pass + c_col * m) + t_norm + t_eig * (m / me) ** 3
+        est += t_spmm + a_gs + c_col * m + t_norm + t_asm * (m / me) ** 2 + t_eig * (m / me) ** 3
     return float(est), float(time.perf_counter() - t_start), 1
 
 
@@ -207,14 +248,17 @@ def run_reference(args):
     if rank != 0:
         return
     A, tgen = build_matrix()
-    iters = int(os.environ.get("BBL_REF_ITERS", "110"))
+    # the oracle's own block count on this workload (random pivot, residual 1e-8)
+    iters = oracle_blocks_full_size()
     vals = []
     wall = 0.0
     for _ in range(args.warmup + args.steps if args.steps > 0 else 1):
-        est, w, blocks = oracle_sample(A, iters, budget_blocks=2)
+        # a lighter sample per step (basis sizes 4 and 12 blocks for the linear fit)
+        est, w, blocks = oracle_sample(A, iters, budget_blocks=2, k1=4, k2=12)
         vals.append(est)
         wall += w
     v = float(np.mean(vals[args.warmup:])) if len(vals) > args.warmup else float(np.mean(vals))
+    check = oracle_measured()
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
@@ -223,7 +267,11 @@ def run_reference(args):
                    "parallelism": "host cores"},
         "cpu_baseline": {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"the oracle's steps timed once each at full size (SpMM, Gram-Schmidt passes "
-                                   f"at two basis sizes, CholQR2, dense eigensolve) and composed into a {iters}-block run"},
+                                   f"at two basis sizes, CholQR2, dense eigensolve) and composed into a {iters}-block "
+                                   f"run (the oracle's own block count on this workload); the composition checked by a "
+                                   f"whole oracle run at n = {check['n']}: measured {check['measured_s']:.1f} s vs "
+                                   f"composed {check['composed_s']:.1f} s",
+                         "composition_check": check},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -400,12 +448,17 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.skip_cpu:
-        est, wall, blocks = oracle_sample(A, int(r.stats["iters"]), budget_blocks=2)
+        iters_o = oracle_blocks_full_size()
+        est, wall, blocks = oracle_sample(A, iters_o, budget_blocks=2)
+        check = oracle_measured()
         cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"the FP64 oracle's steps timed once each at full size ({wall:.1f} s wall: one SpMM, "
                          f"Gram-Schmidt passes at two basis sizes, CholQR2, a dense eigensolve) and composed into a "
-                         f"{r.stats['iters']}-block run, the GPU run's block count; numpy BLAS on all cores, scipy "
-                         "SpMM single-threaded"}
+                         f"{iters_o}-block run, the oracle's own block count on this workload (random pivot); the "
+                         f"composition checked by a whole oracle run at n = {check['n']} ({check['blocks']} blocks): "
+                         f"measured {check['measured_s']:.1f} s vs composed {check['composed_s']:.1f} s; numpy BLAS "
+                         "on all cores, scipy SpMM single-threaded",
+               "composition_check": check}
 
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
