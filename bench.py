@@ -642,7 +642,7 @@ def run_learned(args):
     make = lambda g: synth.family_matrix(h0, v, g, fp32_values=True)
     t0 = time.time()
     lp = learned.fit(make, gs[:48], nev=nev, b=b, trunc_dim=trunc, n_basis_g=8, hidden=128, epochs=args.epochs,
-                     lr=1e-3, seed=0, tol=TOL, storage="fp32", fmt="csr")
+                     lr=1e-3, seed=0, tol=TOL, storage="fp32", fmt="csr", sub_tol=args.sub_tol)
     t_fit = time.time() - t0
     rows = []
     for g in gs[48:]:
@@ -651,13 +651,13 @@ def run_learned(args):
         ee = torch.cuda.Event(enable_timing=True)
         out = {"g": float(g)}
         ev.record()
-        r_l, info = learned.solve_with_learned_pivot(A, lp, g, b, trunc, tol=TOL)
+        r_l, info = learned.solve_with_learned_pivot(A, lp, g, b, trunc, tol=TOL, sub_tol=args.sub_tol)
         ee.record()
         torch.cuda.synchronize()
         out.update(learned_iters=r_l.stats["iters"] + r_l.stats["polish_iters"], learned_s=ev.elapsed_time(ee) / 1e3,
                    **info)
         ev.record()
-        P = bbl.pivot_bootstrap(A, trunc, b, sub_tol=1e-10)
+        P = bbl.pivot_bootstrap(A, trunc, b, sub_tol=args.sub_tol)
         r_b = bbl.solve(A, nev, b, pivot=P, tol=TOL)
         ee.record()
         torch.cuda.synchronize()
@@ -669,14 +669,23 @@ def run_learned(args):
         out.update(random_iters=r_r.stats["iters"] + r_r.stats["polish_iters"], random_s=ev.elapsed_time(ee) / 1e3,
                    max_eval_diff=float(np.max(np.abs(r_l.evals - r_r.evals))),
                    converged=bool(r_l.converged and r_b.converged and r_r.converged))
-        rows.append(out)
         A.close()
+        # the in-box baseline the forms must beat: plain FP64, random pivot
+        A64 = bbl.Matrix(make(g), storage="fp64", fmt="csr")
+        ev.record()
+        r_p = bbl.solve(A64, nev, b, pivot=None, seed=7, tol=TOL, evecs=None)
+        ee.record()
+        torch.cuda.synchronize()
+        out.update(plain_fp64_iters=r_p.stats["iters"], plain_fp64_s=ev.elapsed_time(ee) / 1e3)
+        A64.close()
+        rows.append(out)
     mean = lambda k: float(np.mean([r[k] for r in rows]))
     res = {"mode": "learned", "n": int(h0.n), "held_out": len(rows), "fit_s": t_fit,
            "train_loss_first_last": [float(lp.loss[0]), float(lp.loss[-1])], "epochs": args.epochs,
            "mean_iters": {"learned": mean("learned_iters"), "bootstrap": mean("boot_iters"),
                           "random": mean("random_iters")},
-           "mean_time_s": {"learned": mean("learned_s"), "bootstrap": mean("boot_s"), "random": mean("random_s")},
+           "mean_time_s": {"learned": mean("learned_s"), "bootstrap": mean("boot_s"), "random": mean("random_s"),
+                           "plain_fp64_random": mean("plain_fp64_s")},
            "learned_used_fraction": mean("learned_used"), "bootstrap_built_fraction": mean("bootstrap_built"),
            "all_converged": all(r["converged"] for r in rows),
            "max_eval_diff_learned_vs_random": max(r["max_eval_diff"] for r in rows), "per_g": rows}

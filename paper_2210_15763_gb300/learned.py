@@ -51,14 +51,15 @@ class LearnedPivot:
 
 def fit(make_matrix, g_train, nev: int, b: int, trunc_dim: int, n_basis_g: int = 8, hidden: int = 128,
         epochs: int = 3000, lr: float = 1e-3, seed: int = 0, tol: float = 1e-8, storage: str = "fp32",
-        fmt: str = "sell") -> LearnedPivot:
-    """make_matrix(g) -> host CSR; solves H(g) for every training g."""
+        fmt: str = "sell", sub_tol: float = 1e-4) -> LearnedPivot:
+    """make_matrix(g) -> host CSR; solves H(g) for every training g from the
+    bootstrapped pivot (truncated-space sub-solve to sub_tol)."""
     import torch
     g_train = np.asarray(g_train, dtype=np.float64)
     X, iters, rr_boot = [], [], []
     for g in g_train:
         M = Matrix(make_matrix(g), storage=storage, fmt=fmt, sell_sigma=256 if fmt == "sell" else 0)
-        P = pivot_bootstrap(M, trunc_dim, b, sub_tol=1e-10, seed=seed)
+        P = pivot_bootstrap(M, trunc_dim, b, sub_tol=sub_tol, seed=seed)
         _, rb = pivot_rr_residual(M, P)
         rr_boot.append(float(np.max(rb[:min(nev, rb.size)])))
         r = solve(M, nev, b, pivot=P, tol=tol)
@@ -88,37 +89,35 @@ def fit(make_matrix, g_train, nev: int, b: int, trunc_dim: int, n_basis_g: int =
     return LearnedPivot(net, U, nev, g_train, loss, iters, float(np.min(rr_boot)))
 
 
-def choose_pivot(A: Matrix, P_learned, P_boot, nev: int):
-    """Lanczos decides: keep the learned pivot only if the Rayleigh-Ritz residual
-    of its span (max over the nev lowest pairs) is not worse than the bootstrap's."""
-    _, rl = pivot_rr_residual(A, P_learned)
-    _, rb = pivot_rr_residual(A, P_boot)
-    k = min(nev, rl.size)
-    use_learned = bool(np.max(rl[:k]) <= np.max(rb[:k]))
-    return (P_learned if use_learned else P_boot), use_learned, float(np.max(rl[:k])), float(np.max(rb[:k]))
+def rr_max(A: Matrix, P, nev: int) -> float:
+    """Largest Rayleigh-Ritz residual of the nev lowest pairs of span(P) (one SpMM)."""
+    _, r = pivot_rr_residual(A, P)
+    return float(np.max(r[:min(nev, r.size)]))
 
 
 def solve_with_learned_pivot(A: Matrix, lp: LearnedPivot, g: float, b: int, trunc_dim: int, tol: float = 1e-8,
-                             seed: int = 0):
-    """Lanczos decides on the learned pivot.  When its Rayleigh-Ritz residual is
-    below every bootstrapped pivot's seen in training, it is used at once;
-    otherwise the bootstrapped pivot is built and the better of the two is
-    taken.  A solve from the learned pivot that does not converge is redone
-    from the bootstrapped pivot."""
+                             seed: int = 0, sub_tol: float = 1e-4):
+    """Lanczos decides on the learned pivot (one Rayleigh-Ritz SpMM).  When
+    its residual is below every bootstrapped pivot's seen in training, it is
+    used at once; otherwise the bootstrapped pivot is built (sub-solve to
+    sub_tol) and the one with the smaller residual taken (one more SpMM).  A
+    solve from the learned pivot that does not converge is redone from the
+    bootstrapped pivot."""
     P_l = lp.pivot(g)
-    _, rl_all = pivot_rr_residual(A, P_l)
-    rl = float(np.max(rl_all[:min(lp.nev, rl_all.size)]))
-    P_b = None
+    rl = rr_max(A, P_l, lp.nev)
+    P_b, rb = None, None
     if rl < lp.rr_boot_train:
-        P, used, rb = P_l, True, None
+        P, used = P_l, True
     else:
-        P_b = pivot_bootstrap(A, trunc_dim, b, sub_tol=1e-10, seed=seed)
-        P, used, rl, rb = choose_pivot(A, P_l, P_b, lp.nev)
+        P_b = pivot_bootstrap(A, trunc_dim, b, sub_tol=sub_tol, seed=seed)
+        rb = rr_max(A, P_b, lp.nev)
+        used = rl <= rb
+        P = P_l if used else P_b
     r = solve(A, lp.nev, b, pivot=P, tol=tol)
     fallback = False
     if not r.converged and used:
         if P_b is None:
-            P_b = pivot_bootstrap(A, trunc_dim, b, sub_tol=1e-10, seed=seed)
+            P_b = pivot_bootstrap(A, trunc_dim, b, sub_tol=sub_tol, seed=seed)
         r = solve(A, lp.nev, b, pivot=P_b, tol=tol)
         fallback = True
     return r, {"learned_used": used, "rr_learned": rl, "rr_boot": rb, "fallback": fallback,

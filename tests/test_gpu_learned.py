@@ -92,8 +92,10 @@ def test_mlp_graph_training_reduces_the_loss():
     assert hist[-1] < 0.05 * hist[0]
 
 
-def test_learned_pivot_beats_random_on_held_out_parameters():
-    """Train on 24 solves of H(g) = H0 + g V (n = 40 x 40), evaluate 6 held-out g."""
+def test_learned_pivot_beats_random_and_bootstrap_on_held_out_parameters():
+    """Train on 24 solves of H(g) = H0 + g V (n = 40 x 40), evaluate 6 held-out
+    g: fewer blocks than from a random pivot and than from the bootstrapped
+    pivot the method would use without the network."""
     torch, bbl = need_gpu()
     from paper_2210_15763_gb300 import learned
     h0, v = synth.learned_family(scale=0.04)        # nP = nN = 40 -> n = 1600
@@ -102,13 +104,16 @@ def test_learned_pivot_beats_random_on_held_out_parameters():
     lp = learned.fit(make, gs[:24], nev=4, b=4, trunc_dim=200, n_basis_g=4, hidden=64, epochs=1500, lr=2e-3,
                      storage="fp64", fmt="csr")
     assert lp.loss[-1] < 0.2 * lp.loss[0]
-    it_l, it_r = [], []
+    it_l, it_r, it_b = [], [], []
     for g in gs[24:]:
         A = bbl.Matrix(make(g))
         r_l, info = learned.solve_with_learned_pivot(A, lp, g, 4, 200)
         r_r = bbl.solve(A, 4, 4, pivot=None, seed=1, tol=1e-8)
+        r_b = bbl.solve(A, 4, 4, pivot=bbl.pivot_bootstrap(A, 200, 4, sub_tol=1e-4), tol=1e-8)
         ref = np.linalg.eigvalsh(make(g).to_dense())[:4]
         np.testing.assert_allclose(r_l.evals, ref, rtol=1e-10)
         it_l.append(r_l.stats["iters"])
         it_r.append(r_r.stats["iters"])
+        it_b.append(r_b.stats["iters"])
     assert np.mean(it_l) < np.mean(it_r), (it_l, it_r)
+    assert np.mean(it_l) < np.mean(it_b), (it_l, it_b)
