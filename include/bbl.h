@@ -269,7 +269,11 @@ bbl_status bbl_block_gram(int64_t n, int b, int nblocks, bbl_dtype dtype, const 
  *   basis16 device FP16, nblocks consecutive n x 8 row-major blocks
  *   W       device FP32 n x 8 (not modified)
  *   C       device FP64 (nblocks*8) x 8 row-major
- * Products and sums over a chunk of rows in FP32, chunks summed in FP64.
+ * On the tensor cores (mma.sync m16n8k16, FP16 in, FP32 accumulate): per
+ * chunk of 1024 rows W is scaled by the power of two that puts its largest
+ * |W| in [2^13, 2^14) and rounded to FP16; the chunk's sums stay in FP32,
+ * chunks are unscaled exactly and summed in FP64.  Error against Q16^T W:
+ * below 2^-10 of |Q16|^T |W| entrywise.
  * Both pointers 16-byte aligned (BBL_ERR_INVALID_ARG otherwise).         */
 bbl_status bbl_block_gram_f16(int64_t n, int nblocks, const void* basis16, const float* W, double* C, void* stream);
 

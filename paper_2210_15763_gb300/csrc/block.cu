@@ -790,37 +790,65 @@ bbl_status launch_gram_rows(int64_t n, int m, const T* Q, const T* W, double* C,
     return BBL_OK;
 }
 
-// First-pass Gram from an FP16 copy of an FP32 basis (b = 8): C ~= Q16^T W.
-// The first Gram-Schmidt pass only has to take out the bulk of W's component
-// in span(Q) -- the FP32 second pass removes what is left, and A_j sums both
-// passes' coefficients -- so its coefficients may carry the FP16 rounding of
-// Q (relative 2^-11), and the pass reads 2 instead of 4 bytes per basis
-// element.  Persistent CTAs take chunks of kHalfRows rows from a ticket
-// counter and stage W's rows of the chunk in shared memory; a warp takes
-// basis blocks round-robin and walks the chunk's rows, lane l the rows l,
-// l + 32, ... (a warp's loads of one row position are 512 contiguous bytes),
-// kHalfUnroll rows of loads in flight per lane, 64 FP32 sums per lane;
-// a halving butterfly over the 32 lanes leaves two sums per lane, added to
-// the CTA's FP64 slot (m x 8).
+// First-pass Gram from an FP16 copy of an FP32 basis (b = 8): C ~= Q16^T W,
+// on the tensor cores.  The first Gram-Schmidt pass only has to take out
+// the bulk of W's component in span(Q) -- the FP32 second pass removes what
+// is left, and A_j sums both passes' coefficients -- so its coefficients may
+// carry FP16 roundings (relative 2^-11) of Q and of W, and the pass reads 2
+// instead of 4 bytes per basis element.
+//
+// Persistent CTAs take chunks of kHalfRows rows from a ticket counter.  W's
+// rows of the chunk are scaled by an exact power of two (the chunk's largest
+// |W| lands in [2^13, 2^14)) and rounded to FP16 into shared memory.  Warp w
+// owns the pairs of basis blocks p = w, w + 8, ...: per 16 rows a pair is a
+// 16 x 16 FP16 tile A (16 basis columns x 16 rows), brought into a per-warp
+// shared-memory ring by cp.async (one 16-byte row per lane, kHmSK tiles per
+// stage, kHmNS stages) and loaded transposed with ldmatrix; W's 16 x 8 tile
+// is the B operand; one mma.sync.m16n8k16 (FP16 in, FP32 accumulate) adds
+// the pair's 16 x 8 block of C.  Over a chunk the sums stay in FP32; at the
+// chunk's end they are unscaled (exactly) and added to the CTA's FP64 slot
+// (m x 8), reduced over the CTAs afterwards.
 constexpr int kHalfRows = 1024;
-constexpr int kHalfUnroll = 8;
+constexpr int kHmSK = 2;   // 16-row tiles per ring stage
+constexpr int kHmNS = 3;   // ring stages per warp
+constexpr int kHmWarps = kThreads / 32;
+
+__device__ __forceinline__ void ldsm_x4_trans(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_trans(unsigned& r0, unsigned& r1, const void* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+}
+// D (16x8 FP32) += A (16x16 FP16, row) * B (16x8 FP16, col)
+__device__ __forceinline__ void mma_16816(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
 
 __global__ void __launch_bounds__(kThreads) gram_half_kernel(int64_t n, int m, int nchunks,
                                                              const __half* __restrict__ Q, const float* __restrict__ W,
                                                              double* __restrict__ partial, int* __restrict__ ticket) {
-    constexpr int B = 8, NV = 64;
-    __shared__ __align__(16) float ws[kHalfRows * B];
+    constexpr int B = 8;
+    constexpr int STAGE = kHmSK * 32 * B;  // halves per ring stage (kHmSK tiles of 32 rows of 16 bytes)
+    __shared__ __align__(16) __half ws[kHalfRows * B];
+    __shared__ __align__(16) __half ring[kHmWarps][kHmNS][STAGE];
+    __shared__ float s_max[kHmWarps];
     __shared__ int s_chunk;
     const int nblocks = m / B;
+    const int npairs = (nblocks + 1) / 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tig = lane & 3;
     double* part = partial + (int64_t)blockIdx.x * m * B;
     for (int e = threadIdx.x; e < m * B; e += kThreads) part[e] = 0.0;
-    // after the butterfly lane l holds the sums vbase, vbase + 1
-    int vbase = 0;
-#pragma unroll
-    for (int k = 0; k < 5; ++k)
-        if (lane & (1 << k)) vbase += NV >> (k + 1);
-    const float4* ws4 = reinterpret_cast<const float4*>(ws);
+    const int mypairs = warp < npairs ? (npairs - warp + kHmWarps - 1) / kHmWarps : 0;
+    constexpr int NST = kHalfRows / 16 / kHmSK;  // stages per pair per chunk
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1);
@@ -829,64 +857,76 @@ __global__ void __launch_bounds__(kThreads) gram_half_kernel(int64_t n, int m, i
         if (c >= nchunks) break;
         const int64_t r0 = (int64_t)c * kHalfRows;
         const int rows = (int)min((int64_t)kHalfRows, n - r0);
-        for (int e = threadIdx.x; e < kHalfRows * 2; e += kThreads) {  // two float4 per row, zeros past the end
-            const int r = e >> 1;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (r < rows) v = __ldg(reinterpret_cast<const float4*>(W + (r0 + r) * B) + (e & 1));
-            reinterpret_cast<float4*>(ws)[e] = v;
-        }
+        // the chunk's largest |W| -> power-of-two scale
+        float mx = 0.f;
+        for (int e = threadIdx.x; e < rows * B; e += kThreads) mx = fmaxf(mx, fabsf(W[r0 * B + e]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) s_max[warp] = mx;
         __syncthreads();
-        for (int j = warp; j < nblocks; j += kThreads / 32) {
-            const uint4* qb = reinterpret_cast<const uint4*>(Q + ((int64_t)j * n + r0) * B);
-            float v[NV];
+        mx = 0.f;
 #pragma unroll
-            for (int e = 0; e < NV; ++e) v[e] = 0.f;
-            for (int r = lane; r < rows; r += 32 * kHalfUnroll) {
-                uint4 qv[kHalfUnroll];
+        for (int w = 0; w < kHmWarps; ++w) mx = fmaxf(mx, s_max[w]);
+        int ex = 0;
+        if (mx > 0.f) frexpf(mx, &ex);
+        const float scale = ldexpf(1.f, 14 - ex);
+        const double unscale = ldexp(1.0, ex - 14);
+        for (int e = threadIdx.x; e < kHalfRows * B; e += kThreads)
+            ws[e] = __float2half_rn(e < rows * B ? W[r0 * B + e] * scale : 0.f);
+        __syncthreads();
+        const int total = mypairs * NST;
+        // ring stage k: pair warp + (k / NST) * kHmWarps, rows (k % NST) * 16 * kHmSK ..
+        // lane L copies row (L & 15) of block 2p + (L >> 4) for each tile u
+        auto issue = [&](int k) {
+            if (k < total) {
+                const int p = warp + (k / NST) * kHmWarps;
+                const int j = 2 * p + (lane >> 4);
+                __half* buf = ring[warp][k % kHmNS];
 #pragma unroll
-                for (int u = 0; u < kHalfUnroll; ++u) {
-                    const int rr = r + 32 * u;
-                    qv[u] = rr < rows ? __ldg(qb + rr) : make_uint4(0u, 0u, 0u, 0u);
-                }
-#pragma unroll
-                for (int u = 0; u < kHalfUnroll; ++u) {
-                    const int rr = min(r + 32 * u, kHalfRows - 1);  // past the rows q is zero
-                    const float4 w0 = ws4[2 * rr], w1 = ws4[2 * rr + 1];
-                    const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-                    const __half2* h2 = reinterpret_cast<const __half2*>(&qv[u]);
-                    float q[8];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float2 f = __half22float2(h2[i]);
-                        q[2 * i] = f.x;
-                        q[2 * i + 1] = f.y;
-                    }
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-#pragma unroll
-                        for (int cc = 0; cc < 8; ++cc) v[i * 8 + cc] = fmaf(q[i], w[cc], v[i * 8 + cc]);
+                for (int u = 0; u < kHmSK; ++u) {
+                    const int rr = (k % NST) * 16 * kHmSK + u * 16 + (lane & 15);
+                    const bool ok = j < nblocks && rr < rows;
+                    cp_async16(buf + (u * 32 + lane) * B, ok ? (const void*)(Q + ((int64_t)j * n + r0 + rr) * B)
+                                                             : (const void*)Q, ok ? 16 : 0);
                 }
             }
+            cp_async_commit();
+        };
 #pragma unroll
-            for (int kk = 0; kk < 5; ++kk) {
-                const int o = 1 << kk;
-                const bool up = (lane & o) != 0;
-                const int hv = NV >> (kk + 1);
+        for (int k = 0; k < kHmNS - 1; ++k) issue(k);
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        // ldmatrix row addresses: A, matrix q = lane >> 3 (rows 0-7 / 8-15 of blocks 0 / 1), row lane & 7
+        const int a_row = ((lane >> 3) & 1) * 16 + (lane >> 4) * 8 + (lane & 7);
+        const int b_row = ((lane >> 3) & 1) * 8 + (lane & 7);
+        for (int k = 0; k < total; ++k) {
+            cp_async_wait<kHmNS - 2>();
+            __syncwarp();
+            issue(k + kHmNS - 1);  // into the stage consumed at k - 1
+            const __half* buf = ring[warp][k % kHmNS];
 #pragma unroll
-                for (int x = 0; x < NV / 2; ++x) {
-                    if (x < hv) {
-                        const float send = up ? v[x] : v[x + hv];
-                        const float keep = up ? v[x + hv] : v[x];
-                        v[x] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-                    }
-                }
+            for (int u = 0; u < kHmSK; ++u) {
+                unsigned a[4], bq[2];
+                ldsm_x4_trans(a[0], a[1], a[2], a[3], buf + (u * 32 + a_row) * B);
+                const int kk = (k % NST) * kHmSK + u;  // 16-row tile of the chunk
+                ldsm_x2_trans(bq[0], bq[1], ws + (kk * 16 + b_row) * B);
+                mma_16816(acc, a, bq);
             }
-#pragma unroll
-            for (int x = 0; x < 2; ++x) {
-                const int e = vbase + x;
-                part[(int64_t)(j * B + e / B) * B + (e % B)] += (double)v[x];
+            if ((k % NST) == NST - 1) {
+                // the pair's sums over this chunk: rows g (block 2p) and g + 8 (block 2p + 1), columns 2 tig, 2 tig + 1
+                const int p = warp + (k / NST) * kHmWarps;
+                const int j0 = 2 * p, j1 = 2 * p + 1;
+                double* o0 = part + ((int64_t)j0 * B + g) * B + 2 * tig;
+                o0[0] += (double)acc[0] * unscale;
+                o0[1] += (double)acc[1] * unscale;
+                if (j1 < nblocks) {
+                    double* o1 = part + ((int64_t)j1 * B + g) * B + 2 * tig;
+                    o1[0] += (double)acc[2] * unscale;
+                    o1[1] += (double)acc[3] * unscale;
+                }
+                acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
             }
         }
+        cp_async_wait<0>();
     }
 }
 

@@ -132,12 +132,17 @@ def test_block_reorth_matches_oracle_cgs2(dtype, b, nb):
 
 @pytest.mark.parametrize("n,nb", [(1024, 1), (3001, 5), (70_001, 40), (400_003, 3)])
 def test_block_gram_f16_matches_fp64_product_of_the_fp16_basis(n, nb):
-    """The FP16 first-pass Gram C = Q16^T W (b = 8) against the FP64 product
-    of the same FP16-rounded basis and FP32 W.  Products and sums over a
-    chunk in FP32 (at most 32 rows per lane, then 32 lanes), chunks in FP64:
-    entrywise |C - C_ref| <= 64 eps32 (|Q16|^T |W|).  The sizes cover one
-    exact chunk, a ragged last chunk, many blocks, and more chunks than
-    persistent CTAs (several chunks per CTA from the ticket counter)."""
+    """The FP16 first-pass Gram C = Q16^T W (b = 8, tensor cores) against the
+    FP64 product of the same FP16 basis and of W as the kernel rounds it:
+    per chunk of 1024 rows, W times the power of two that puts the chunk's
+    largest |W| in [2^13, 2^14), rounded to FP16 (nearest even), and the
+    product scaled back.  Per chunk the tensor core sums 16 exact products
+    per step and 64 steps in FP32, chunks in FP64: entrywise
+    |C - C_ref| <= 128 eps32 (|Q16|^T |W16|).  The sizes cover one exact
+    chunk, a ragged last chunk, many blocks (odd and even counts), and more
+    chunks than persistent CTAs (several chunks per CTA from the ticket
+    counter).  Against the unrounded W the error stays below 2^-10 of the
+    same scale (the first pass only has to remove the bulk)."""
     import ctypes as C
     torch, bbl = need_gpu()
     from paper_2210_15763_gb300 import _lib
@@ -152,10 +157,20 @@ def test_block_gram_f16_matches_fp64_product_of_the_fp16_basis(n, nb):
                                 C.c_void_p(Cd.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == 0, lib.bbl_last_error()
     Qh = Q.astype(np.float64)
+    W16 = np.empty((n, 8))
+    for r0 in range(0, n, 1024):
+        Wc = W[r0:r0 + 1024]
+        mx = float(np.max(np.abs(Wc)))
+        ex = int(np.frexp(np.float32(mx))[1]) if mx > 0 else 0
+        sc = np.float32(2.0 ** (14 - ex))
+        W16[r0:r0 + 1024] = (Wc * sc).astype(np.float16).astype(np.float64) / float(sc)
+    got = Cd.cpu().numpy()
+    ref = np.concatenate([Qh[j].T @ W16 for j in range(nb)])
+    bound = np.concatenate([np.abs(Qh[j]).T @ np.abs(W16) for j in range(nb)])
+    assert np.all(np.abs(got - ref) <= 128 * EPS32 * bound)
     Wh = W.astype(np.float64)
-    ref = np.concatenate([Qh[j].T @ Wh for j in range(nb)])
-    bound = np.concatenate([np.abs(Qh[j]).T @ np.abs(Wh) for j in range(nb)])
-    assert np.all(np.abs(Cd.cpu().numpy() - ref) <= 64 * EPS32 * bound)
+    ref32 = np.concatenate([Qh[j].T @ Wh for j in range(nb)])
+    assert np.all(np.abs(got - ref32) <= 2.0 ** -10 * bound)
 
 
 def test_fp16_first_pass_keeps_the_fp32_stage_and_the_result():
