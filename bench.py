@@ -47,10 +47,11 @@ SPMM_TRAFFIC_PER_NNZ = 1.185e9 / 139_708_000
 SELL_TRAFFIC_PER_NNZ = 1.248e9 / 139_708_000
 SELL_SIGMA = 256
 # DRAM bytes per algorithmic byte of the first-pass Gram from the FP16 basis
-# copy (gram_half_kernel, n*m*2 + n*8*4), from an ncu capture at n = 500,000,
-# m = 720 (0.7906 GB for 0.736 GB); it reads the copy once, so traffic grows
-# with n*m (None: not captured since the kernel last changed)
-GRAM16_TRAFFIC_PER_BYTE = 0.7906e9 / 0.736e9
+# copy (gram_half_kernel on the tensor cores, n*m*2 + n*8*4), from an ncu
+# capture at n = 500,000, m = 400 (451.9 MB for 416 MB); it reads the copy
+# once, so traffic grows with n*m (None: not captured since the kernel last
+# changed)
+GRAM16_TRAFFIC_PER_BYTE = 451.919616e6 / 416e6
 METRIC = "time-to-solve lowest 8 eigenpairs @resid 1e-8 (s)"
 # the headline step's settings: truncated-space sub-solve tolerance (FP32
 # storage at >= 1e-5), FP32 stage tolerance before the polish, FP16 copy of
@@ -389,7 +390,7 @@ def run_ours(args):
                  "traffic": (SPMM_TRAFFIC_PER_NNZ * A.nnz if sched["fmt"] == "csr" and (sched["lanes"] or 32) == 32
                              else SELL_TRAFFIC_PER_NNZ * A.nnz if sched["fmt"] == "sell" else None)},
         "gram": {"kernel": "gram_half_kernel + reduce_partials_kernel (first Gram-Schmidt pass of the FP32 "
-                 "stage, from the FP16 copy of the basis)", "launches": gram_calls, "total_ms": tot["t_gram_ms"],
+                 "stage, from the FP16 copy of the basis, mma.sync on the tensor cores)", "launches": gram_calls, "total_ms": tot["t_gram_ms"],
                  "achieved": gram_gbs, "bytes_per_launch": tot["gram_bytes_total"] / max(gram_calls, 1),
                  "traffic": GRAM16_TRAFFIC_PER_BYTE * tot["gram_bytes_total"] / max(gram_calls, 1)
                  if GRAM16_TRAFFIC_PER_BYTE else None},
