@@ -532,6 +532,198 @@ __global__ void __launch_bounds__(NT, 1024 / NT) kron_spmm_kernel(KronDesc d, in
         if (live(i)) kstore<T, VEC>(Ws + goff(i), acc[i]);
 }
 
+// 16-byte asynchronous global -> shared copy (cp.async), its group commit and wait
+__device__ __forceinline__ void kcp16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void kcommit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void kwait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int kPipeStages = 2;  // slabs in the per-thread ring
+
+// The same product with the slab stream prefetched: the slabs a CTA reads
+// form one sequence over all terms -- row p of Hp, then V[p] itself (for
+// Hn), then row p of each Cp_k -- and each thread copies its chunks of the
+// next slab into its own shared-memory ring with cp.async while it
+// accumulates the current one, so the stream runs on through the barriers
+// and the n-factor gathers (only a thread's own copies are read back by it,
+// so the ring needs no barrier).  The n-factor gathers load the row
+// pointers of the next factor ahead and the columns and values of up to 4
+// entries of a row at once.  Chunks are 16 bytes (VEC * sizeof(T) == 16).
+template <typename T, int CB, int IPT, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) kron_pipe_kernel(KronDesc d, int b, const T* __restrict__ V,
+                                                                  T* __restrict__ W) {
+    using H = typename KronVal<T>::type;
+    using Sh = KronShape<T, CB>;
+    constexpr int VEC = Sh::VEC, CPR = Sh::CPR;
+    static_assert(VEC * sizeof(T) == 16, "16-byte chunks");
+    constexpr int NS = kPipeStages;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nN = d.nN;
+    T* ring = reinterpret_cast<T*>(smem);                                // NS x IPT x NT chunks
+    T* S = ring + (size_t)NS * IPT * NT * VEC;                          // nN x CB tile
+    int* tstart = reinterpret_cast<int*>(S + (int64_t)nN * CB);          // segment starts (K + 3)
+    int* tcol = tstart + 40;
+    const int p = blockIdx.x;
+    const int c0 = blockIdx.y * CB;
+    const int nch = nN * CPR;
+    const int64_t slab = (int64_t)nN * b;
+    // segments: 0 = row p of Hp, 1 = V[p] itself, 2 + k = row p of Cp_k
+    const int nseg = 2 + d.K;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int len = 0;
+        if (lane < nseg) {
+            if (lane == 1) {
+                len = 1;
+            } else {
+                const int f = lane == 0 ? fHp() : fCp(lane - 2);
+                len = d.ptr[d.ptr_off[f] + p + 1] - d.ptr[d.ptr_off[f] + p];
+            }
+        }
+        int incl = len;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane < nseg) tstart[lane] = incl - len;
+        if (lane == nseg - 1) tstart[nseg] = incl;
+    }
+    __syncthreads();
+    H* tval = reinterpret_cast<H*>((reinterpret_cast<uintptr_t>(tcol + tstart[nseg]) + 15) & ~uintptr_t(15));
+    for (int sg = threadIdx.x >> 5; sg < nseg; sg += NT / 32) {
+        const int lane = threadIdx.x & 31;
+        if (sg == 1) {
+            if (lane == 0) {
+                tcol[tstart[1]] = p;
+                tval[tstart[1]] = H(1.0f);
+            }
+            continue;
+        }
+        const int fi = sg == 0 ? fHp() : fCp(sg - 2);
+        const int a0 = d.ptr[d.ptr_off[fi] + p];
+        const int la = d.ptr[d.ptr_off[fi] + p + 1] - a0;
+        for (int e = lane; e < la; e += 32) {
+            tcol[tstart[sg] + e] = d.col[d.nz_off[fi] + a0 + e];
+            tval[tstart[sg] + e] = kron_val<T>(d, d.nz_off[fi] + a0 + e);
+        }
+    }
+    __syncthreads();
+    const int J = tstart[nseg];  // slabs streamed
+
+    auto live = [&](int i) { return (int)threadIdx.x + i * NT < nch; };
+    auto goff = [&](int i) {
+        const int ch = threadIdx.x + i * NT;
+        return (int64_t)(ch / CPR) * b + c0 + (ch % CPR) * VEC;
+    };
+    auto soff = [&](int i) {
+        const int ch = threadIdx.x + i * NT;
+        return (ch / CPR) * CB + (ch % CPR) * VEC;
+    };
+    auto slot = [&](int j, int i) { return ring + ((size_t)((j % NS) * IPT + i) * NT + threadIdx.x) * VEC; };
+    auto issue = [&](int j) {
+        if (j < J) {
+            const T* Vs = V + (int64_t)tcol[j] * slab;
+#pragma unroll
+            for (int i = 0; i < IPT; ++i)
+                if (live(i)) kcp16(slot(j, i), Vs + goff(i));
+        }
+        kcommit();  // an empty group past the end keeps the count uniform
+    };
+
+    T acc[IPT][VEC];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[i][v] = T(0.0f);
+    // row pointers of an n-factor for this thread's rows
+    int f0[IPT], f1[IPT];
+    auto load_rows = [&](int fb) {
+        const int* bp = d.ptr + d.ptr_off[fb];
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            const int q = live(i) ? (int)((threadIdx.x + i * NT) / CPR) : 0;
+            f0[i] = __ldg(bp + q);
+            f1[i] = live(i) ? __ldg(bp + q + 1) : f0[i];
+        }
+    };
+    auto gather = [&](int fb) {
+        const int* bc = d.col + d.nz_off[fb];
+        const int vo = d.nz_off[fb];
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            const int cofs = soff(i) % CB;
+            for (int f = f0[i]; f < f1[i]; f += 4) {
+                int qc[4];
+                H h[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool ok = f + u < f1[i];
+                    qc[u] = ok ? __ldg(bc + f + u) : 0;
+                    h[u] = ok ? kron_val<T>(d, vo + f + u) : H(0.0f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (f + u < f1[i]) {
+                        T x[VEC];
+                        kload<T, VEC>(S + qc[u] * CB + cofs, x);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) acc[i][v] = kfma<T>(h[u], x[v], acc[i][v]);
+                    }
+                }
+            }
+        }
+    };
+
+    issue(0);
+    int j = 0;
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int fb = sg == 0 ? -1 : (sg == 1 ? fHn() : fCn(sg - 2));
+        if (fb >= 0) load_rows(fb);  // in flight during the stream
+        T u[IPT][VEC];
+#pragma unroll
+        for (int i = 0; i < IPT; ++i)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) u[i][v] = T(0.0f);
+        for (; j < tstart[sg + 1]; ++j) {
+            issue(j + 1);
+            kwait<1>();  // slab j has landed (the one just issued may be in flight)
+            const H a = tval[j];
+#pragma unroll
+            for (int i = 0; i < IPT; ++i) {
+                if (!live(i)) continue;
+                T x[VEC];
+                kload<T, VEC>(slot(j, i), x);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) u[i][v] = kfma<T>(a, x[v], u[i][v]);
+            }
+        }
+        if (sg == 0) {
+#pragma unroll
+            for (int i = 0; i < IPT; ++i)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[i][v] = acc[i][v] + u[i][v];
+            continue;
+        }
+        __syncthreads();  // every thread is done with the previous gather: the tile is free
+#pragma unroll
+        for (int i = 0; i < IPT; ++i)
+            if (live(i)) kstore<T, VEC>(S + soff(i), u[i]);
+        __syncthreads();
+        gather(fb);
+    }
+    kwait<0>();
+    T* Ws = W + (int64_t)p * slab;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i)
+        if (live(i)) kstore<T, VEC>(Ws + goff(i), acc[i]);
+}
+
 // Shared memory of one CTA: the tile, 32 table offsets, the table's columns
 // and (16-byte aligned) values.
 template <typename T>
@@ -545,8 +737,38 @@ size_t kron_smem(const bbl_matrix* A, int CB) {
 
 constexpr size_t kKronSmemMax = 200 * 1024;
 
+// the prefetching kernel's shared memory: ring + tile + segment table (one more entry)
+template <typename T>
+size_t kron_pipe_smem(const bbl_matrix* A, int CB, int IPT, int NT) {
+    using H = typename KronVal<T>::type;
+    const size_t ring = (size_t)kPipeStages * IPT * NT * 16;
+    const size_t tile = (size_t)A->kron_nN * CB * sizeof(T);
+    const size_t tab = 40 * sizeof(int) + (size_t)(A->kron_prow_cap + 1) * sizeof(int) + 16 +
+                       (size_t)(A->kron_prow_cap + 1) * sizeof(H);
+    return ring + tile + tab;
+}
+
+template <typename T, int CB, int IPT, int NT>
+bbl_status launch_kron_pipe(const bbl_matrix* A, int b, const T* V, T* W, size_t smem, cudaStream_t st) {
+    auto kern = kron_pipe_kernel<T, CB, IPT, NT>;
+    static bool attr = false;
+    if (!attr) {
+        BBL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKronSmemMax));
+        attr = true;
+    }
+    dim3 grid((unsigned)A->kron_nP, (unsigned)(b / CB));
+    kern<<<grid, NT, smem, st>>>(make_desc(A), b, V, W);
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
+}
+
 template <typename T, int CB, int IPT, int NT>
 bbl_status launch_kron_t(const bbl_matrix* A, int b, const T* V, T* W, size_t smem, cudaStream_t st) {
+    // 16-byte chunks: the prefetching kernel when its ring fits as well
+    if constexpr (CB * sizeof(T) >= 16 && CB <= 16) {
+        const size_t ps = kron_pipe_smem<T>(A, CB, IPT, NT);
+        if (ps <= kKronSmemMax && A->kron_K + 3 <= 40) return launch_kron_pipe<T, CB, IPT, NT>(A, b, V, W, ps, st);
+    }
     auto kern = kron_spmm_kernel<T, CB, IPT, NT>;
     static bool attr = false;
     if (!attr) {
