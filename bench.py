@@ -855,6 +855,40 @@ def run_kron(args):
     print(json.dumps(out))
 
 
+def run_kron_spmm(args):
+    """The factored SpMM alone on the kron_n2e6 factors (n = 2,000,000): FP32
+    blocks of b = 8 and 16, FP64 blocks of b = 8, each timed with CUDA events
+    over --reps launches after one warm-up; used for the ncu captures of the
+    factored kernel."""
+    import torch
+    import synth
+    import paper_2210_15763_gb300 as bbl
+    f = synth.named_factors(WORKLOAD)
+    M = bbl.KronMatrix(f, storage="fp32")
+    lens = np.diff(f.Hp.row_ptr) + 1 + sum(np.diff(c.row_ptr) for c in f.Cp)
+    out = {"mode": "kron-spmm", "n": M.n, "nnz_expansion": M.nnz, "factor_bytes": int(M.device_bytes)}
+    for dt, b in (("fp32", 8), ("fp32", 16), ("fp64", 8)):
+        V = torch.randn(M.n, b, device="cuda", dtype=torch.float32 if dt == "fp32" else torch.float64)
+        W = torch.empty_like(V)
+        fn = (lambda: bbl.spmm(M, V, W)) if dt == "fp32" else (lambda: bbl.spmm_f64(M, V, W))
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.reps
+        s_el = 4 if dt == "fp32" else 8
+        stream = float(lens.sum()) * f.Hn.n * b * s_el
+        out[f"{dt}_b{b}"] = {"ms": ms, "stream_bytes": stream, "stream_gbs": stream / (ms * 1e-3) / 1e9,
+                             "hbm_alg_bytes": 2.0 * M.n * b * s_el,
+                             "gflops_expansion": 2.0 * M.nnz * b / (ms * 1e-3) / 1e9}
+    print(json.dumps(out))
+
+
 def run_c2(args):
     """The b sweep of the plain FP64 configuration at n = 2,000,000 (the
     paper's Tables I-II: time per operation and vector-equivalent iterations
@@ -898,7 +932,8 @@ def run_c2(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--mode", default="solve", choices=["solve", "kernels", "batched", "learned", "c3", "kron", "c2"])
+    ap.add_argument("--mode", default="solve",
+                    choices=["solve", "kernels", "batched", "learned", "c3", "kron", "c2", "kron-spmm"])
     ap.add_argument("--c2-blocks", default="1,4,8,16")
     ap.add_argument("--c3-vectors", type=int, default=300)
     ap.add_argument("--c3-fp64", action="store_true")
@@ -938,6 +973,8 @@ def main():
         run_kron(args)
     elif args.mode == "c2":
         run_c2(args)
+    elif args.mode == "kron-spmm":
+        run_kron_spmm(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -72,7 +72,8 @@ class Matrix:
     """Device copy of a sparse symmetric matrix (bbl_matrix).
 
     `csr` is anything with n, row_ptr (int64), col (int32) and val (float64 or
-    float32) as numpy arrays or torch tensors (host or device)."""
+    float32) as numpy arrays or torch tensors (host or device).  fmt: "csr",
+    "sell" (sell_sigma = sorting window) or "tiled" (sell_sigma = tile size)."""
 
     def __init__(self, csr, storage: str = "fp64", fmt: str = "csr", sell_sigma: int = 0, keep_fp64: bool = False,
                  check_symmetry: bool = False, stream=None):
@@ -92,7 +93,7 @@ class Matrix:
         h = C.c_void_p()
         st = lib.bbl_matrix_create(int(csr.n), int(rp[-1]) if isinstance(rp, np.ndarray) else int(rp[-1].item()),
                                    _ptr(rp), _ptr(col), _ptr(val), vdt, FP32 if storage == "fp32" else FP64,
-                                   SELL if fmt == "sell" else CSR, int(sell_sigma), int(keep_fp64),
+                                   {"sell": SELL, "tiled": _lib.TILED}.get(fmt, CSR), int(sell_sigma), int(keep_fp64),
                                    int(check_symmetry), _stream(stream), C.byref(h))
         self._keep = None
         _lib.check(st)

@@ -10,7 +10,7 @@ BBL_OK = 0
 STATUS = {0: "BBL_OK", 1: "BBL_ERR_INVALID_ARG", 2: "BBL_ERR_NOT_SYMMETRIC", 3: "BBL_ERR_OOM", 4: "BBL_ERR_CUDA",
           5: "BBL_ERR_NOT_CONVERGED", 6: "BBL_ERR_NUMERICAL", 7: "BBL_ERR_TIMEOUT", 8: "BBL_ERR_UNSUPPORTED"}
 FP64, FP32 = 0, 1
-CSR, SELL, KRON = 0, 1, 2
+CSR, SELL, KRON, TILED = 0, 1, 2, 3
 
 
 class Options(C.Structure):

@@ -183,12 +183,20 @@ struct bbl_matrix {
     int kron_prow_cap = 0;  // most entries of one row p over Hp and all Cp_k
     int kron_row_cap = 0;   // power of two >= the most term contributions of one row of H
     bbl::DevBuf kf_ptr, kf_col, kf_val32, kf_val64;
+    // tiled format (fmt == BBL_TILED, tiled.cu): row blocks and column tiles of
+    // `tile` rows; per (row block, column tile) pair with entries: the tile id
+    // (int32), its first entry (int64), tile + 1 row offsets (uint16); entries
+    // as the column within the tile (uint16) and the value (storage type)
+    int tile = 0;
+    int64_t t_nrb = 0, t_npairs = 0;
+    bbl::DevBuf t_pair_ptr, t_pair_tile, t_pair_base, t_off, t_lcol, t_val;
     int64_t kf_ptr_off[bbl::kKronMaxFactors] = {};
     int64_t kf_nz_off[bbl::kKronMaxFactors] = {};
     int64_t device_bytes() const {
         return (int64_t)(row_ptr.bytes + col.bytes + val.bytes + val64.bytes + slice_ptr.bytes + sell_col.bytes +
                          sell_val.bytes + sell_len.bytes + perm.bytes + diag.bytes + kf_ptr.bytes + kf_col.bytes +
-                         kf_val32.bytes + kf_val64.bytes);
+                         kf_val32.bytes + kf_val64.bytes + t_pair_ptr.bytes + t_pair_tile.bytes +
+                         t_pair_base.bytes + t_off.bytes + t_lcol.bytes + t_val.bytes);
     }
 };
 
@@ -209,11 +217,24 @@ bbl_status spmm_rows_f64(const bbl_matrix* A, int b, const double* V, double* W,
 inline double spmm_alg_bytes(const bbl_matrix* A, int b, double sv, double sx) {
     const double blocks = 2.0 * (double)A->n * b * sx;
     if (A->fmt == BBL_KRON) return (double)(A->kf_ptr.bytes + A->kf_col.bytes + A->kf_val32.bytes) + blocks;
+    // tiled: 16-bit columns and the values, the pair tables and row offsets
+    if (A->fmt == BBL_TILED)
+        return (double)A->nnz * (sv + 2.0) + (double)A->t_npairs * (12.0 + 2.0 * (A->tile + 1)) + blocks;
     return (double)A->nnz * (sv + 4.0) + (double)(A->n + 1) * 8.0 + blocks;
 }
 // kron.cu: W = H V from the factors of a BBL_KRON matrix; dt = element type
 // of V and W (BBL_FP32, BBL_FP64 or kDF32)
 bbl_status kron_spmm(const bbl_matrix* A, int b, int dt, const void* V, void* W, cudaStream_t st);
+// tiled.cu: the tiled copy of A's CSR (tile rows per row block / columns per
+// tile), and W = H V from it (dt as in kron_spmm; b a multiple of 16 bytes of
+// blocks: tiled_supports)
+bbl_status tiled_build(bbl_matrix* A, int T, cudaStream_t st);
+bbl_status tiled_spmm(const bbl_matrix* A, int b, int dt, const void* V, void* W, cudaStream_t st);
+inline bool tiled_supports(const bbl_matrix* A, int b, int dt) {
+    const int es = (dt == BBL_FP32) ? 4 : 8;
+    const int vec = 16 / es;
+    return A->fmt == BBL_TILED && A->tile > 0 && b % vec == 0 && 2 * (int64_t)A->tile * vec * es <= 200 * 1024;
+}
 // the principal submatrix H[S,S] of a BBL_KRON matrix as CSR (FP64 values):
 // S device int32 [k] ascending rows, pos device int32 [n] (position in S or
 // -1); row_ptr (int64 [k+1]), col, val allocated here

@@ -308,7 +308,12 @@ bbl_status bbl_matrix_create(int64_t n, int64_t nnz, const int64_t* row_ptr, con
         return set_error(BBL_ERR_INVALID_ARG, "matrix_create: NULL array");
     if ((val_dtype != BBL_FP64 && val_dtype != BBL_FP32) || (storage != BBL_FP64 && storage != BBL_FP32))
         return set_error(BBL_ERR_INVALID_ARG, "matrix_create: bad dtype");
-    if (fmt != BBL_CSR && fmt != BBL_SELL) return set_error(BBL_ERR_INVALID_ARG, "matrix_create: bad format");
+    if (fmt != BBL_CSR && fmt != BBL_SELL && fmt != BBL_TILED)
+        return set_error(BBL_ERR_INVALID_ARG, "matrix_create: bad format");
+    const int tile = fmt == BBL_TILED ? (sell_sigma > 0 ? sell_sigma : 1024) : 0;
+    if (fmt == BBL_TILED && (tile < 16 || tile > 8192))
+        return set_error(BBL_ERR_INVALID_ARG, "matrix_create: tile %d outside 16..8192", tile);
+    if (fmt == BBL_TILED) sell_sigma = 0;
     if (sell_sigma == 0) sell_sigma = kSellC;
     if (fmt == BBL_SELL && (sell_sigma < kSellC || sell_sigma % kSellC || sell_sigma > 4096))
         return set_error(BBL_ERR_INVALID_ARG, "matrix_create: sell_sigma must be a multiple of 32 in 32..4096");
@@ -375,6 +380,7 @@ bbl_status bbl_matrix_create(int64_t n, int64_t nnz, const int64_t* row_ptr, con
         else s = sell_build<float>(A, A->val.as<float>(), st);
         if (s != BBL_OK) return fail(s);
     }
+    if (fmt == BBL_TILED && (s = tiled_build(A, tile, st)) != BBL_OK) return fail(s);
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(set_error(BBL_ERR_CUDA, "matrix_create: sync failed"));
     *out = A;
     return BBL_OK;

@@ -368,6 +368,10 @@ bbl_status spmm_typed(const bbl_matrix* A, int b, const TM* csr_val, const TM* s
 bbl_status spmm_dispatch(const bbl_matrix* A, int b, const void* V, void* W, bool f64_arith, cudaStream_t st,
                          int G) {
     if (A->fmt == BBL_KRON) return kron_spmm(A, b, (f64_arith || A->storage == BBL_FP64) ? BBL_FP64 : BBL_FP32, V, W, st);
+    {
+        const int dt = (f64_arith || A->storage == BBL_FP64) ? BBL_FP64 : BBL_FP32;
+        if (G <= 0 && tiled_supports(A, b, dt)) return tiled_spmm(A, b, dt, V, W, st);
+    }
     if (A->storage == BBL_FP64) {
         return spmm_typed<double, double>(A, b, A->has_csr ? A->val.as<double>() : nullptr,
                                           A->fmt == BBL_SELL ? A->sell_val.as<double>() : nullptr,
@@ -403,6 +407,7 @@ bbl_status spmm_df32(const bbl_matrix* A, int b, const void* V, void* W, cudaStr
     if (A->storage != BBL_FP32)
         return set_error(BBL_ERR_UNSUPPORTED, "spmm: float-float blocks need FP32 matrix values");
     if (A->fmt == BBL_KRON) return kron_spmm(A, b, kDF32, V, W, st);
+    if (tiled_supports(A, b, kDF32)) return tiled_spmm(A, b, kDF32, V, W, st);
     return spmm_typed<float, df32>(A, b, A->has_csr ? A->val.as<float>() : nullptr,
                                    A->fmt == BBL_SELL ? A->sell_val.as<float>() : nullptr, static_cast<const df32*>(V),
                                    static_cast<df32*>(W), st, 0);

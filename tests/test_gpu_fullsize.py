@@ -69,13 +69,14 @@ def test_fullsize_mixed_precision_matches_oracle(kron_n2e6):
     assert rel.max() <= 1e-6, rel
 
 
-@pytest.mark.parametrize("fmt,sigma", [("sell", 1024), ("csr", 0)])
+@pytest.mark.parametrize("fmt,sigma", [("sell", 1024), ("csr", 0), ("tiled", 1000)])
 def test_fullsize_headline_step_matches_oracle(kron_n2e6, fmt, sigma):
     """The benchmark's timed step exactly: the bootstrapped pivot (20,000
     lowest-diagonal rows, truncated-space sub-solve to 1e-4 in FP32 storage),
     the FP32 stage to 3e-7 with the FP16 first-pass Gram, the float-float
-    polish and the FP64 residuals, on the FP32-stored matrix in either format
-    the SpMM autotuner may pick (SELL-C-sigma with sigma = 1024, or CSR).
+    polish and the FP64 residuals, on the FP32-stored matrix in each format
+    the SpMM autotuner may pick (SELL-C-sigma with sigma = 1024, CSR, or
+    the tiled format with tiles of 1000).
     The eight eigenvalues agree with the FP64 oracle's to relative 1e-10."""
     import bench
     torch, bbl = need_gpu()
