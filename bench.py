@@ -42,10 +42,12 @@ TRUNC = 20000
 # of the same family (dram__bytes_read.sum + dram__bytes_write.sum =
 # 1.185 GB for 139,708,000 nonzeros); traffic grows with the nonzeros.
 SPMM_TRAFFIC_PER_NNZ = 1.185e9 / 139_708_000
-# the same for the FP32 SELL-C-sigma SpMM (b = 8; sigma = 256 in the capture):
-# 1.248 GB for 139,708,000 nonzeros
-SELL_TRAFFIC_PER_NNZ = 1.248e9 / 139_708_000
+# the same for the FP32 SELL-C-sigma SpMM (b = 8; sigma = 1024 in the
+# capture, the window the autotuner picks): 1.2045 GB for 139,708,000 nonzeros
+SELL_TRAFFIC_PER_NNZ = 1.2045e9 / 139_708_000
 SELL_SIGMA = 256
+# the sorting window the autotuner picks for this family (kernels mode)
+KERNELS_SELL_SIGMA = 1024
 # DRAM bytes per algorithmic byte of the first-pass Gram from the FP16 basis
 # copy (gram_half_kernel on the tensor cores, n*m*2 + n*8*4), from an ncu
 # capture at n = 500,000, m = 400 (451.9 MB for 416 MB); it reads the copy
@@ -502,7 +504,7 @@ def run_kernels(args):
     import paper_2210_15763_gb300 as bbl
     A = synth.kron_matrix(WORKLOAD, scale=args.scale)
     n = A.n
-    M = bbl.Matrix(A, storage="fp32", fmt="sell", sell_sigma=SELL_SIGMA)
+    M = bbl.Matrix(A, storage="fp32", fmt="sell", sell_sigma=KERNELS_SELL_SIGMA)
     g = torch.Generator(device="cuda").manual_seed(1)
     V = torch.randn(n, B, device="cuda", dtype=torch.float32, generator=g)
     W = torch.empty_like(V)
@@ -531,6 +533,21 @@ def run_kernels(args):
     t = timeit(lambda: bbl.spmm(Mc, V, W), args.reps)
     out["spmm_csr_fp32"] = {"ms": t, "GBs": by / t / 1e6}
     del Mc
+    # the tiled format with tiles of nN rows (one proton row per row block,
+    # one proton column per tile), and b = 16 (64-byte rows of V) beside b = 8
+    nN = synth.kron_config(WORKLOAD, args.scale)["nN"]
+    Mt = bbl.Matrix(A, storage="fp32", fmt="tiled", sell_sigma=nN)
+    t = timeit(lambda: bbl.spmm(Mt, V, W), args.reps)
+    out["spmm_tiled_fp32"] = {"ms": t, "GBs": by / t / 1e6, "tile": nN}
+    V16 = torch.randn(n, 16, device="cuda", dtype=torch.float32, generator=g)
+    W16 = torch.empty_like(V16)
+    by16 = A.nnz * 8 + (n + 1) * 8 + 2 * n * 16 * 4
+    t = timeit(lambda: bbl.spmm(Mt, V16, W16), args.reps)
+    out["spmm_tiled_fp32_b16"] = {"ms": t, "GBs": by16 / t / 1e6}
+    del Mt
+    t = timeit(lambda: bbl.spmm(M, V16, W16), args.reps)
+    out["spmm_sell_fp32_b16"] = {"ms": t, "GBs": by16 / t / 1e6}
+    del V16, W16
     m = nb * B
     t = timeit(lambda: bbl.block_gram(basis, Wr), args.reps)
     out["gram_fp32"] = {"ms": t, "GBs": (n * m * 4 + n * B * 4) / t / 1e6}

@@ -186,14 +186,15 @@ bbl_status bbl_workspace_release(void);
  *   fmt         BBL_CSR, or BBL_SELL (SELL-C-sigma with C = 32 rows per
  *               slice, rows sorted by length inside windows of sell_sigma
  *               rows; sell_sigma a multiple of 32, 0 = 32 = no sorting)
- *               BBL_TILED: rows in blocks of `sell_sigma` rows (0 = 1024, at
- *               most 8192) and columns in tiles of as many columns; per row
+ *               BBL_TILED: rows in blocks of `sell_sigma` rows (0 = 1024,
+ *               16..1024) and columns in tiles of as many columns; per row
  *               block the entries are grouped by column tile (16-bit column
  *               in the tile, 16-bit row offsets; at most 65535 entries of
- *               one row block in one tile, BBL_ERR_UNSUPPORTED otherwise),
- *               and the SpMM stages each touched tile of V in shared memory
- *               (b a multiple of 16 bytes of block elements; other b use the
- *               CSR copy)
+ *               one row block in one tile, BBL_ERR_UNSUPPORTED otherwise;
+ *               inside a tile, slot-major per 64-row slice), and the SpMM
+ *               stages each touched tile of V in shared memory (b a
+ *               multiple of 16 bytes of block elements; other b use the CSR
+ *               copy)
  *   keep_fp64   FP32 storage only: also keep an FP64 CSR copy of the values
  *               for the FP64 polish stage and the FP64 residual
  *   check_symmetry  1: verify H_ij == H_ji exactly (BBL_ERR_NOT_SYMMETRIC)

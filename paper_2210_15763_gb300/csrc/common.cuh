@@ -184,9 +184,10 @@ struct bbl_matrix {
     int kron_row_cap = 0;   // power of two >= the most term contributions of one row of H
     bbl::DevBuf kf_ptr, kf_col, kf_val32, kf_val64;
     // tiled format (fmt == BBL_TILED, tiled.cu): row blocks and column tiles of
-    // `tile` rows; per (row block, column tile) pair with entries: the tile id
-    // (int32), its first entry (int64), tile + 1 row offsets (uint16); entries
-    // as the column within the tile (uint16) and the value (storage type)
+    // `tile` rows (<= 1024); per (row block, column tile) pair with entries:
+    // the tile id (int32), its first entry (int64), tile + 1 row offsets
+    // (uint16, row-major prefix sums); entries as the column within the tile
+    // (uint16) and the value (storage type), slot-major per 64-row slice
     int tile = 0;
     int64_t t_nrb = 0, t_npairs = 0;
     bbl::DevBuf t_pair_ptr, t_pair_tile, t_pair_base, t_off, t_lcol, t_val;
@@ -233,7 +234,8 @@ bbl_status tiled_spmm(const bbl_matrix* A, int b, int dt, const void* V, void* W
 inline bool tiled_supports(const bbl_matrix* A, int b, int dt) {
     const int es = (dt == BBL_FP32) ? 4 : 8;
     const int vec = 16 / es;
-    return A->fmt == BBL_TILED && A->tile > 0 && b % vec == 0 && 2 * (int64_t)A->tile * vec * es <= 200 * 1024;
+    return A->fmt == BBL_TILED && A->tile > 0 && A->tile <= 1024 && b % vec == 0 &&
+           2 * (int64_t)A->tile * vec * es <= 200 * 1024;
 }
 // the principal submatrix H[S,S] of a BBL_KRON matrix as CSR (FP64 values):
 // S device int32 [k] ascending rows, pos device int32 [n] (position in S or

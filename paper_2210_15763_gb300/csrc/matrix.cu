@@ -311,8 +311,8 @@ bbl_status bbl_matrix_create(int64_t n, int64_t nnz, const int64_t* row_ptr, con
     if (fmt != BBL_CSR && fmt != BBL_SELL && fmt != BBL_TILED)
         return set_error(BBL_ERR_INVALID_ARG, "matrix_create: bad format");
     const int tile = fmt == BBL_TILED ? (sell_sigma > 0 ? sell_sigma : 1024) : 0;
-    if (fmt == BBL_TILED && (tile < 16 || tile > 8192))
-        return set_error(BBL_ERR_INVALID_ARG, "matrix_create: tile %d outside 16..8192", tile);
+    if (fmt == BBL_TILED && (tile < 16 || tile > 1024))
+        return set_error(BBL_ERR_INVALID_ARG, "matrix_create: tile %d outside 16..1024", tile);
     if (fmt == BBL_TILED) sell_sigma = 0;
     if (sell_sigma == 0) sell_sigma = kSellC;
     if (fmt == BBL_SELL && (sell_sigma < kSellC || sell_sigma % kSellC || sell_sigma > 4096))

@@ -2,22 +2,32 @@
 // from shared memory (Sec. II.B, Eq. 3: each stored element H_ij reads the b
 // contiguous values V[j, :]).
 //
-// Rows are grouped into row blocks of T rows and columns into column tiles
-// of T columns.  For each row block the stored entries are grouped by
-// column tile ("pairs" (row block, tile) with at least one entry), and
-// inside a pair by row: 16-bit column within the tile, the value, and per
-// row a 16-bit offset into the pair's segment.  One CTA forms the W rows of
-// one row block (or a group of its columns): it walks the block's pairs,
-// copies the pair's T x b tile of V into shared memory with cp.async (two
-// buffers: the next tile lands while the current one is used), and each
-// thread multiplies its rows' entries of the pair by rows of the staged
-// tile.  The stored entries stream from HBM once (6 bytes per nonzero in
-// FP32: 2 + 4); the tiles of V come from L2.  The L1 serves about one
-// gathered 32-byte row per cycle when rows of V are fetched straight from
-// global memory; from shared memory the same gathers take a few rows per
-// cycle.  The format helps when the rows of a block touch few column
-// tiles (a block-structured sparsity such as the proton x neutron
-// factorised matrices); the CSR copy is kept for the rest of the library.
+// Rows are grouped into row blocks of T rows (T <= 1024) and columns into
+// column tiles of T columns.  For each row block the stored entries are
+// grouped by column tile ("pairs" (row block, tile) with at least one
+// entry): a 16-bit column within the tile and the value per entry, and per
+// row a 16-bit offset into the pair's segment.  Inside a pair the rows come
+// in slices of 64; one warp owns a slice, lane l rows l and 32 + l, and the
+// slice's entries are stored slot-major ("jagged diagonal"): slot s holds,
+// in lane order, the s-th entry of every lane whose two rows have more than
+// s entries in the pair (row l's entries, then row 32 + l's).  The active
+// lanes of a slot read consecutive entries, so every load of the entry
+// stream is coalesced, and a lane finds its entry from a warp ballot.
+//
+// One CTA forms the W rows of one row block (or a group of its columns): it
+// walks the block's pairs, copies the pair's T x CB tile of V into shared
+// memory with cp.async (two buffers: the next tile lands while the current
+// one is used), and each lane multiplies its rows' entries of the pair by
+// rows of the staged tile, accumulating in registers.  The 16-byte chunks
+// of a tile row are XOR-swizzled by the row index so that the first chunks
+// of rows that differ in their low bits fall in all eight bank groups.  The
+// stored entries stream from HBM once (6 bytes per nonzero in FP32: 2 + 4);
+// the tiles of V come from L2.  The L1 serves about one gathered 32-byte
+// row per cycle when rows of V are fetched straight from global memory;
+// from shared memory the same gathers take several rows per cycle.  The
+// format helps when the rows of a block touch few column tiles (a
+// block-structured sparsity such as the proton x neutron factorised
+// matrices); the CSR copy is kept for the rest of the library.
 #include <algorithm>
 #include <vector>
 
@@ -136,25 +146,36 @@ __global__ void __launch_bounds__(kTileHistThreads) tile_fill_kernel(int64_t n, 
         __syncthreads();
         unsigned short* po = off + pr * (T + 1);
         for (int q = threadIdx.x; q <= T; q += blockDim.x) po[q] = (unsigned short)cnt[q];
+        // copies in slot-major order per 64-row slice (warp per slice): the
+        // stream of lane l is row q0 + l's entries, then row q0 + 32 + l's
         const int64_t base = pbase[pr];
-        for (int q = threadIdx.x; q < rows; q += blockDim.x) {
-            int64_t k = cur[q];
-            int64_t o = base + cnt[q];
-            const int64_t e = rp[r0 + q + 1];
-            while (k < e && ci[k] < lim) {
-                lcol[o] = (unsigned short)(ci[k] - t * T);
-                tval[o] = va[k];
-                ++o;
-                ++k;
+        const unsigned lt = (1u << lane) - 1u;
+        for (int q0 = warp * 64; q0 < T; q0 += (int)(blockDim.x / 32) * 64) {
+            const int qa = q0 + lane, qb = qa + 32;
+            const int ca = qa < T ? cnt[qa + 1] - cnt[qa] : 0;
+            const int cb = qb < T ? cnt[qb + 1] - cnt[qb] : 0;
+            const int tot = ca + cb;
+            const int smax = __reduce_max_sync(0xffffffffu, tot);
+            int64_t o = base + cnt[q0];
+            for (int sl = 0; sl < smax; ++sl) {
+                const unsigned m = __ballot_sync(0xffffffffu, sl < tot);
+                if (sl < tot) {
+                    const int64_t k = sl < ca ? cur[qa] + sl : cur[qb] + (sl - ca);
+                    const int64_t w = o + __popc(m & lt);
+                    lcol[w] = (unsigned short)(ci[k] - t * T);
+                    tval[w] = va[k];
+                }
+                o += __popc(m);
             }
-            cur[q] = k;
+            if (qa < T) cur[qa] += ca;
+            if (qb < T) cur[qb] += cb;
         }
         __syncthreads();
     }
 }
 
 // ------------------------------------------------------------------ SpMM
-constexpr int kTiledThreads = 512;
+constexpr int kTiledMaxThreads = 512;  // tiles of at most 1024 rows
 
 __device__ __forceinline__ void tcp16(void* smem, const void* gmem, int src_bytes) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -214,122 +235,154 @@ __device__ __forceinline__ TX tfma(typename TiledVal<TX>::type h, TX v, TX c) {
     else return fma(h, v, c);
 }
 
+// Chunk of row r of a staged tile that holds its 16-byte chunk c (C chunks
+// per row): c XOR a few bits of r, so that rows differing in their low bits
+// spread their chunks over the eight 16-byte bank groups.
+template <int C>
+__device__ __forceinline__ int tswz(int r, int c) {
+    if constexpr (C == 1) return 0;
+    else return c ^ ((r / (8 / C)) & (C - 1));
+}
+
 // One CTA: row block rb = blockIdx.x, columns [c0, c0 + CB), c0 =
-// blockIdx.y * CB.  Thread t owns the 16-byte chunks ch = t + i * kTiledThreads
-// (i < IPT) of the block's T x CB rows: row q = ch / CPR, part ch % CPR.
-// Shared memory: two T x CB tiles of V.  TM: stored value type; TX: block
-// type (and, through TiledVal, the type of the value in the product).
-template <typename TM, typename TX, int CB, int IPT>
-__global__ void __launch_bounds__(kTiledThreads, 2) tiled_spmm_kernel(
+// blockIdx.y * CB; 32 * ceil(T / 64) threads.  Warp w owns rows 64 w + l and
+// 64 w + 32 + l (lane l).  Shared memory: two T x CB tiles of V.  TM: stored
+// value type; TX: block type (and, through TiledVal, the type of the value
+// in the product).
+template <typename TM, typename TX, int CB>
+__global__ void __launch_bounds__(kTiledMaxThreads, 2) tiled_spmm_kernel(
     int64_t n, int T, int b, const int64_t* __restrict__ pair_ptr, const int* __restrict__ ptile,
     const int64_t* __restrict__ pbase, const unsigned short* __restrict__ off, const unsigned short* __restrict__ lcol,
     const TM* __restrict__ tval, const TX* __restrict__ V, TX* __restrict__ W) {
     using H = typename TiledVal<TX>::type;
     constexpr int VEC = 16 / (int)sizeof(TX);
-    constexpr int CPR = CB / VEC;
-    static_assert(CB % VEC == 0, "column group of whole 16-byte chunks");
+    constexpr int C = CB / VEC;
+    static_assert(CB % VEC == 0 && C <= 8, "column group of one to eight 16-byte chunks");
     extern __shared__ __align__(16) unsigned char smem[];
     TX* Sbuf = reinterpret_cast<TX*>(smem);  // [2][T * CB]
     const int rb = blockIdx.x;
     const int c0 = blockIdx.y * CB;
     const int64_t r0 = (int64_t)rb * T;
     const int rows = (int)min((int64_t)T, n - r0);
-    const int nch = T * CPR;
+    const int nch = T * C;
     const int64_t p0 = pair_ptr[rb], p1 = pair_ptr[rb + 1];
     const int np = (int)(p1 - p0);
+    const int lane = threadIdx.x & 31;
+    const int q0 = (threadIdx.x >> 5) * 64;  // < T
+    const int qa = q0 + lane, qb = qa + 32;
+    const unsigned lt = (1u << lane) - 1u;
 
     // copy tile k (pair p0 + k) of V into buffer k & 1: rows t*T .. t*T + T - 1
-    // (zeros past n), columns [c0, c0 + CB)
+    // (zeros past n), columns [c0, c0 + CB), chunks swizzled
     auto issue = [&](int k) {
         if (k < np) {
             const int t = ptile[p0 + k];
             TX* S = Sbuf + (size_t)(k & 1) * T * CB;
             const int64_t g0 = (int64_t)t * T;
-            for (int ch = threadIdx.x; ch < nch; ch += kTiledThreads) {
-                const int q = ch / CPR, cp = ch % CPR;
+            for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) {
+                const int q = ch / C, c = ch % C;
                 const bool ok = g0 + q < n;
-                tcp16(S + q * CB + cp * VEC, ok ? (const void*)(V + (g0 + q) * b + c0 + cp * VEC) : (const void*)V,
-                      ok ? 16 : 0);
+                tcp16(S + (q * C + tswz<C>(q, c)) * VEC,
+                      ok ? (const void*)(V + (g0 + q) * b + c0 + c * VEC) : (const void*)V, ok ? 16 : 0);
             }
         }
         tcommit();
     };
-
-    TX acc[IPT][VEC];
-#pragma unroll
-    for (int i = 0; i < IPT; ++i)
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) acc[i][v] = TX(0.0f);
-    int qrow[IPT], cofs[IPT];
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        const int ch = threadIdx.x + i * kTiledThreads;
-        qrow[i] = (ch < nch && ch / CPR < rows) ? ch / CPR : -1;
-        cofs[i] = (ch % CPR) * VEC;
-    }
-    // row offsets of the next pair, loaded ahead
-    int o0[IPT], o1[IPT];
-    auto load_offs = [&](int k) {
-#pragma unroll
-        for (int i = 0; i < IPT; ++i) {
-            o0[i] = o1[i] = 0;
-            if (k < np && qrow[i] >= 0) {
-                const unsigned short* po = off + (p0 + k) * (T + 1);
-                o0[i] = __ldg(po + qrow[i]);
-                o1[i] = __ldg(po + qrow[i] + 1);
+    // the two rows' entry counts and the slice's first entry in pair k
+    int na = 0, nb = 0, ns = 0;
+    auto fetch = [&](int k) {
+        na = nb = ns = 0;
+        if (k < np) {
+            const unsigned short* po = off + (p0 + k) * (T + 1);
+            int a0 = 0;
+            if (qa < T) {
+                a0 = __ldg(po + qa);
+                na = __ldg(po + qa + 1) - a0;
             }
+            if (qb < T) nb = __ldg(po + qb + 1) - __ldg(po + qb);
+            ns = __shfl_sync(0xffffffffu, a0, 0);  // lane 0: row q0 < T
         }
     };
+
+    TX accA[CB], accB[CB];
+#pragma unroll
+    for (int v = 0; v < CB; ++v) accA[v] = accB[v] = TX(0.0f);
     issue(0);
-    load_offs(0);
+    fetch(0);
     for (int k = 0; k < np; ++k) {
         issue(k + 1);  // buffer (k + 1) & 1 was released by the barrier at the end of step k - 1
         twait<1>();
         __syncthreads();  // tile k complete from every thread's copies
         const TX* S = Sbuf + (size_t)(k & 1) * T * CB;
-        const int64_t base = pbase[p0 + k];
-        int a0[IPT], a1[IPT];
+        const int ca = na, tot = na + nb;
+        int64_t pos = pbase[p0 + k] + ns;
+        fetch(k + 1);
+        const int smax = __reduce_max_sync(0xffffffffu, tot);
+        const int send = (smax + 3) & ~3;
+        TX cur[CB];
 #pragma unroll
-        for (int i = 0; i < IPT; ++i) {
-            a0[i] = o0[i];
-            a1[i] = o1[i];
-        }
-        load_offs(k + 1);
+        for (int v = 0; v < CB; ++v) cur[v] = TX(0.0f);
+        for (int s0 = 0; s0 < send; s0 += 4) {
+            int lc[4];
+            H h[4];
 #pragma unroll
-        for (int i = 0; i < IPT; ++i) {
-            for (int e = a0[i]; e < a1[i]; e += 4) {
-                int lc[4];
-                H h[4];
+            for (int u = 0; u < 4; ++u) {
+                const bool on = s0 + u < tot;
+                const unsigned m = __ballot_sync(0xffffffffu, on);
+                const int64_t w = pos + __popc(m & lt);
+                pos += __popc(m);
+                lc[u] = on ? (int)__ldg(lcol + w) : 0;
+                h[u] = on ? (H)__ldg(tval + w) : H(0.0f);
+            }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const bool ok = e + u < a1[i];
-                    lc[u] = ok ? (int)__ldg(lcol + base + e + u) : 0;
-                    h[u] = ok ? (H)__ldg(tval + base + e + u) : H(0.0f);
+            for (int u = 0; u < 4; ++u) {
+                if (s0 + u == ca) {  // the lane's stream moves from row qa to row qb
+#pragma unroll
+                    for (int v = 0; v < CB; ++v) {
+                        accA[v] += cur[v];
+                        cur[v] = TX(0.0f);
+                    }
                 }
+                if (s0 + u < tot) {
+                    const TX* row = S + lc[u] * CB;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (e + u < a1[i]) {
+                    for (int c = 0; c < C; ++c) {
                         TX x[VEC];
-                        tload<TX, VEC>(S + lc[u] * CB + cofs[i], x);
+                        tload<TX, VEC>(row + tswz<C>(lc[u], c) * VEC, x);
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) acc[i][v] = tfma<TX>(h[u], x[v], acc[i][v]);
+                        for (int v = 0; v < VEC; ++v) cur[c * VEC + v] = tfma<TX>(h[u], x[v], cur[c * VEC + v]);
                     }
                 }
             }
+        }
+        if (ca < send) {
+#pragma unroll
+            for (int v = 0; v < CB; ++v) accB[v] += cur[v];
+        } else {
+#pragma unroll
+            for (int v = 0; v < CB; ++v) accA[v] += cur[v];
         }
         __syncthreads();  // every thread is done with buffer k & 1
     }
     twait<0>();
 #pragma unroll
-    for (int i = 0; i < IPT; ++i)
-        if (qrow[i] >= 0) tstore<TX, VEC>(W + (r0 + qrow[i]) * b + c0 + cofs[i], acc[i]);
+    for (int c = 0; c < C; ++c) {
+        TX oa[VEC], ob[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            oa[v] = accA[c * VEC + v];
+            ob[v] = accB[c * VEC + v];
+        }
+        if (qa < rows) tstore<TX, VEC>(W + (r0 + qa) * b + c0 + c * VEC, oa);
+        if (qb < rows) tstore<TX, VEC>(W + (r0 + qb) * b + c0 + c * VEC, ob);
+    }
 }
 
 constexpr size_t kTiledSmemMax = 200 * 1024;
 
-template <typename TM, typename TX, int CB, int IPT>
+template <typename TM, typename TX, int CB>
 bbl_status launch_tiled_t(const bbl_matrix* A, int b, const TM* val, const TX* V, TX* W, cudaStream_t st) {
-    auto kern = tiled_spmm_kernel<TM, TX, CB, IPT>;
+    auto kern = tiled_spmm_kernel<TM, TX, CB>;
     static bool attr = false;
     if (!attr) {
         BBL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTiledSmemMax));
@@ -338,33 +391,26 @@ bbl_status launch_tiled_t(const bbl_matrix* A, int b, const TM* val, const TX* V
     const int T = A->tile;
     const size_t smem = 2 * (size_t)T * CB * sizeof(TX);
     dim3 grid((unsigned)A->t_nrb, (unsigned)(b / CB));
-    kern<<<grid, kTiledThreads, smem, st>>>(A->n, T, b, A->t_pair_ptr.as<int64_t>(), A->t_pair_tile.as<int>(),
-                                            A->t_pair_base.as<int64_t>(), A->t_off.as<unsigned short>(),
-                                            A->t_lcol.as<unsigned short>(), val, V, W);
+    const unsigned threads = 32u * (unsigned)ceil_div(T, 64);
+    kern<<<grid, threads, smem, st>>>(A->n, T, b, A->t_pair_ptr.as<int64_t>(), A->t_pair_tile.as<int>(),
+                                      A->t_pair_base.as<int64_t>(), A->t_off.as<unsigned short>(),
+                                      A->t_lcol.as<unsigned short>(), val, V, W);
     BBL_LAUNCH_CHECK();
     return BBL_OK;
 }
 
-template <typename TM, typename TX, int CB>
-bbl_status launch_tiled_cb(const bbl_matrix* A, int b, const TM* val, const TX* V, TX* W, int ipt, cudaStream_t st) {
-    if (ipt <= 1) return launch_tiled_t<TM, TX, CB, 1>(A, b, val, V, W, st);
-    if (ipt <= 2) return launch_tiled_t<TM, TX, CB, 2>(A, b, val, V, W, st);
-    if (ipt <= 4) return launch_tiled_t<TM, TX, CB, 4>(A, b, val, V, W, st);
-    return launch_tiled_t<TM, TX, CB, 8>(A, b, val, V, W, st);
-}
-
 // Column group: 32 bytes of a row (or 16 when b holds no 32-byte group),
-// at most 8 chunks per thread, two tiles within the shared-memory limit.
+// two tiles within the shared-memory limit.
 template <typename TM, typename TX>
 bbl_status tiled_typed(const bbl_matrix* A, int b, const TM* val, const TX* V, TX* W, cudaStream_t st) {
     constexpr int VEC = 16 / (int)sizeof(TX);
+    if (A->tile > 2 * kTiledMaxThreads)
+        return set_error(BBL_ERR_UNSUPPORTED, "spmm: tiled tile %d above %d rows", A->tile, 2 * kTiledMaxThreads);
     for (int CB = 2 * VEC; CB >= VEC; CB /= 2) {
         if (b % CB) continue;
-        const int64_t nch = (int64_t)A->tile * (CB / VEC);
-        const int64_t ipt = ceil_div(nch, kTiledThreads);
-        if (ipt > 8 || 2 * (size_t)A->tile * CB * sizeof(TX) > kTiledSmemMax) continue;
-        if (CB == 2 * VEC) return launch_tiled_cb<TM, TX, 2 * VEC>(A, b, val, V, W, (int)ipt, st);
-        return launch_tiled_cb<TM, TX, VEC>(A, b, val, V, W, (int)ipt, st);
+        if (2 * (size_t)A->tile * CB * sizeof(TX) > kTiledSmemMax) continue;
+        if (CB == 2 * VEC) return launch_tiled_t<TM, TX, 2 * VEC>(A, b, val, V, W, st);
+        return launch_tiled_t<TM, TX, VEC>(A, b, val, V, W, st);
     }
     return set_error(BBL_ERR_UNSUPPORTED,
                      "spmm: the tiled format needs b a multiple of %d and a tile of at most %lld rows", VEC,
@@ -456,7 +502,7 @@ bbl_status tiled_build_t(bbl_matrix* A, int T, cudaStream_t st) {
 }
 
 bbl_status tiled_build(bbl_matrix* A, int T, cudaStream_t st) {
-    if (T < 16 || T > 8192) return set_error(BBL_ERR_INVALID_ARG, "matrix_create: tile %d outside 16..8192", T);
+    if (T < 16 || T > 1024) return set_error(BBL_ERR_INVALID_ARG, "matrix_create: tile %d outside 16..1024", T);
     if (A->storage == BBL_FP64) return tiled_build_t<double>(A, T, st);
     return tiled_build_t<float>(A, T, st);
 }
