@@ -569,8 +569,9 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     // on with block j+1 (whose SpMM does not need it); the host checks the
     // result of T_j after enqueuing block j+1.  When T_j has converged, block
     // j+1 was speculative and is not used.
-    Timer tm;
-    BBL_TRY(tm.init());
+    Timer tms[2];  // block tb uses tms[tb & 1]: its times are read one block later
+    BBL_TRY(tms[0].init());
+    BBL_TRY(tms[1].init());
     // ritz_overlap = 0: the Ritz solve runs on the caller's stream right after
     // its block and is read at once (no speculative block, no concurrency)
     const bool serial = o.ritz_overlap == 0;
@@ -579,7 +580,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     else BBL_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
     struct SideGuard {
         cudaStream_t s;
-        cudaEvent_t e[6];
+        cudaEvent_t e[7];
         ~SideGuard() {
             if (s) {
                 cudaStreamSynchronize(s);
@@ -589,10 +590,11 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
                 if (x) cudaEventDestroy(x);
         }
     } guard{serial ? nullptr : side, {}};
-    for (int q = 0; q < 6; ++q) BBL_CUDA(cudaEventCreate(&guard.e[q]));
+    for (int q = 0; q < 7; ++q) BBL_CUDA(cudaEventCreate(&guard.e[q]));
     cudaEvent_t* ev_main = guard.e;       // [2] main-stream block done
     cudaEvent_t* ev_r0 = guard.e + 2;     // [2] Ritz start
     cudaEvent_t* ev_r1 = guard.e + 4;     // [2] Ritz done (report in host memory)
+    cudaEvent_t ev_defl = guard.e[6];     // deflation count of the last CholQR2 in host memory
     DevBuf theta2, S2, est2;
     BBL_TRY(theta2.alloc(sizeof(double) * 2 * 64));
     BBL_TRY(S2.alloc(sizeof(double) * 2 * (size_t)m_max * nev));
@@ -709,14 +711,30 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     int tb = 0;       // its index over all restarts (SpMM calls so far)
     int pending_t = -1;
     bool stop = false;
+    // W = H V_j is formed directly in the next basis slot (or Z when the
+    // basis is full) and turned into V_{j+1} there (Gram-Schmidt only reads
+    // blocks 0..j)
+    auto spmm_block = [&](int jj, Timer& t) -> bbl_status {
+        char* Wo = (jj + 1 < J_max) ? blockp(jj + 1) : Z.as<char>();
+        BBL_CUDA(cudaEventRecord(t.ev[0], st));
+        if (dtype == kDF32) return spmm_df32(A, b, blockp(jj), Wo, st);
+        return spmm_dispatch(A, b, blockp(jj), Wo, f64_spmm, st);
+    };
+    // waits for the deflation count of block tb's CholQR2 and adds its phase times
+    auto block_done = [&](Timer& t) -> bbl_status {
+        BBL_CUDA(cudaEventSynchronize(ev_defl));
+        out.t_spmm += t.ms(0, 1);
+        out.t_reorth += t.ms(1, 2);
+        out.t_chol += t.ms(2, 3);
+        out.t_gram += t.ms(4, 5);
+        return BBL_OK;
+    };
+    bool spmm_ahead = false;  // the current block's SpMM is already enqueued
     while (!stop) {
-        char* Vj = blockp(j);
+        Timer& tm = tms[tb & 1];
         char* Wn = (j + 1 < J_max) ? blockp(j + 1) : Z.as<char>();
-        BBL_CUDA(cudaEventRecord(tm.ev[0], st));
-        // W = H V_j is formed directly in the next basis slot and turned into
-        // V_{j+1} there (Gram-Schmidt only reads blocks 0..j)
-        if (dtype == kDF32) BBL_TRY(spmm_df32(A, b, Vj, Wn, st));
-        else BBL_TRY(spmm_dispatch(A, b, Vj, Wn, f64_spmm, st));
+        if (!spmm_ahead) BBL_TRY(spmm_block(j, tm));
+        spmm_ahead = false;
         // ritz_overlap = 2: the Gram-Schmidt passes wait for the Ritz solve in
         // flight, which then shares the GPU with this SpMM only (the wait is
         // counted in the SpMM phase)
@@ -750,11 +768,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         BBL_CUDA(cudaEventRecord(tm.ev[3], st));
         BBL_CUDA(cudaEventRecord(ev_main[tb & 1], st));
         BBL_CUDA(cudaMemcpyAsync(h_ndefl, d_ndefl, sizeof(int), cudaMemcpyDeviceToHost, st));
-        BBL_CUDA(cudaStreamSynchronize(st));
-        out.t_spmm += tm.ms(0, 1);
-        out.t_reorth += tm.ms(1, 2);
-        out.t_chol += tm.ms(2, 3);
-        out.t_gram += tm.ms(4, 5);
+        BBL_CUDA(cudaEventRecord(ev_defl, st));
         out.gram_bytes += half1 ? (double)n * (j + 1) * b * 2.0 + (double)n * b * 4.0
                                 : ((double)n * (j + 1) * b + (double)n * b) * (double)s;
         ++out.gram_calls;
@@ -785,6 +799,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             if (done) {
                 out.converged = true;
                 stop = true;
+                BBL_TRY(block_done(tm));
                 break;
             }
         }
@@ -792,11 +807,27 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             pending = j;
             pending_t = tb;
         }
-        if (last) break;
+        if (last) {
+            BBL_TRY(block_done(tm));
+            break;
+        }
+        // The next block's SpMM is enqueued before the host reads this
+        // block's deflation count, so that the GPU does not idle while the
+        // host decides; a deflation (rare) replaces columns of V_{j+1}, and
+        // the product is then formed again.
+        const bool ahead = !full;
+        if (ahead) {
+            BBL_TRY(shadow_block(j + 1));
+            BBL_TRY(spmm_block(j + 1, tms[(tb + 1) & 1]));
+        }
+        BBL_TRY(block_done(tm));
+        spmm_ahead = ahead;
         if (h_ndefl[0] > last_defl) {
             BBL_TRY(replace_deflated(j + 1, Wn, d_mask));
             last_defl = h_ndefl[0];
             if (exhausted) break;  // no direction left to extend the basis with
+            if (ahead) BBL_TRY(shadow_block(j + 1));
+            spmm_ahead = false;
         }
         if (full) {
             // the basis is full: this block's report decides between stopping
@@ -815,7 +846,6 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             ++tb;
             continue;
         }
-        BBL_TRY(shadow_block(j + 1));
         ++j;
         ++tb;
     }
@@ -833,12 +863,13 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     BBL_CUDA(cudaMemcpyAsync(theta_dev, theta2.as<double>() + 64 * slot, sizeof(double) * final_k,
                              cudaMemcpyDeviceToDevice, st));
     // Ritz vectors X = Q S (k columns) from the blocks of the returned T
-    BBL_CUDA(cudaEventRecord(tm.ev[0], st));
+    Timer& tf = tms[0];
+    BBL_CUDA(cudaEventRecord(tf.ev[0], st));
     BBL_TRY(ritz_vectors(n, b, final_j + 1, dtype, basis.p, final_k, S2.as<double>() + (size_t)slot * m_max * nev, X,
                          st));
-    BBL_CUDA(cudaEventRecord(tm.ev[1], st));
+    BBL_CUDA(cudaEventRecord(tf.ev[1], st));
     BBL_CUDA(cudaStreamSynchronize(st));
-    out.t_other += tm.ms(0, 1);
+    out.t_other += tf.ms(0, 1);
     return BBL_OK;
 }
 

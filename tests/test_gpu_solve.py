@@ -367,3 +367,31 @@ def test_workspace_cache_reuses_the_bases_across_calls_and_streams():
     np.testing.assert_allclose(r3.evals, r1.evals, rtol=1e-12)
     bbl.workspace_release()
     assert bbl.workspace_bytes() == 0
+
+
+@pytest.mark.parametrize("storage,overlap", [("fp64", None), ("fp64", 0), ("fp32", None)])
+def test_solve_through_a_deflation_matches_the_dense_spectrum(storage, overlap):
+    """H = diag(H1, H2), H1 the 6-point 1-D Laplacian and H2 the 200-point one
+    shifted by 1.  Pivot column 0 lives on H1 alone, so the block Krylov
+    space exhausts H1's 6-dimensional invariant subspace within a few blocks;
+    CholQR2 then deflates a column of W (Sec. II.A, the rank-deficient block)
+    and the solver replaces it with a fresh random direction, while the SpMM
+    of the next block is already enqueued (it is formed again after the
+    replacement).  The lowest 4 eigenvalues are those of the dense matrix."""
+    torch, bbl = need_gpu()
+    import scipy.sparse as sp
+    n1, n2 = 6, 200
+    L1 = synth.laplacian_1d(n1)
+    L2 = synth.laplacian_1d(n2)
+    a1 = sp.csr_matrix((L1.val, L1.col, L1.row_ptr), shape=(n1, n1))
+    a2 = sp.csr_matrix((L2.val, L2.col, L2.row_ptr), shape=(n2, n2)) + sp.identity(n2)
+    H = synth.csr_from_scipy(sp.block_diag([a1, a2]))
+    piv = OR.normal_block(11, H.n, 2)
+    piv[n1:, 0] = 0.0
+    ref = np.linalg.eigvalsh(sp.block_diag([a1, a2]).toarray())[:4]
+    opts = {} if overlap is None else {"ritz_overlap": overlap}
+    res = bbl.solve(bbl.Matrix(H, storage=storage, keep_fp64=(storage == "fp32")), 4, 2, pivot=piv, tol=1e-8,
+                    check_every=1, **opts)
+    assert res.converged
+    assert res.stats["deflations"] >= 1
+    _check_eigs(res, ref, H, 1e-8)
