@@ -466,7 +466,11 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        # FP32 storage, SpMM and Gram-Schmidt; FP16 products (FP32 sums) in
+        # the first Gram pass when it reads the FP16 copy of the basis; FP64
+        # coefficients, T, Ritz quotients and residuals
+        "dtype": "f32+f16+f64" if args.half_first_pass else "f32+f64", "data": "synthetic",
         "config": {"workload": workload_name(A),
                    "method": f"bootstrap trunc_dim={TRUNC} sub_tol={args.sub_tol:g}, FP32 stage "
                              f"({sched['fmt']}, lanes {sched['lanes']}, sigma {sched['sigma']}"
