@@ -327,6 +327,7 @@ def run_ours(args):
     solve_opts = {} if args.ritz_overlap is None else {"ritz_overlap": args.ritz_overlap}
     solve_opts["stage1_tol"] = args.stage1_tol
     solve_opts["half_first_pass"] = args.half_first_pass
+    solve_opts["fused_update_gram"] = args.fused_update_gram
 
     def step():
         b0 = torch.cuda.Event(enable_timing=True)
@@ -563,6 +564,12 @@ def run_kernels(args):
     Wt = torch.empty_like(Wr)
     t = timeit(lambda: bbl.block_reorth(basis, Wt.copy_(Wr), passes=1), args.reps)
     out["gram_update_fp32"] = {"ms": t, "GBs": (2 * n * m * 4 + 3 * n * B * 4) / t / 1e6}
+    # the fused first update + second Gram (tensor cores): one read of the basis
+    C1 = bbl.block_gram(basis, Wr)
+    Wf = torch.empty_like(Wr)
+    t = timeit(lambda: bbl.block_update_gram(basis, Wf.copy_(Wr), C1), args.reps)
+    out["update_gram_fused"] = {"ms": t, "GBs": (n * m * 4 + 3 * n * B * 4) / t / 1e6}
+    del Wf
     Wc = Wr.clone()
     t = timeit(lambda: bbl.cholqr2(Wc.copy_(Wr)), args.reps)
     out["cholqr2_fp32"] = {"ms": t, "GBs": 6 * n * B * 4 / t / 1e6}
@@ -963,6 +970,9 @@ def main():
     ap.add_argument("--sub-tol", type=float, default=SUB_TOL)
     ap.add_argument("--half-first-pass", type=int, default=HALF_FIRST_PASS,
                     help="1: the FP32 stage's first Gram-Schmidt pass reads the FP16 basis copy (library default)")
+    ap.add_argument("--fused-update-gram", type=int, default=0,
+                    help="1: the first update and the second Gram in one tensor-core kernel; 0 (library default, "
+                         "faster at n = 2e6): two FP32 kernels")
     ap.add_argument("--stage1-tol", type=float, default=STAGE1_TOL,
                     help="FP32 stage tolerance before the polish (the library's default is 2e-6; 3e-7 measured "
                          "fastest on kron_n2e6)")

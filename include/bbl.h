@@ -118,6 +118,14 @@ typedef struct {
                                    matrix stays block tridiagonal.              */
     int max_blocks;             /* with restart_keep: cap on the blocks (SpMM
                                    calls) of a stage; 0 (default) = 10000        */
+    int fused_update_gram;      /* FP32 blocks with b = 8 and at most 128 stored
+                                   blocks: 1 the first pass's update and the
+                                   second pass's Gram run as one kernel on the
+                                   tensor cores, reading the basis once
+                                   (bbl_block_update_gram); 0 (default): two
+                                   kernels on the FP32 pipes, which are faster
+                                   at n = 2e6 (the fused kernel's 16-row
+                                   chunks are latency-bound)                     */
 } bbl_options;
 
 typedef struct {
@@ -285,6 +293,28 @@ bbl_status bbl_block_gram(int64_t n, int b, int nblocks, bbl_dtype dtype, const 
  * below 2^-10 of |Q16|^T |W| entrywise.
  * Both pointers 16-byte aligned (BBL_ERR_INVALID_ARG otherwise).         */
 bbl_status bbl_block_gram_f16(int64_t n, int nblocks, const void* basis16, const float* W, double* C, void* stream);
+
+/* W -= Q C1, then C2 = Q^T W of the updated W, for b = 8 and FP32: the
+ * update of the first and the Gram of the second classical Gram-Schmidt
+ * pass of the full reorthogonalisation (Sec. II.A, Eqs. 7-8) in one read of
+ * the basis (bbl_options.fused_update_gram).
+ *   basis   device FP32, nblocks consecutive n x 8 row-major blocks,
+ *           1 <= nblocks <= 128 (BBL_ERR_UNSUPPORTED otherwise)
+ *   C1      device FP64 (nblocks*8) x 8 row-major (rounded to FP32 for the
+ *           products, as in the FP32 update)
+ *   W       device FP32 n x 8, updated in place
+ *   C2      device FP64 (nblocks*8) x 8 row-major, written
+ * Each CTA stages 16 rows of every block in shared memory and forms both
+ * products from them on the tensor cores (mma.sync m16n8k8 TF32, FP32
+ * accumulate), each FP32 operand split into a TF32 high part and remainder
+ * (three products per pair; error per product below 2^-21 of |a b|), except
+ * the update's products with the two newest blocks, which are FP32 FMAs
+ * (in Lanczos these carry the large coefficients A_j and B_{j-1}).  The
+ * update sums over the basis in FP32; the Gram sums a CTA's rows in FP32 and
+ * the CTAs in FP64.  basis and W 16-byte aligned (BBL_ERR_INVALID_ARG
+ * otherwise).  The call allocates its workspace and synchronises `stream`. */
+bbl_status bbl_block_update_gram(int64_t n, int nblocks, const float* basis, const double* C1, float* W, double* C2,
+                                 void* stream);
 
 /* Allocation-free variant of bbl_block_gram (no counterpart in the paper).
  * For callers that must not allocate device memory: e.g. a process whose

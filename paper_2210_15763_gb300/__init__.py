@@ -271,6 +271,19 @@ def block_gram_f16(basis16, W, stream=None):
     return C_
 
 
+def block_update_gram(basis, W, C1, stream=None):
+    """W -= Q C1 in place, then C2 = Q^T W (FP64 m x 8), in one kernel
+    (FP32 basis of n x 8 blocks, at most 128 blocks)."""
+    torch = _torch()
+    nb, n, b = basis.shape
+    if b != 8 or basis.dtype != torch.float32 or W.dtype != torch.float32 or C1.dtype != torch.float64:
+        raise ValueError("block_update_gram: FP32 basis of n x 8 blocks, FP32 W, FP64 C1")
+    C2 = torch.empty((nb * 8, 8), dtype=torch.float64, device=W.device)
+    _lib.check(_lib.load().bbl_block_update_gram(n, nb, _ptr(basis), _ptr(C1.contiguous()), _ptr(W), _ptr(C2),
+                                                 _stream(stream)))
+    return C2
+
+
 def pivot_rr_residual(A: Matrix, P, stream=None):
     """Rayleigh-Ritz values and residual norms of span(P) (the test that chooses a pivot)."""
     b = P.shape[1]

@@ -218,6 +218,7 @@ void bbl_options_default(bbl_options* o) {
     o->check_every = 0;
     o->ritz_overlap = 1;
     o->half_first_pass = 1;
+    o->fused_update_gram = 0;
     o->stream = nullptr;
 }
 

@@ -682,7 +682,7 @@ template <typename T, int B>
 bbl_status launch_syrk(int64_t n, const T* W, double* G, DevBuf& partials, cudaStream_t st) {
     const int grid = (int)std::min<int64_t>(152 * 4, std::max<int64_t>(1, ceil_div(n, kThreads)));
     const size_t need = sizeof(double) * (size_t)grid * B * B;
-    if (partials.bytes < need) BBL_TRY(partials.alloc(need));
+    BBL_TRY(partials.grow(need));
     syrk_kernel<T, B><<<grid, kThreads, 0, st>>>(n, W, partials.as<double>());
     BBL_LAUNCH_CHECK();
     launch_reduce((int64_t)B * B, grid, partials.as<double>(), G, st);
@@ -779,7 +779,7 @@ bbl_status launch_gram_rows(int64_t n, int m, const T* Q, const T* W, double* C,
     const int64_t per = (int64_t)m * B;
     const int64_t slots = workers * wpb;
     const size_t need = sizeof(double) * (size_t)(slots * per) + 256;
-    if (partials.bytes < need) BBL_TRY(partials.alloc(need));
+    BBL_TRY(partials.grow(need));
     int* ticket = reinterpret_cast<int*>(partials.as<char>() + sizeof(double) * (size_t)(slots * per));
     BBL_CUDA(cudaMemsetAsync(ticket, 0, sizeof(int), st));
     gram_rows_kernel<T, B><<<(unsigned)workers, kThreads, S::smem_bytes, st>>>(n, m, wpb, (int)rc, nch, Q, W,
@@ -942,7 +942,7 @@ bbl_status launch_gram_half(int64_t n, int m, const __half* Q, const float* W, d
     const int64_t workers = std::min<int64_t>(slots_max, nch);
     const int64_t per = (int64_t)m * 8;
     const size_t need = sizeof(double) * (size_t)(workers * per) + 256;
-    if (partials.bytes < need) BBL_TRY(partials.alloc(need));
+    BBL_TRY(partials.grow(need));
     int* ticket = reinterpret_cast<int*>(partials.as<char>() + sizeof(double) * (size_t)(workers * per));
     BBL_CUDA(cudaMemsetAsync(ticket, 0, sizeof(int), st));
     gram_half_kernel<<<(unsigned)workers, kThreads, 0, st>>>(n, m, nch, Q, W, partials.as<double>(), ticket);
@@ -964,7 +964,7 @@ bbl_status launch_gram(int64_t n, int m, const T* Q, const T* W, double* C, DevB
     const int64_t gy = gram_groups<CPT>(m);                   // one ticket per column group
     const size_t ticket_bytes = 256 * (size_t)ceil_div(gy * (int64_t)sizeof(int), 256);
     const size_t need = sizeof(double) * (size_t)cap + ticket_bytes;
-    if (partials.bytes < need) BBL_TRY(partials.alloc(need));
+    BBL_TRY(partials.grow(need));
     int* tickets = reinterpret_cast<int*>(partials.as<char>() + sizeof(double) * (size_t)cap);
     return gram_core<T, B, CPT>(n, m, Q, W, C, partials.as<double>(), cap, tickets,
                                 (int64_t)(ticket_bytes / sizeof(int)), st);
@@ -981,7 +981,7 @@ bbl_status launch_gram_generic(int64_t n, int m, int b, const T* Q, const T* W, 
     rpc = ceil_div(rpc, kRT) * kRT;
     const int64_t nch = std::max<int64_t>(1, ceil_div(n, rpc));
     const size_t need = sizeof(double) * (size_t)nch * m * b;
-    if (partials.bytes < need) BBL_TRY(partials.alloc(need));
+    BBL_TRY(partials.grow(need));
     const size_t smem = sizeof(double) * kThreads * kMaxB;
     static bool attr_set = false;
     if (!attr_set) {
@@ -1333,6 +1333,12 @@ __global__ void trmul_kernel(int b, const double* __restrict__ R2, const double*
 }  // namespace
 
 // -------------------------------------------------------------------- internal API
+void reduce_partials(int64_t count, int nparts, const double* partial, double* out, cudaStream_t st) {
+    launch_reduce(count, nparts, partial, out, st);
+}
+
+int gram_worker_sms() { return std::max(1, sm_count() - kRitzReserveSMs); }
+
 bbl_status gram(int64_t n, int b, int nblocks, int dtype, const void* Q, const void* W, double* C, DevBuf& partials,
                 cudaStream_t st) {
     const int m = nblocks * b;

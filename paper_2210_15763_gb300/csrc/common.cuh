@@ -81,6 +81,13 @@ struct DevBuf {
         p = nullptr;
         bytes = 0;
     }
+    // workspace growth: at least doubles, so that a buffer sized by a
+    // growing basis is reallocated (cudaFree synchronises the device) a
+    // logarithmic number of times
+    bbl_status grow(size_t need) {
+        if (bytes >= need) return BBL_OK;
+        return alloc(need > 2 * bytes ? need : 2 * bytes);
+    }
     bbl_status alloc(size_t nbytes) {
         release();
         if (nbytes == 0) nbytes = 16;
@@ -253,6 +260,16 @@ bbl_status gram_half(int64_t n, int nblocks, const void* Q16, const float* W, do
                      cudaStream_t st);
 // FP16 copy (round to nearest) of count FP32 values
 bbl_status to_half(int64_t count, const float* in, void* out, cudaStream_t st);
+// out[e] = sum over the nparts parts of partial[p * count + e], in a fixed order
+void reduce_partials(int64_t count, int nparts, const double* partial, double* out, cudaStream_t st);
+// SMs the persistent Gram kernels use (the rest stay free for the Ritz solve)
+int gram_worker_sms();
+// cgs.cu: W -= Q C1 (written over W) and C2 = Q^T W (the updated W) in one
+// read of the FP32 basis, on the tensor cores (b = 8, nblocks <=
+// 128: update_gram_tc_supports); work is grown as needed
+bool update_gram_tc_supports(int nblocks);
+bbl_status update_gram_tc(int64_t n, int nblocks, const float* Q, const double* C1, float* W, double* C2,
+                          DevBuf& work, cudaStream_t st);
 bbl_status ritz_vectors(int64_t n, int b, int nblocks, int dtype, const void* Q, int k, const double* S,
                         double* X, cudaStream_t st);
 bbl_status cholqr2_dev(int64_t n, int b, int dtype, void* W, double* B, double defl_abs2, int* d_ndefl,

@@ -443,6 +443,8 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     int J_max = std::max(1, o.max_vectors / b);
     // FP32 blocks, b = 8: the first Gram-Schmidt pass reads an FP16 copy of the basis
     const bool half1 = dtype == BBL_FP32 && b == 8 && o.half_first_pass != 0;
+    // FP32 blocks, b = 8: the first update and the second Gram share one read of the basis
+    const bool fuse_on = dtype == BBL_FP32 && b == 8 && o.fused_update_gram != 0;
     {
         size_t freeb = 0, totalb = 0;
         BBL_CUDA(cudaMemGetInfo(&freeb, &totalb));
@@ -742,6 +744,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         BBL_CUDA(cudaEventRecord(tm.ev[1], st));
         double* C1 = coeff.as<double>();
         double* C2 = C1 + (size_t)m_max * b;
+        const bool fused2 = fuse_on && update_gram_tc_supports(j + 1);
         BBL_CUDA(cudaEventRecord(tm.ev[4], st));
         if (dtype == kDF32) {
             df32_hi_kernel<<<cg, 256, 0, st>>>(n * b, reinterpret_cast<const df32*>(Wn), whi.as<float>());
@@ -753,8 +756,13 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             BBL_TRY(gram(n, b, j + 1, dtype, basis.p, Wn, C1, partials, st));
         }
         BBL_CUDA(cudaEventRecord(tm.ev[5], st));
-        BBL_TRY(update(n, b, j + 1, dtype, basis.p, C1, Wn, st));
-        BBL_TRY(gram(n, b, j + 1, dtype, basis.p, Wn, C2, partials, st));
+        if (fused2) {
+            // first update and second Gram in one read of the basis (tensor cores)
+            BBL_TRY(update_gram_tc(n, j + 1, basis.as<float>(), C1, reinterpret_cast<float*>(Wn), C2, partials, st));
+        } else {
+            BBL_TRY(update(n, b, j + 1, dtype, basis.p, C1, Wn, st));
+            BBL_TRY(gram(n, b, j + 1, dtype, basis.p, Wn, C2, partials, st));
+        }
         BBL_TRY(update(n, b, j + 1, dtype, basis.p, C2, Wn, st));
         // A_j = sym(C1 + C2)[j-block]: the second pass's own-block coefficients
         // are the rounding (or, from a cheaper first pass, the approximation)
@@ -777,8 +785,10 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             const double sx = (double)s;
             const double sv = (A->storage == BBL_FP64 || (dtype != kDF32 && f64_spmm && A->val64.p)) ? 8.0 : 4.0;
             out.spmm_bytes += spmm_alg_bytes(A, b, sv, sx);
-            // two passes of Gram + update; an FP16 first-pass Gram reads 2 bytes per basis element
-            out.reorth_bytes += (half1 ? 3.5 : 4.0) * (double)n * m * sx + 6.0 * (double)n * b * sx;
+            // two passes of Gram + update; an FP16 first-pass Gram reads 2 bytes per basis
+            // element, and the fused first update + second Gram reads the basis once
+            out.reorth_bytes += ((half1 ? 0.5 : 1.0) + (fused2 ? 2.0 : 3.0)) * (double)n * m * sx +
+                                6.0 * (double)n * b * sx;
         }
         out.spmm_calls = tb + 1;
         const bool full = (j == J_max - 1);
@@ -1068,6 +1078,24 @@ extern "C" bbl_status bbl_block_gram_f16(int64_t n, int nblocks, const void* bas
     cudaStream_t st = as_stream(stream);
     DevBuf partials;
     BBL_TRY(gram_half(n, nblocks, basis16, W, C, partials, st));
+    BBL_CUDA(cudaStreamSynchronize(st));
+    return BBL_OK;
+}
+
+// W -= Q C1, then C2 = Q^T W (the updated W), b = 8, FP32: the fused first
+// update and second Gram of the FP32 stage on its own.
+extern "C" bbl_status bbl_block_update_gram(int64_t n, int nblocks, const float* basis, const double* C1, float* W,
+                                            double* C2, void* stream) {
+    using namespace bbl;
+    if (n < 1 || nblocks < 1 || !basis || !C1 || !W || !C2)
+        return set_error(BBL_ERR_INVALID_ARG, "block_update_gram: bad arguments");
+    if (!aligned16(basis) || !aligned16(W))
+        return set_error(BBL_ERR_INVALID_ARG, "block_update_gram: pointers must be 16-byte aligned");
+    if (!update_gram_tc_supports(nblocks))
+        return set_error(BBL_ERR_UNSUPPORTED, "block_update_gram: %d blocks (at most 128)", nblocks);
+    cudaStream_t st = as_stream(stream);
+    DevBuf work;
+    BBL_TRY(update_gram_tc(n, nblocks, basis, C1, W, C2, work, st));
     BBL_CUDA(cudaStreamSynchronize(st));
     return BBL_OK;
 }

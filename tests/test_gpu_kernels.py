@@ -192,6 +192,109 @@ def test_fp16_first_pass_keeps_the_fp32_stage_and_the_result():
     np.testing.assert_allclose(p1.evals, p0.evals, rtol=1e-11)
 
 
+def _split_bound(K):
+    """Entrywise bound, relative to sum_k |a_k| |b_k|, of a sum of K products
+    formed on the tensor cores from exact three-part BF16 splits of FP32
+    operands (six of the nine partial products, dropping at most 2^-23 of
+    |a b| each; bounded here by 2^-22) and accumulated in FP32 (K additions,
+    each allowed a full FP32 ulp)."""
+    return 2.0 ** -22 + 2 * K * EPS32
+
+
+@pytest.mark.parametrize("n,nb", [(5, 1), (16, 2), (37, 3), (40, 4), (1000, 7), (20_011, 50), (100_003, 99),
+                                  (4096, 128), (70_001, 127)])
+def test_block_update_gram_matches_fp64_products(n, nb):
+    """The fused first update and second Gram (b = 8, tensor cores):
+    W1 = W - Q C1 against the FP64 product of the same FP32 basis and of C1
+    rounded to FP32, and C2 = Q^T W1 against the FP64 product with the
+    kernel's own W1.  The sizes cover fewer rows than one 16-row chunk, an
+    exact chunk, ragged last chunks, one and two blocks (no tensor-core
+    update; the two newest blocks are FMA products), odd block counts (the
+    last block pair of the Gram, or of the tensor-core update, has one
+    block) and the largest supported basis (128 blocks)."""
+    torch, bbl = need_gpu()
+    rng = np.random.default_rng(7 * n + nb)
+    Q = (rng.standard_normal((nb, n, 8)) / np.sqrt(n)).astype(np.float32)
+    W = rng.standard_normal((n, 8)).astype(np.float32)
+    C1 = rng.standard_normal((nb * 8, 8))
+    Qd = torch.from_numpy(Q).cuda()
+    Wd = torch.from_numpy(W).cuda()
+    C2 = bbl.block_update_gram(Qd, Wd, torch.from_numpy(C1).cuda()).cpu().numpy()
+    W1 = Wd.cpu().numpy().astype(np.float64)
+    Qf = Q.astype(np.float64)
+    C1f = C1.astype(np.float32).astype(np.float64)
+    Qcat = np.concatenate(list(Qf), axis=1)          # n x m, column 8j + c = block j column c
+    ref1 = W.astype(np.float64) - Qcat @ C1f
+    S1 = np.abs(Qcat) @ np.abs(C1f)
+    m = nb * 8
+    assert np.all(np.abs(W1 - ref1) <= _split_bound(m) * S1 + EPS32 * np.abs(ref1))
+    ref2 = Qcat.T @ W1
+    S2 = np.abs(Qcat).T @ np.abs(W1)
+    assert np.all(np.abs(C2 - ref2) <= _split_bound(n) * S2)
+    # typical error far below the worst case: a misplaced fragment would show here
+    assert np.abs(C2 - ref2).max() <= 1e-5 * S2.max()
+    assert np.abs(W1 - ref1).max() <= 1e-5 * S1.max()
+
+
+def test_block_update_gram_zero_coefficients_leave_w_exact():
+    """C1 = 0: the update subtracts exact zeros (W unchanged bit for bit) and
+    C2 is the Gram Q^T W."""
+    torch, bbl = need_gpu()
+    rng = np.random.default_rng(3)
+    n, nb = 3001, 9
+    Q = rng.standard_normal((nb, n, 8)).astype(np.float32)
+    W = rng.standard_normal((n, 8)).astype(np.float32)
+    Wd = torch.from_numpy(W).cuda()
+    C2 = bbl.block_update_gram(torch.from_numpy(Q).cuda(), Wd, torch.zeros((nb * 8, 8), dtype=torch.float64,
+                                                                             device="cuda")).cpu().numpy()
+    assert np.array_equal(Wd.cpu().numpy(), W)
+    Qcat = np.concatenate(list(Q.astype(np.float64)), axis=1)
+    ref = Qcat.T @ W.astype(np.float64)
+    assert np.all(np.abs(C2 - ref) <= _split_bound(n) * (np.abs(Qcat).T @ np.abs(W.astype(np.float64))))
+
+
+def test_block_update_gram_on_an_orthonormal_basis_removes_the_projection():
+    """Orthonormal basis and C1 = Q^T W (the FP32 Gram): W1 = W - Q C1 is
+    orthogonal to the basis up to FP32 rounding, and C2 = Q^T W1 is that
+    rounding-sized remainder, as the second classical pass expects."""
+    torch, bbl = need_gpu()
+    rng = np.random.default_rng(5)
+    n, nb = 50_001, 40
+    Qo, _ = np.linalg.qr(rng.standard_normal((n, nb * 8)))
+    Q = np.stack([Qo[:, 8 * j:8 * j + 8] for j in range(nb)]).astype(np.float32)
+    W = rng.standard_normal((n, 8)).astype(np.float32)
+    Qd = torch.from_numpy(Q).cuda()
+    C1 = bbl.block_gram(Qd, torch.from_numpy(W).cuda())
+    Wd = torch.from_numpy(W).cuda()
+    C2 = bbl.block_update_gram(Qd, Wd, C1).cpu().numpy()
+    W1 = Wd.cpu().numpy().astype(np.float64)
+    Qcat = np.concatenate(list(Q.astype(np.float64)), axis=1)
+    ref1 = W.astype(np.float64) - Qcat @ C1.cpu().numpy().astype(np.float32).astype(np.float64)
+    scale = np.abs(W).max()
+    assert np.abs(W1 - ref1).max() <= 1e-6 * scale
+    assert np.abs(Qcat.T @ W1).max() <= 1e-5 * scale
+    np.testing.assert_allclose(C2, Qcat.T @ W1, atol=1e-6 * scale)
+
+
+def test_fused_update_gram_keeps_the_fp32_stage_and_the_result():
+    """The FP32 stage with the fused first update + second Gram and
+    with the two FP32-pipe kernels reach the same eigenvalues; after the
+    polish both agree to the FP64 level."""
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4", scale=0.6)
+    M = bbl.Matrix(H, storage="fp32")
+    piv = OR.normal_block(9, H.n, 8)
+    r1 = bbl.solve(M, 8, 8, pivot=piv, tol=2e-6, polish=0, max_vectors=800, fused_update_gram=1)
+    r0 = bbl.solve(M, 8, 8, pivot=piv, tol=2e-6, polish=0, max_vectors=800, fused_update_gram=0)
+    assert r1.converged and r0.converged
+    assert abs(r1.stats["iters"] - r0.stats["iters"]) <= 2
+    np.testing.assert_allclose(r1.evals, r0.evals, rtol=2e-6)
+    p1 = bbl.solve(M, 8, 8, pivot=piv, tol=1e-9, max_vectors=800, fused_update_gram=1)
+    p0 = bbl.solve(M, 8, 8, pivot=piv, tol=1e-9, max_vectors=800, fused_update_gram=0)
+    assert p1.converged and p0.converged
+    np.testing.assert_allclose(p1.evals, p0.evals, rtol=1e-11)
+
+
 @pytest.mark.parametrize("dtype", ["fp64", "fp32"])
 @pytest.mark.parametrize("b", [1, 2, 4, 6, 8, 16])
 def test_cholqr2_matches_oracle(dtype, b):
