@@ -29,7 +29,9 @@
 //  * Gram: M = 16 basis columns (a pair of blocks), N = 8, K = the chunk's
 //    16 rows (k = 2t, 2t+1, 2t+8, 2t+9 read rows t, t+4, t+8, t+12, the same
 //    order for W1); each warp keeps its pairs' 16 x 8 sums in registers over
-//    every chunk its CTA takes, and the CTAs' sums are added in FP64.
+//    every chunk its CTA takes (a chunk's products are formed from zero and
+//    added to the running sum in FP32, so the accumulation's rounding is
+//    that of plain FP32 additions), and the CTAs' sums are added in FP64.
 // Every shared-memory access pattern above is free of bank conflicts.
 #include <cuda_bf16.h>
 
@@ -260,7 +262,12 @@ __global__ void __launch_bounds__(kFuThreads, 1) cgs_update_gram_kernel(int64_t 
                 bf16x3_split(T1[0], T1[32], a[0][1], a[1][1], a[2][1]);
                 bf16x3_split(T0[64], T0[96], a[0][2], a[1][2], a[2][2]);
                 bf16x3_split(T1[64], T1[96], a[0][3], a[1][3], a[2][3]);
-                mma_bf16x3(acc[i], a, bw);
+                // the chunk's products from zero (the tensor cores' FP32 accumulation
+                // truncates), then one rounded FP32 addition to the running sum
+                float d[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_bf16x3(d, a, bw);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc[i][r] += d[r];
             }
         }
         __syncthreads();  // stage s is read; the next ticket's chunk may land in it
