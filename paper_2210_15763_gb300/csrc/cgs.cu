@@ -45,7 +45,7 @@ constexpr int kFuWarps = 16;
 constexpr int kFuThreads = 32 * kFuWarps;
 constexpr int kFuMaxPairsPerWarp = 4;                // register sums per warp
 constexpr int kFuMaxBlocks = 2 * kFuWarps * kFuMaxPairsPerWarp;  // 128 blocks = 1024 columns
-constexpr int kFuMaxStages = 4;
+constexpr int kFuMaxStages = 5;
 constexpr size_t kFuSmemLimit = 220 * 1024;
 
 // two FP32 values rounded to BF16 (nearest even), packed: lo in bits 0-15
@@ -122,171 +122,195 @@ __global__ void cgs_split_c1_kernel(int nblocks, const double* __restrict__ C1, 
     fb[e] = make_uint2(b0[2], b1[2]);
 }
 
-// Shared memory: [update B fragments: tc pairs x 768 B][stages x (the
-// chunk's rows of every block, nblocks x 512 B, then W's rows, 512 B)][warp
-// partials of the update: kFuWarps x 512 B][W1's rows: 512 B][C1's rows of
-// the two newest blocks in FP32: 512 B].
-__host__ __device__ inline size_t fu_frag_bytes(int nblocks) { return (size_t)fu_tc_pairs(nblocks) * 768; }
+// Named barriers of the two warp groups (id 0 is __syncthreads): the update
+// group's own barrier, "W1 of chunk i is ready" (ids 2, 3 by the parity of
+// i) and "the Gram group is done with chunk i" (ids 4, 5).  A group never
+// arrives twice at one id before the other group has passed it: the next
+// arrival at the same id is two chunks later, and each group's chunk i + 2
+// waits for the other group's chunk i.
+__device__ __forceinline__ void fu_bar_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fu_bar_arrive(int id, int count) {
+    asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(count) : "memory");
+}
+constexpr int kFuGroupWarps = kFuWarps / 2;          // warps per group
+constexpr int kFuGroupThreads = 32 * kFuGroupWarps;
+
+// Shared memory: [stages x (the chunk's rows of every block, nblocks x 512
+// B, then W's rows, 512 B)][update partials: kFuGroupWarps x 512 B][W1's
+// rows, two buffers: 1024 B][C1's rows of the two newest blocks in FP32:
+// 512 B].  The update's B fragments are read through the L1 cache.
 __host__ __device__ inline size_t fu_stage_bytes(int nblocks) { return (size_t)nblocks * 512 + 512; }
 inline size_t fu_smem_bytes(int nblocks, int stages) {
-    return fu_frag_bytes(nblocks) + (size_t)stages * fu_stage_bytes(nblocks) + (size_t)kFuWarps * 512 + 1024;
+    return (size_t)stages * fu_stage_bytes(nblocks) + (size_t)kFuGroupWarps * 512 + 1536;
 }
 
-// Persistent CTAs take 16-row chunks from a ticket counter, `stages` chunks
-// staged ahead (a CTA that starts late, e.g. behind a Ritz solve on another
-// stream, simply takes fewer chunks).
+// Persistent CTAs take the 16-row chunks blockIdx.x, blockIdx.x + gridDim.x,
+// ...; `stages` >= 3 shared-memory stages hold the chunks in flight.  Warps
+// 0-7 (the update group) copy the chunks in, form W1 = W - Q C1 of chunk i
+// and hand it over; warps 8-15 (the Gram group) meanwhile form chunk i - 1's
+// contribution to Q^T W1.  A stage is refilled (with chunk i - 2 + stages)
+// once both groups are done with its chunk i - 2.
 __global__ void __launch_bounds__(kFuThreads, 1) cgs_update_gram_kernel(int64_t n, int nblocks, int64_t nchunks,
                                                                      int stages, const float* __restrict__ Q,
                                                                      const double* __restrict__ C1,
-                                                                     const uint4* __restrict__ c1fa,
-                                                                     const uint2* __restrict__ c1fb,
+                                                                     const uint4* __restrict__ fa,
+                                                                     const uint2* __restrict__ fb,
                                                                      float* __restrict__ W,
-                                                                     double* __restrict__ partial,
-                                                                     int* __restrict__ ticket) {
+                                                                     double* __restrict__ partial) {
     extern __shared__ __align__(16) unsigned char fu_smem[];
     const int nt = fu_tc_blocks(nblocks), ne = nblocks - nt;  // tensor-core blocks, FMA blocks
     const int ntp = fu_tc_pairs(nblocks);
-    uint4* fa = reinterpret_cast<uint4*>(fu_smem);
-    uint2* fb = reinterpret_cast<uint2*>(fu_smem + (size_t)ntp * 512);
     const size_t sb = fu_stage_bytes(nblocks);
-    unsigned char* stage0 = fu_smem + fu_frag_bytes(nblocks);
-    float* red = reinterpret_cast<float*>(stage0 + (size_t)stages * sb);  // [kFuWarps][16][8]
-    float* W1s = red + kFuWarps * 128;                                      // [16][8]
-    float* c1x = W1s + 128;  // [8 ne][8]: C1's rows of the ne newest blocks, FP32
+    unsigned char* stage0 = fu_smem;
+    float* red = reinterpret_cast<float*>(stage0 + (size_t)stages * sb);  // [kFuGroupWarps][16][8]
+    float* W1s = red + kFuGroupWarps * 128;                                 // [2][16][8]
+    float* c1x = W1s + 256;  // [8 ne][8]: C1's rows of the ne newest blocks, FP32
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
-    const int npairs = (nblocks + 1) >> 1;
-    __shared__ int s_chunk[kFuMaxStages];  // chunk held by each stage
-    __shared__ int s_next;
+    const int64_t G = gridDim.x;
 
-    for (int e = threadIdx.x; e < ntp * 32; e += kFuThreads) {
-        fa[e] = __ldg(c1fa + e);
-        fb[e] = __ldg(c1fb + e);
-    }
     for (int e = threadIdx.x; e < ne * 64; e += kFuThreads) c1x[e] = (float)C1[(int64_t)nt * 64 + e];
-
-    // 16-byte piece `lane` (row lane / 2, half lane % 2) of the chunk's rows
-    // of blocks warp, warp + kFuWarps, ...; the last warp also copies W's.
-    const int pr = lane >> 1, ph = lane & 1;
-    auto stage_chunk = [&](int64_t c, int s) {
-        if (c < nchunks) {
-            const int64_t row = c * kFuRows + pr;
-            const bool ok = row < n;
-            float* dst = reinterpret_cast<float*>(stage0 + (size_t)s * sb) + warp * 128 + lane * 4;
-            const float* src = Q + ((int64_t)warp * n + row) * 8 + ph * 4;
-            const int64_t step = (int64_t)kFuWarps * n * 8;
-            for (int j = warp; j < nblocks; j += kFuWarps, src += step, dst += kFuWarps * 128)
-                fu_cp16(dst, ok ? (const void*)src : (const void*)Q, ok ? 16 : 0);
-            if (warp == kFuWarps - 1) {
-                float* wd = reinterpret_cast<float*>(stage0 + (size_t)s * sb) + nblocks * 128 + lane * 4;
-                fu_cp16(wd, ok ? (const void*)(W + row * 8 + ph * 4) : (const void*)W, ok ? 16 : 0);
-            }
-        }
-        fu_commit();
-    };
-
-    float acc[kFuMaxPairsPerWarp][4];
-#pragma unroll
-    for (int i = 0; i < kFuMaxPairsPerWarp; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-
-    if (threadIdx.x == 0)
-        for (int q = 0; q < stages; ++q) s_chunk[q] = atomicAdd(ticket, 1);
     __syncthreads();
-    for (int q = 0; q < stages; ++q) stage_chunk(s_chunk[q], q);
-    for (int s = 0;; s = (s + 1 == stages) ? 0 : s + 1) {
-        fu_wait(stages - 1);
-        __syncthreads();
-        const int64_t c = s_chunk[s];
-        if (c >= nchunks) break;  // tickets only grow: every later stage is empty too
-        const float* Qs = reinterpret_cast<const float*>(stage0 + (size_t)s * sb);
-        const float* Ws = Qs + nblocks * 128;
-        const int64_t r0 = c * kFuRows;
-        // update: tensor-core pairs warp, warp + kFuWarps, ..., two chains
-        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
-        auto upd = [&](int q, float (&d)[4]) {
-            // A: rows g / g + 8, k = 2t, 2t + 1 of block 2q (a0, a1) and of block 2q + 1 (a2, a3)
-            const float* T0 = Qs + (2 * q) * 128 + g * 8 + 2 * t;
-            const float2 x0 = *reinterpret_cast<const float2*>(T0);
-            const float2 x1 = *reinterpret_cast<const float2*>(T0 + 64);
-            const float2 x2 = *reinterpret_cast<const float2*>(T0 + 128);
-            const float2 x3 = *reinterpret_cast<const float2*>(T0 + 192);
-            unsigned a[3][4];
-            bf16x3_split(x0.x, x0.y, a[0][0], a[1][0], a[2][0]);
-            bf16x3_split(x1.x, x1.y, a[0][1], a[1][1], a[2][1]);
-            bf16x3_split(x2.x, x2.y, a[0][2], a[1][2], a[2][2]);
-            bf16x3_split(x3.x, x3.y, a[0][3], a[1][3], a[2][3]);
-            const uint4 f = fa[q * 32 + lane];
-            const uint2 f3 = fb[q * 32 + lane];
-            const unsigned b[3][2] = {{f.x, f.y}, {f.z, f.w}, {f3.x, f3.y}};
-            mma_bf16x3(d, a, b);
-        };
-        int q = warp;
-        for (; q + kFuWarps < ntp; q += 2 * kFuWarps) {
-            upd(q, d0);
-            upd(q + kFuWarps, d1);
-        }
-        if (q < ntp) upd(q, d0);
-        float* rw = red + warp * 128;
-        *reinterpret_cast<float2*>(rw + g * 8 + 2 * t) = make_float2(d0[0] + d1[0], d0[1] + d1[1]);
-        *reinterpret_cast<float2*>(rw + (g + 8) * 8 + 2 * t) = make_float2(d0[2] + d1[2], d0[3] + d1[3]);
-        __syncthreads();
-        if (threadIdx.x == kFuThreads - 1) s_next = atomicAdd(ticket, 1);  // the chunk to stage next
-        if (threadIdx.x < 128) {
-            const int e = threadIdx.x;  // 16 rows x 8 columns
-            const int r = e >> 3, col = e & 7;
-            float x = Ws[e];
-            for (int cc = 0; cc < 8 * ne; ++cc)
-                x = fmaf(-Qs[(nt + (cc >> 3)) * 128 + r * 8 + (cc & 7)], c1x[cc * 8 + col], x);
-            float sum = red[e];
-#pragma unroll
-            for (int w = 1; w < kFuWarps; ++w) sum += red[w * 128 + e];
-            const float w1 = x - sum;
-            W1s[e] = w1;
-            if (r0 + r < n) W[r0 * 8 + e] = w1;
-        }
-        __syncthreads();
-        // Gram: B = W1 (k = 2t, 2t + 1 -> rows t, t + 4; k = 2t + 8, 2t + 9 -> rows t + 8, t + 12), split
-        unsigned bw[3][2];
-        bf16x3_split(W1s[t * 8 + g], W1s[(t + 4) * 8 + g], bw[0][0], bw[1][0], bw[2][0]);
-        bf16x3_split(W1s[(t + 8) * 8 + g], W1s[(t + 12) * 8 + g], bw[0][1], bw[1][1], bw[2][1]);
-#pragma unroll
-        for (int i = 0; i < kFuMaxPairsPerWarp; ++i) {
-            const int p = warp + kFuWarps * i;
-            if (p < npairs) {
-                // A = [Q_2p Q_2p+1]^T: row = column of the pair (g: block 2p, g + 8: block
-                // 2p + 1; for an odd last pair the second block's rows are unused)
-                const float* T0 = Qs + (2 * p) * 128 + t * 8 + g;
-                const float* T1 = T0 + 128;
-                unsigned a[3][4];
-                bf16x3_split(T0[0], T0[32], a[0][0], a[1][0], a[2][0]);
-                bf16x3_split(T1[0], T1[32], a[0][1], a[1][1], a[2][1]);
-                bf16x3_split(T0[64], T0[96], a[0][2], a[1][2], a[2][2]);
-                bf16x3_split(T1[64], T1[96], a[0][3], a[1][3], a[2][3]);
-                // the chunk's products from zero (the tensor cores' FP32 accumulation
-                // truncates), then one rounded FP32 addition to the running sum
-                float d[4] = {0.f, 0.f, 0.f, 0.f};
-                mma_bf16x3(d, a, bw);
-#pragma unroll
-                for (int r = 0; r < 4; ++r) acc[i][r] += d[r];
+
+    if (warp < kFuGroupWarps) {
+        // ---------------- update group
+        const int uw = warp;
+        // 16-byte piece `lane` (row lane / 2, half lane % 2) of the chunk's
+        // rows of blocks uw, uw + 8, ...; the last warp also copies W's.
+        const int pr = lane >> 1, ph = lane & 1;
+        auto stage_chunk = [&](int64_t c, int s) {
+            if (c < nchunks) {
+                const int64_t row = c * kFuRows + pr;
+                const bool ok = row < n;
+                float* dst = reinterpret_cast<float*>(stage0 + (size_t)s * sb) + uw * 128 + lane * 4;
+                const float* src = Q + ((int64_t)uw * n + row) * 8 + ph * 4;
+                const int64_t step = (int64_t)kFuGroupWarps * n * 8;
+                for (int j = uw; j < nblocks; j += kFuGroupWarps, src += step, dst += kFuGroupWarps * 128)
+                    fu_cp16(dst, ok ? (const void*)src : (const void*)Q, ok ? 16 : 0);
+                if (uw == kFuGroupWarps - 1) {
+                    float* wd = reinterpret_cast<float*>(stage0 + (size_t)s * sb) + nblocks * 128 + lane * 4;
+                    fu_cp16(wd, ok ? (const void*)(W + row * 8 + ph * 4) : (const void*)W, ok ? 16 : 0);
+                }
             }
-        }
-        __syncthreads();  // stage s is read; the next ticket's chunk may land in it
-        const int cn = s_next;
-        if (threadIdx.x == 0) s_chunk[s] = cn;  // read again only after the next barrier
-        stage_chunk(cn, s);
-    }
-    fu_wait(0);
-    // this CTA's sums -> its FP64 slot (row-major m x 8)
-    double* part = partial + (int64_t)blockIdx.x * nblocks * 64;
+            fu_commit();
+        };
+        for (int q = 0; q < stages; ++q) stage_chunk(blockIdx.x + q * G, q);
+        int i = 0;
+        for (int64_t c = blockIdx.x; c < nchunks; c += G, ++i) {
+            const int s = i % stages;
+            if (i >= 2) {
+                // the Gram group is done with chunk i - 2: its stage takes chunk i - 2 + stages
+                fu_bar_sync(4 + (i & 1), kFuThreads);
+                stage_chunk(c + (int64_t)(stages - 2) * G, (i - 2) % stages);
+            }
+            // copy group k holds chunk k; at most stages - 2 later groups may be in flight
+            fu_wait(stages - 2);
+            fu_bar_sync(1, kFuGroupThreads);  // every piece of chunk i has landed
+            const float* Qs = reinterpret_cast<const float*>(stage0 + (size_t)s * sb);
+            const float* Ws = Qs + nblocks * 128;
+            const int64_t r0 = c * kFuRows;
+            float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+            auto upd = [&](int q, float (&d)[4]) {
+                // A: rows g / g + 8, k = 2t, 2t + 1 of block 2q (a0, a1) and of block 2q + 1 (a2, a3)
+                const float* T0 = Qs + (2 * q) * 128 + g * 8 + 2 * t;
+                const float2 x0 = *reinterpret_cast<const float2*>(T0);
+                const float2 x1 = *reinterpret_cast<const float2*>(T0 + 64);
+                const float2 x2 = *reinterpret_cast<const float2*>(T0 + 128);
+                const float2 x3 = *reinterpret_cast<const float2*>(T0 + 192);
+                unsigned a[3][4];
+                bf16x3_split(x0.x, x0.y, a[0][0], a[1][0], a[2][0]);
+                bf16x3_split(x1.x, x1.y, a[0][1], a[1][1], a[2][1]);
+                bf16x3_split(x2.x, x2.y, a[0][2], a[1][2], a[2][2]);
+                bf16x3_split(x3.x, x3.y, a[0][3], a[1][3], a[2][3]);
+                const uint4 f = __ldg(fa + q * 32 + lane);
+                const uint2 f3 = __ldg(fb + q * 32 + lane);
+                const unsigned b[3][2] = {{f.x, f.y}, {f.z, f.w}, {f3.x, f3.y}};
+                mma_bf16x3(d, a, b);
+            };
+            int q = uw;
+            for (; q + kFuGroupWarps < ntp; q += 2 * kFuGroupWarps) {
+                upd(q, d0);
+                upd(q + kFuGroupWarps, d1);
+            }
+            if (q < ntp) upd(q, d0);
+            float* rw = red + uw * 128;
+            *reinterpret_cast<float2*>(rw + g * 8 + 2 * t) = make_float2(d0[0] + d1[0], d0[1] + d1[1]);
+            *reinterpret_cast<float2*>(rw + (g + 8) * 8 + 2 * t) = make_float2(d0[2] + d1[2], d0[3] + d1[3]);
+            fu_bar_sync(1, kFuGroupThreads);
+            if (threadIdx.x < 128) {
+                const int e = threadIdx.x;  // 16 rows x 8 columns
+                const int r = e >> 3, col = e & 7;
+                float x = Ws[e];
+                for (int cc = 0; cc < 8 * ne; ++cc)
+                    x = fmaf(-Qs[(nt + (cc >> 3)) * 128 + r * 8 + (cc & 7)], c1x[cc * 8 + col], x);
+                float sum = red[e];
 #pragma unroll
-    for (int i = 0; i < kFuMaxPairsPerWarp; ++i) {
-        const int p = warp + kFuWarps * i;
-        if (p < npairs) {
-            part[((2 * p) * 8 + g) * 8 + 2 * t] = (double)acc[i][0];
-            part[((2 * p) * 8 + g) * 8 + 2 * t + 1] = (double)acc[i][1];
-            if (2 * p + 1 < nblocks) {
-                part[((2 * p + 1) * 8 + g) * 8 + 2 * t] = (double)acc[i][2];
-                part[((2 * p + 1) * 8 + g) * 8 + 2 * t + 1] = (double)acc[i][3];
+                for (int w = 1; w < kFuGroupWarps; ++w) sum += red[w * 128 + e];
+                const float w1 = x - sum;
+                W1s[(i & 1) * 128 + e] = w1;
+                if (r0 + r < n) W[r0 * 8 + e] = w1;
+            }
+            fu_bar_arrive(2 + (i & 1), kFuThreads);  // W1 of chunk i is ready
+        }
+        // the Gram group's last two chunks: their stages are not refilled, but
+        // the arrivals are matched so that no barrier is left half-passed
+        if (i >= 2) fu_bar_sync(4 + (i & 1), kFuThreads);
+        if (i >= 1) fu_bar_sync(4 + ((i + 1) & 1), kFuThreads);
+        fu_wait(0);
+    } else {
+        // ---------------- Gram group
+        const int gw = warp - kFuGroupWarps;
+        const int npairs = (nblocks + 1) >> 1;
+        float acc[2 * kFuMaxPairsPerWarp][4];
+#pragma unroll
+        for (int k = 0; k < 2 * kFuMaxPairsPerWarp; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.f;
+        int i = 0;
+        for (int64_t c = blockIdx.x; c < nchunks; c += G, ++i) {
+            const int s = i % stages;
+            fu_bar_sync(2 + (i & 1), kFuThreads);  // W1 of chunk i (and its stage) are ready
+            const float* Qs = reinterpret_cast<const float*>(stage0 + (size_t)s * sb);
+            const float* W1c = W1s + (i & 1) * 128;
+            // B = W1 (k = 2t, 2t + 1 -> rows t, t + 4; k = 2t + 8, 2t + 9 -> rows t + 8, t + 12), split
+            unsigned bw[3][2];
+            bf16x3_split(W1c[t * 8 + g], W1c[(t + 4) * 8 + g], bw[0][0], bw[1][0], bw[2][0]);
+            bf16x3_split(W1c[(t + 8) * 8 + g], W1c[(t + 12) * 8 + g], bw[0][1], bw[1][1], bw[2][1]);
+#pragma unroll
+            for (int k = 0; k < 2 * kFuMaxPairsPerWarp; ++k) {
+                const int p = gw + kFuGroupWarps * k;
+                if (p < npairs) {
+                    // A = [Q_2p Q_2p+1]^T: row = column of the pair (g: block 2p, g + 8:
+                    // block 2p + 1; for an odd last pair the second block's rows are unused)
+                    const float* T0 = Qs + (2 * p) * 128 + t * 8 + g;
+                    const float* T1 = T0 + 128;
+                    unsigned a[3][4];
+                    bf16x3_split(T0[0], T0[32], a[0][0], a[1][0], a[2][0]);
+                    bf16x3_split(T1[0], T1[32], a[0][1], a[1][1], a[2][1]);
+                    bf16x3_split(T0[64], T0[96], a[0][2], a[1][2], a[2][2]);
+                    bf16x3_split(T1[64], T1[96], a[0][3], a[1][3], a[2][3]);
+                    // the chunk's products from zero (the tensor cores' FP32 accumulation
+                    // truncates), then one rounded FP32 addition to the running sum
+                    float d[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma_bf16x3(d, a, bw);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) acc[k][r] += d[r];
+                }
+            }
+            fu_bar_arrive(4 + (i & 1), kFuThreads);  // done with chunk i's stage and W1
+        }
+        // this CTA's sums -> its FP64 slot (row-major m x 8)
+        double* part = partial + (int64_t)blockIdx.x * nblocks * 64;
+#pragma unroll
+        for (int k = 0; k < 2 * kFuMaxPairsPerWarp; ++k) {
+            const int p = gw + kFuGroupWarps * k;
+            if (p < npairs) {
+                part[((2 * p) * 8 + g) * 8 + 2 * t] = (double)acc[k][0];
+                part[((2 * p) * 8 + g) * 8 + 2 * t + 1] = (double)acc[k][1];
+                if (2 * p + 1 < nblocks) {
+                    part[((2 * p + 1) * 8 + g) * 8 + 2 * t] = (double)acc[k][2];
+                    part[((2 * p + 1) * 8 + g) * 8 + 2 * t + 1] = (double)acc[k][3];
+                }
             }
         }
     }
@@ -294,7 +318,7 @@ __global__ void __launch_bounds__(kFuThreads, 1) cgs_update_gram_kernel(int64_t 
 
 // stages of the ring for nblocks (0: the basis does not fit)
 int fu_stages(int nblocks) {
-    for (int s = kFuMaxStages; s >= 2; --s)
+    for (int s = kFuMaxStages; s >= 3; --s)
         if (fu_smem_bytes(nblocks, s) <= kFuSmemLimit) return s;
     return 0;
 }
@@ -302,7 +326,7 @@ int fu_stages(int nblocks) {
 }  // namespace
 
 bool update_gram_tc_supports(int nblocks) {
-    return nblocks >= 1 && nblocks <= kFuMaxBlocks && fu_stages(nblocks) >= 2;
+    return nblocks >= 1 && nblocks <= kFuMaxBlocks && fu_stages(nblocks) >= 3;
 }
 
 bbl_status update_gram_tc(int64_t n, int nblocks, const float* Q, const double* C1, float* W, double* C2,
@@ -327,19 +351,17 @@ bbl_status update_gram_tc(int64_t n, int nblocks, const float* Q, const double* 
     // [ update B fragments: tc pairs x 32 x (16 + 8) bytes | CTA slots: workers x per doubles ]
     const int ntp = fu_tc_pairs(nblocks);
     const size_t frag_bytes = (size_t)ntp * 32 * 24 + 256;
-    const size_t need = frag_bytes + sizeof(double) * (size_t)(workers * per) + 256;
+    const size_t need = frag_bytes + sizeof(double) * (size_t)(workers * per);
     BBL_TRY(work.grow(need));
     uint4* fa = reinterpret_cast<uint4*>(work.as<char>());
     uint2* fb = reinterpret_cast<uint2*>(work.as<char>() + (size_t)ntp * 32 * 16);
     double* slots = reinterpret_cast<double*>(work.as<char>() + frag_bytes);
-    int* ticket = reinterpret_cast<int*>(work.as<char>() + frag_bytes + sizeof(double) * (size_t)(workers * per));
-    BBL_CUDA(cudaMemsetAsync(ticket, 0, sizeof(int), st));
     if (ntp > 0) {
         cgs_split_c1_kernel<<<(unsigned)ceil_div(ntp * 32, 256), 256, 0, st>>>(nblocks, C1, fa, fb);
         BBL_LAUNCH_CHECK();
     }
     cgs_update_gram_kernel<<<(unsigned)workers, kFuThreads, smem, st>>>(n, nblocks, nchunks, stages, Q, C1, fa, fb,
-                                                                        W, slots, ticket);
+                                                                        W, slots);
     BBL_LAUNCH_CHECK();
     reduce_partials(per, (int)workers, slots, C2, st);
     BBL_LAUNCH_CHECK();
