@@ -474,7 +474,8 @@ def solve(A: Matrix, nev: int, b: int, pivot=None, evecs: str = "device", **opts
     """Block Lanczos for the nev lowest eigenpairs (bbl_solve).
 
     pivot: None (random), a CUDA tensor or a numpy array, n x b FP64.
-    evecs: "device" (CUDA tensor), "host" (numpy array) or None."""
+    evecs: "device" (CUDA tensor), "host" (numpy array), "pinned" (page-locked
+    CPU tensor: the copy back runs at the host link's full rate) or None."""
     torch = _torch()
     o = options(**opts)
     if "storage" not in opts:
@@ -487,6 +488,8 @@ def solve(A: Matrix, nev: int, b: int, pivot=None, evecs: str = "device", **opts
         X = torch.empty((A.n, nev), dtype=torch.float64, device="cuda")
     elif evecs == "host":
         X = np.zeros((A.n, nev))
+    elif evecs == "pinned":
+        X = torch.empty((A.n, nev), dtype=torch.float64, pin_memory=True)
     else:
         X = None
     if isinstance(pivot, np.ndarray):

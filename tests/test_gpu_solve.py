@@ -395,3 +395,26 @@ def test_solve_through_a_deflation_matches_the_dense_spectrum(storage, overlap):
     assert res.converged
     assert res.stats["deflations"] >= 1
     _check_eigs(res, ref, H, 1e-8)
+
+
+def test_solve_evecs_into_page_locked_host_memory_and_matrix_from_pinned_csr():
+    """A matrix built from page-locked host CSR arrays equals one built from
+    numpy arrays, and evecs="pinned" returns the eigenvectors in a
+    page-locked CPU tensor equal to the device result."""
+    torch, bbl = need_gpu()
+    import types
+    H = synth.kron_matrix("kron_n2e4", scale=0.3)
+    Hp = types.SimpleNamespace(n=H.n, row_ptr=torch.from_numpy(H.row_ptr).pin_memory(),
+                               col=torch.from_numpy(H.col).pin_memory(), val=torch.from_numpy(H.val).pin_memory())
+    M = bbl.Matrix(H)
+    Mp = bbl.Matrix(Hp)
+    assert Mp.nnz == M.nnz and Mp.norm_inf == M.norm_inf
+    np.testing.assert_array_equal(Mp.diagonal().cpu().numpy(), M.diagonal().cpu().numpy())
+    piv = OR.normal_block(5, H.n, 4)
+    rd = bbl.solve(M, 4, 4, pivot=piv, tol=1e-8, evecs="device")
+    rp = bbl.solve(Mp, 4, 4, pivot=piv, tol=1e-8, evecs="pinned")
+    assert rp.evecs.device.type == "cpu" and rp.evecs.is_pinned()
+    # the Gram-Schmidt kernels hand out row chunks dynamically: equal up to
+    # the order of their partial sums
+    np.testing.assert_allclose(rp.evals, rd.evals, rtol=1e-12)
+    np.testing.assert_allclose(rp.evecs.numpy(), rd.evecs.cpu().numpy(), atol=1e-9)
