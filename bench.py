@@ -329,6 +329,7 @@ def run_ours(args):
     solve_opts["stage1_tol"] = args.stage1_tol
     solve_opts["half_first_pass"] = args.half_first_pass
     solve_opts["fused_update_gram"] = args.fused_update_gram
+    solve_opts["half_first_update"] = args.half_first_update
 
     def step():
         b0 = torch.cuda.Event(enable_timing=True)
@@ -571,6 +572,13 @@ def run_kernels(args):
     Wt = torch.empty_like(Wr)
     t = timeit(lambda: bbl.block_reorth(basis, Wt.copy_(Wr), passes=1), args.reps)
     out["gram_update_fp32"] = {"ms": t, "GBs": (2 * n * m * 4 + 3 * n * B * 4) / t / 1e6}
+    # the first update with the blocks older than the two newest from the FP16 copy (tensor cores)
+    basis16 = basis.to(torch.float16)
+    C1h = bbl.block_gram(basis, Wr)
+    Wh = torch.empty_like(Wr)
+    t = timeit(lambda: bbl.block_update_f16old(basis16, basis, Wh.copy_(Wr), C1h), args.reps)
+    out["update_f16old"] = {"ms": t, "GBs": (n * (m - 16) * 2 + n * 16 * 4 + 3 * n * B * 4) / t / 1e6}
+    del basis16, Wh
     # the fused first update + second Gram (tensor cores): one read of the basis
     C1 = bbl.block_gram(basis, Wr)
     Wf = torch.empty_like(Wr)
@@ -980,6 +988,9 @@ def main():
     ap.add_argument("--fused-update-gram", type=int, default=0,
                     help="1: the first update and the second Gram in one tensor-core kernel; 0 (library default, "
                          "faster at n = 2e6): two FP32 kernels")
+    ap.add_argument("--half-first-update", type=int, default=1,
+                    help="1 (library default): the FP32 stage's first update reads the blocks older than the two "
+                         "newest from the FP16 copy; 0: every block in FP32")
     ap.add_argument("--stage1-tol", type=float, default=STAGE1_TOL,
                     help="FP32 stage tolerance before the polish (the library's default is 2e-6; 3e-7 measured "
                          "fastest on kron_n2e6)")

@@ -126,6 +126,16 @@ typedef struct {
                                    kernels on the FP32 pipes, which are faster
                                    at n = 2e6 (the fused kernel's 16-row
                                    chunks are latency-bound)                     */
+    int half_first_update;      /* with half_first_pass (FP32 blocks, b = 8): 1
+                                   (default) the first pass's update reads the
+                                   blocks older than the two newest from the
+                                   FP16 copy (their coefficients are of the
+                                   order of the lost orthogonality, so the
+                                   FP16 rounding changes W far below its FP32
+                                   rounding; bbl_block_update_f16old); 0 reads
+                                   every block in FP32.  Off after a thick
+                                   restart (restart_keep > 0), whose kept
+                                   blocks carry large coefficients.             */
 } bbl_options;
 
 typedef struct {
@@ -315,6 +325,28 @@ bbl_status bbl_block_gram_f16(int64_t n, int nblocks, const void* basis16, const
  * otherwise).  The call allocates its workspace and synchronises `stream`. */
 bbl_status bbl_block_update_gram(int64_t n, int nblocks, const float* basis, const double* C1, float* W, double* C2,
                                  void* stream);
+
+/* W -= Q C for b = 8 and FP32, with the blocks older than the `nnew` newest
+ * read from the FP16 copy of the basis: the first pass's update of the
+ * full reorthogonalisation (Sec. II.A, Eqs. 7-8) in the FP32 stage
+ * (bbl_options.half_first_update, nnew = 2: the blocks j and j-1 whose
+ * coefficients are A_j and B_{j-1}^T stay FP32).
+ *   basis16  device FP16, nblocks consecutive n x 8 row-major blocks
+ *            (round-to-nearest copies of the FP32 blocks)
+ *   basis    device FP32, the same blocks
+ *   C        device FP64 (nblocks*8) x 8 row-major
+ *   W        device FP32 n x 8, updated in place
+ *   nnew     0 <= nnew (all blocks FP16 when 0, all FP32 when >= nblocks)
+ * The older blocks' product runs on the tensor cores (mma.sync m16n8k16,
+ * FP16 in, FP32 accumulate) with their rows of C multiplied by one power of
+ * two s (largest entry into [2^13, 2^14)), rounded to FP16, and the sum
+ * multiplied by 1/s: a rounding of those coefficients, which the second
+ * Gram-Schmidt pass removes.  The newest blocks are FP32 FMA products with
+ * C rounded to FP32, added to the same FP32 sum, which is then subtracted
+ * from W.  basis16, basis and W 16-byte aligned (BBL_ERR_INVALID_ARG
+ * otherwise).  The call allocates its workspace and synchronises `stream`. */
+bbl_status bbl_block_update_f16old(int64_t n, int nblocks, int nnew, const void* basis16, const float* basis,
+                                   const double* C, float* W, void* stream);
 
 /* Allocation-free variant of bbl_block_gram (no counterpart in the paper).
  * For callers that must not allocate device memory: e.g. a process whose

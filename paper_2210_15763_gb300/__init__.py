@@ -284,6 +284,18 @@ def block_update_gram(basis, W, C1, stream=None):
     return C2
 
 
+def block_update_f16old(basis16, basis, W, C, nnew: int = 2, stream=None):
+    """W -= Q C in place (FP32, b = 8), the blocks older than the nnew newest
+    read from the FP16 copy basis16 (nblocks x n x 8 float16)."""
+    torch = _torch()
+    nb, n, b = basis.shape
+    if b != 8 or basis.dtype != torch.float32 or basis16.dtype != torch.float16 or W.dtype != torch.float32:
+        raise ValueError("block_update_f16old: FP32 basis of n x 8 blocks, its FP16 copy, FP32 W")
+    _lib.check(_lib.load().bbl_block_update_f16old(n, nb, int(nnew), _ptr(basis16), _ptr(basis),
+                                                   _ptr(C.contiguous()), _ptr(W), _stream(stream)))
+    return W
+
+
 def pivot_rr_residual(A: Matrix, P, stream=None):
     """Rayleigh-Ritz values and residual norms of span(P) (the test that chooses a pivot)."""
     b = P.shape[1]

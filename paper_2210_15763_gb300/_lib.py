@@ -18,7 +18,7 @@ class Options(C.Structure):
                 ("seed", C.c_uint64), ("defl_tol", C.c_double), ("storage", C.c_int), ("polish", C.c_int),
                 ("stage1_tol", C.c_double), ("check_every", C.c_int), ("stream", C.c_void_p),
                 ("ritz_overlap", C.c_int), ("half_first_pass", C.c_int), ("restart_keep", C.c_int),
-                ("max_blocks", C.c_int), ("fused_update_gram", C.c_int)]
+                ("max_blocks", C.c_int), ("fused_update_gram", C.c_int), ("half_first_update", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -72,6 +72,7 @@ SIGNATURES = {
     "bbl_block_gram_noalloc": (ST, [I64, I32, I32, I32, P, P, P, P]),
     "bbl_block_gram_f16": (ST, [I64, I32, P, P, P, P]),
     "bbl_block_update_gram": (ST, [I64, I32, P, P, P, P, P]),
+    "bbl_block_update_f16old": (ST, [I64, I32, I32, P, P, P, P, P]),
     "bbl_pivot_rr_residual": (ST, [P, I32, P, P, P, P]),
     "bbl_pivot_overlap": (ST, [I64, I32, P, I32, P, P, P]),
     "bbl_mlp_create": (ST, [I32, I32, C.POINTER(P)]),

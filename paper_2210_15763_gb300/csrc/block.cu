@@ -1147,6 +1147,131 @@ __global__ void __launch_bounds__(kThreads) apply_generic_kernel(int64_t n, int 
     }
 }
 
+// First-pass update of the FP32 stage, b = 8, with the older blocks read
+// from the FP16 copy: W -= sum_j Q_j C_j.  In Lanczos the first pass's
+// coefficients of the blocks older than the two newest are of the order of
+// the lost orthogonality (about 1e-7 of ||W|| in FP32): the FP16 rounding
+// of those blocks (2^-12 relative) changes W by about 2^-12 of that, far
+// below W's own FP32 rounding, and a rounding of their coefficients is a
+// change of the coefficients only (it stays in span(Q), and the second
+// pass removes it).  So the older blocks' product runs on the tensor cores
+// straight from the FP16 copy (mma.sync m16n8k16, FP16 in, FP32
+// accumulate): C's rows of those blocks are scaled by one power of two s
+// (the largest entry to [2^13, 2^14)) and rounded to FP16, and the sum is
+// multiplied by 1/s.  The newest blocks (jsplit and up), whose coefficients
+// are A_j and B_{j-1}^T, are FP32 FMA products with C rounded to FP32, as
+// in the FP32 update.
+
+// B fragments of the older blocks' product, per block pair q (blocks 2q,
+// 2q + 1 < jsplit, the second zero past it) and lane (g = lane / 4, t = lane
+// % 4): {C rows 16q + 2t, +1 | C rows 16q + 8 + 2t, +1}, column g, times s,
+// in FP16 pairs (low half = lower row); scale[0] = 1/s.  One CTA.
+__global__ void __launch_bounds__(256) half_old_prep_kernel(int jsplit, const double* __restrict__ C,
+                                                            uint2* __restrict__ frag, float* __restrict__ scale) {
+    __shared__ double smax[256];
+    double mx = 0.0;
+    for (int e = threadIdx.x; e < jsplit * 64; e += 256) mx = fmax(mx, fabs(C[e]));
+    smax[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + w]);
+        __syncthreads();
+    }
+    mx = smax[0];
+    int ex = 0;
+    if (mx > 0.0) (void)frexp(mx, &ex);  // mx = f 2^ex, f in [0.5, 1)
+    const double sc = (mx > 0.0) ? ldexp(1.0, 14 - ex) : 1.0;  // max * sc in [2^13, 2^14)
+    if (threadIdx.x == 0) scale[0] = (float)(1.0 / sc);
+    const int npo = (jsplit + 1) >> 1;
+    for (int e = threadIdx.x; e < npo * 32; e += 256) {
+        const int q = e >> 5, lane = e & 31, g = lane >> 2, t = lane & 3;
+        const int ra = 16 * q + 2 * t, rb = 16 * q + 8 + 2 * t;
+        const bool two = 2 * q + 1 < jsplit;
+        const __half2 b0 = __floats2half2_rn((float)(C[ra * 8 + g] * sc), (float)(C[(ra + 1) * 8 + g] * sc));
+        const __half2 b1 = two ? __floats2half2_rn((float)(C[rb * 8 + g] * sc), (float)(C[(rb + 1) * 8 + g] * sc))
+                               : __floats2half2_rn(0.f, 0.f);
+        frag[e] = make_uint2(*reinterpret_cast<const unsigned*>(&b0), *reinterpret_cast<const unsigned*>(&b1));
+    }
+}
+
+// One warp per 16-row tile.  A fragments of the older blocks come straight
+// from global memory (each 4-byte load of a warp covers 8 rows x 16 bytes
+// of one block: one 128-byte line).
+__global__ void __launch_bounds__(256) apply_half_old_kernel(int64_t n, int nblocks, int jsplit,
+                                                             const __half* __restrict__ Q16,
+                                                             const float* __restrict__ Q,
+                                                             const double* __restrict__ C,
+                                                             const uint2* __restrict__ frag,
+                                                             const float* __restrict__ scale, float* __restrict__ W) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t r0 = tile * 16;
+    if (r0 >= n) return;
+    const int64_t ra = r0 + g, rb = r0 + g + 8;
+    const bool oka = ra < n, okb = rb < n;
+    const unsigned* Q16w = reinterpret_cast<const unsigned*>(Q16);  // two halves per word
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    const int npo = (jsplit + 1) >> 1;
+    // groups of kHoU block pairs: every load of a group is issued before its products
+    constexpr int kHoU = 8;
+    for (int q0 = 0; q0 < npo; q0 += kHoU) {
+        unsigned a[kHoU][4];
+        unsigned b[kHoU][2];
+#pragma unroll
+        for (int u = 0; u < kHoU; ++u) {
+            const int q = q0 + u;
+            const bool on = q < npo;
+            const int j0 = on ? 2 * q : 0;
+            const int j1 = (on && 2 * q + 1 < nblocks) ? 2 * q + 1 : j0;  // past the basis: b1 is zero
+            a[u][0] = (on && oka) ? __ldg(Q16w + (((int64_t)j0 * n + ra) * 8 + 2 * t) / 2) : 0u;
+            a[u][1] = (on && okb) ? __ldg(Q16w + (((int64_t)j0 * n + rb) * 8 + 2 * t) / 2) : 0u;
+            a[u][2] = (on && oka) ? __ldg(Q16w + (((int64_t)j1 * n + ra) * 8 + 2 * t) / 2) : 0u;
+            a[u][3] = (on && okb) ? __ldg(Q16w + (((int64_t)j1 * n + rb) * 8 + 2 * t) / 2) : 0u;
+            const uint2 f = on ? __ldg(frag + q * 32 + lane) : make_uint2(0u, 0u);
+            b[u][0] = f.x;
+            b[u][1] = f.y;
+        }
+#pragma unroll
+        for (int u = 0; u < kHoU; ++u)
+            if (q0 + u < npo) mma_16816(d, a[u], b[u]);
+    }
+    const float inv = npo > 0 ? __ldg(scale) : 0.f;
+    // acc[row][col]: rows ra / rb, columns 2t, 2t + 1
+    float acc[2][2] = {{d[0] * inv, d[1] * inv}, {d[2] * inv, d[3] * inv}};
+    for (int j = jsplit; j < nblocks; ++j) {
+        float cj[8][2];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            cj[i][0] = (float)__ldg(C + (8 * j + i) * 8 + 2 * t);
+            cj[i][1] = (float)__ldg(C + (8 * j + i) * 8 + 2 * t + 1);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t rr = h ? rb : ra;
+            if (rr < n) {
+                const float4 x0 = __ldg(reinterpret_cast<const float4*>(Q + ((int64_t)j * n + rr) * 8));
+                const float4 x1 = __ldg(reinterpret_cast<const float4*>(Q + ((int64_t)j * n + rr) * 8 + 4));
+                const float qv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    acc[h][0] = fmaf(qv[i], cj[i][0], acc[h][0]);
+                    acc[h][1] = fmaf(qv[i], cj[i][1], acc[h][1]);
+                }
+            }
+        }
+    }
+    if (oka) {
+        float2* w = reinterpret_cast<float2*>(W + ra * 8 + 2 * t);
+        const float2 v = *w;
+        *w = make_float2(v.x - acc[0][0], v.y - acc[0][1]);
+    }
+    if (okb) {
+        float2* w = reinterpret_cast<float2*>(W + rb * 8 + 2 * t);
+        const float2 v = *w;
+        *w = make_float2(v.x - acc[1][0], v.y - acc[1][1]);
+    }
+}
+
 template <typename T, bool SUB, typename TA, typename TO>
 bbl_status apply_typed(int64_t n, int b, int m, int kc, const T* Q, const double* C, TO* W, cudaStream_t st) {
     const unsigned grid = (unsigned)ceil_div(n, kThreads);
@@ -1372,6 +1497,24 @@ bbl_status update(int64_t n, int b, int nblocks, int dtype, const void* Q, const
                                                    st);
     return apply_typed<float, true, float, float>(n, b, m, b, static_cast<const float*>(Q), C, static_cast<float*>(W),
                                                   st);
+}
+
+bbl_status update_half_old(int64_t n, int nblocks, int nnew, const void* Q16, const float* Q, const double* C,
+                           float* W, DevBuf& work, cudaStream_t st) {
+    const int jsplit = nblocks > nnew ? nblocks - nnew : 0;
+    const int npo = (jsplit + 1) >> 1;
+    BBL_TRY(work.grow(sizeof(uint2) * (size_t)npo * 32 + 256));
+    uint2* frag = work.as<uint2>();
+    float* scale = reinterpret_cast<float*>(work.as<char>() + sizeof(uint2) * (size_t)npo * 32);
+    if (npo > 0) {
+        half_old_prep_kernel<<<1, 256, 0, st>>>(jsplit, C, frag, scale);
+        BBL_LAUNCH_CHECK();
+    }
+    const int64_t warps = ceil_div(n, (int64_t)16);
+    apply_half_old_kernel<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, st>>>(
+        n, nblocks, jsplit, static_cast<const __half*>(Q16), Q, C, frag, scale, W);
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
 }
 
 bbl_status ritz_vectors(int64_t n, int b, int nblocks, int dtype, const void* Q, int k, const double* S, double* X,

@@ -258,6 +258,12 @@ bbl_status update(int64_t n, int b, int nblocks, int dtype, const void* Q, const
 // first-pass Gram C ~= Q16^T W from the FP16 copy Q16 of an FP32 basis (b = 8)
 bbl_status gram_half(int64_t n, int nblocks, const void* Q16, const float* W, double* C, DevBuf& partials,
                      cudaStream_t st);
+// W -= Q C (b = 8, FP32) with blocks 0 .. nblocks - nnew - 1 read from the
+// FP16 copy Q16 (tensor cores, their coefficients rounded to FP16 after a
+// power-of-two scaling) and the nnew newest from the FP32 basis Q (FMA);
+// work is grown as needed
+bbl_status update_half_old(int64_t n, int nblocks, int nnew, const void* Q16, const float* Q, const double* C,
+                           float* W, DevBuf& work, cudaStream_t st);
 // FP16 copy (round to nearest) of count FP32 values
 bbl_status to_half(int64_t count, const float* in, void* out, cudaStream_t st);
 // out[e] = sum over the nparts parts of partial[p * count + e], in a fixed order

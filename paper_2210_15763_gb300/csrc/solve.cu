@@ -445,6 +445,10 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     const bool half1 = dtype == BBL_FP32 && b == 8 && o.half_first_pass != 0;
     // FP32 blocks, b = 8: the first update and the second Gram share one read of the basis
     const bool fuse_on = dtype == BBL_FP32 && b == 8 && o.fused_update_gram != 0;
+    // FP32 blocks, b = 8, FP16 copy kept: the first update reads the blocks
+    // older than the two newest from it (not after a thick restart, whose
+    // kept blocks carry large coefficients)
+    const bool half_upd = half1 && o.half_first_update != 0 && keep == 0;
     {
         size_t freeb = 0, totalb = 0;
         BBL_CUDA(cudaMemGetInfo(&freeb, &totalb));
@@ -469,7 +473,7 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
                          "solve: restart_keep=%d must be a multiple of b=%d, >= nev=%d, <= %d, with room for %d more "
                          "blocks (basis capacity %d blocks)", keep, b, nev, kRestartMaxK, 2, J_max);
     const int max_total = restart_on ? (o.max_blocks > 0 ? o.max_blocks : 10000) : J_max;
-    DevBuf Z, coeff, partials, small, Tb, S, rwork, flags, bj;
+    DevBuf Z, coeff, partials, small, Tb, S, rwork, flags, bj, hwork;
     PoolBuf basis;
     // float-float blocks: FP32 copies of the basis (high parts) and of W for
     // the first Gram-Schmidt pass, whose coefficients only need to remove the
@@ -760,7 +764,11 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             // first update and second Gram in one read of the basis (tensor cores)
             BBL_TRY(update_gram_tc(n, j + 1, basis.as<float>(), C1, reinterpret_cast<float*>(Wn), C2, partials, st));
         } else {
-            BBL_TRY(update(n, b, j + 1, dtype, basis.p, C1, Wn, st));
+            if (half_upd)
+                BBL_TRY(update_half_old(n, j + 1, 2, shadow.p, basis.as<float>(), C1, reinterpret_cast<float*>(Wn),
+                                        hwork, st));
+            else
+                BBL_TRY(update(n, b, j + 1, dtype, basis.p, C1, Wn, st));
             BBL_TRY(gram(n, b, j + 1, dtype, basis.p, Wn, C2, partials, st));
         }
         BBL_TRY(update(n, b, j + 1, dtype, basis.p, C2, Wn, st));
@@ -787,7 +795,8 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             out.spmm_bytes += spmm_alg_bytes(A, b, sv, sx);
             // two passes of Gram + update; an FP16 first-pass Gram reads 2 bytes per basis
             // element, and the fused first update + second Gram reads the basis once
-            out.reorth_bytes += ((half1 ? 0.5 : 1.0) + (fused2 ? 2.0 : 3.0)) * (double)n * m * sx +
+            const double upd1 = (half_upd && !fused2 && j >= 2) ? 0.5 * (double)(j - 1) / (j + 1) + 2.0 / (j + 1) : 1.0;
+            out.reorth_bytes += ((half1 ? 0.5 : 1.0) + (fused2 ? 2.0 : 2.0 + upd1)) * (double)n * m * sx +
                                 6.0 * (double)n * b * sx;
         }
         out.spmm_calls = tb + 1;
@@ -1096,6 +1105,22 @@ extern "C" bbl_status bbl_block_update_gram(int64_t n, int nblocks, const float*
     cudaStream_t st = as_stream(stream);
     DevBuf work;
     BBL_TRY(update_gram_tc(n, nblocks, basis, C1, W, C2, work, st));
+    BBL_CUDA(cudaStreamSynchronize(st));
+    return BBL_OK;
+}
+
+// W -= Q C with the blocks older than the nnew newest read from the FP16 copy
+// (b = 8, FP32): the FP32 stage's first-pass update on its own.
+extern "C" bbl_status bbl_block_update_f16old(int64_t n, int nblocks, int nnew, const void* basis16,
+                                              const float* basis, const double* C, float* W, void* stream) {
+    using namespace bbl;
+    if (n < 1 || nblocks < 1 || nnew < 0 || !basis16 || !basis || !C || !W)
+        return set_error(BBL_ERR_INVALID_ARG, "block_update_f16old: bad arguments");
+    if (!aligned16(basis16) || !aligned16(basis) || !aligned16(W))
+        return set_error(BBL_ERR_INVALID_ARG, "block_update_f16old: pointers must be 16-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    DevBuf work;
+    BBL_TRY(update_half_old(n, nblocks, nnew, basis16, basis, C, W, work, st));
     BBL_CUDA(cudaStreamSynchronize(st));
     return BBL_OK;
 }

@@ -276,6 +276,69 @@ def test_block_update_gram_on_an_orthonormal_basis_removes_the_projection():
     np.testing.assert_allclose(C2, Qcat.T @ W1, atol=1e-6 * scale)
 
 
+def _f16old_coefficients(C, js):
+    """The coefficients the FP16-copy update applies: rows of the js older
+    blocks times s = 2^(14 - e) (max |C_old| = f 2^e, f in [0.5, 1)), rounded
+    to FP16 and divided by s; the newer rows rounded to FP32."""
+    Ce = C.astype(np.float32).astype(np.float64)
+    if js > 0:
+        mx = np.abs(C[:8 * js]).max()
+        s = 2.0 ** (14 - np.frexp(mx)[1]) if mx > 0 else 1.0
+        Ce[:8 * js] = (C[:8 * js] * s).astype(np.float32).astype(np.float16).astype(np.float64) / s
+    return Ce
+
+
+@pytest.mark.parametrize("n,nb,nnew", [(5, 1, 2), (37, 3, 2), (1000, 7, 2), (20_011, 50, 2), (4096, 9, 0),
+                                      (3001, 6, 6), (100_003, 99, 2), (17, 4, 1)])
+def test_block_update_f16old_matches_fp64_product(n, nb, nnew):
+    """W -= Q C with the blocks older than the nnew newest read from the FP16
+    copy (tensor cores, their coefficients scaled by a power of two and
+    rounded to FP16): against the FP64 product of exactly those operands,
+    within the FP32 sums' rounding.  The sizes cover one block, a ragged
+    last 16-row tile, fewer rows than one tile, odd older-block counts (the
+    last pair has one block), all blocks FP16 (nnew = 0) and all FP32."""
+    torch, bbl = need_gpu()
+    rng = np.random.default_rng(11 * n + nb)
+    Q = (rng.standard_normal((nb, n, 8)) / np.sqrt(n)).astype(np.float32)
+    Q16 = Q.astype(np.float16)
+    W = rng.standard_normal((n, 8)).astype(np.float32)
+    C = rng.standard_normal((nb * 8, 8))
+    Wd = torch.from_numpy(W).cuda()
+    bbl.block_update_f16old(torch.from_numpy(Q16).cuda(), torch.from_numpy(Q).cuda(), Wd, torch.from_numpy(C).cuda(),
+                            nnew=nnew)
+    W1 = Wd.cpu().numpy().astype(np.float64)
+    js = max(nb - nnew, 0)
+    Qused = np.concatenate([Q16[:js].astype(np.float64), Q[js:].astype(np.float64)], axis=0)
+    Qcat = np.concatenate(list(Qused), axis=1)   # n x m
+    Ce = _f16old_coefficients(C, js)
+    ref = W.astype(np.float64) - Qcat @ Ce
+    S = np.abs(Qcat) @ np.abs(Ce)
+    m = nb * 8
+    assert np.all(np.abs(W1 - ref) <= 2 * (m + 1) * EPS32 * (S + np.abs(W)))
+    # the typical error is far below that bound: a misread block would show here
+    assert np.abs(W1 - ref).max() <= 1e-5 * (S.max() + np.abs(W).max())
+
+
+def test_half_first_update_keeps_the_fp32_stage_and_the_result():
+    """The FP32 stage with the first update's older blocks read from the FP16
+    copy (default) and from the FP32 basis: the same block counts to within
+    two, the FP32-stage eigenvalues to the stage's accuracy, and after the
+    polish the same eigenvalues to the FP64 level."""
+    torch, bbl = need_gpu()
+    H = synth.kron_matrix("kron_n2e4", scale=0.6)
+    M = bbl.Matrix(H, storage="fp32")
+    piv = OR.normal_block(13, H.n, 8)
+    r1 = bbl.solve(M, 8, 8, pivot=piv, tol=2e-6, polish=0, max_vectors=800, half_first_update=1)
+    r0 = bbl.solve(M, 8, 8, pivot=piv, tol=2e-6, polish=0, max_vectors=800, half_first_update=0)
+    assert r1.converged and r0.converged
+    assert abs(r1.stats["iters"] - r0.stats["iters"]) <= 2
+    np.testing.assert_allclose(r1.evals, r0.evals, rtol=2e-6)
+    p1 = bbl.solve(M, 8, 8, pivot=piv, tol=1e-9, max_vectors=800, half_first_update=1)
+    p0 = bbl.solve(M, 8, 8, pivot=piv, tol=1e-9, max_vectors=800, half_first_update=0)
+    assert p1.converged and p0.converged
+    np.testing.assert_allclose(p1.evals, p0.evals, rtol=1e-11)
+
+
 def test_fused_update_gram_keeps_the_fp32_stage_and_the_result():
     """The FP32 stage with the fused first update + second Gram and
     with the two FP32-pipe kernels reach the same eigenvalues; after the
