@@ -989,7 +989,7 @@ def main():
                     help="1: the first update and the second Gram in one tensor-core kernel; 0 (library default, "
                          "faster at n = 2e6): two FP32 kernels")
     ap.add_argument("--half-first-update", type=int, default=1,
-                    help="1 (library default): the FP32 stage's first update reads the blocks older than the two "
+                    help="1 (library default): the FP32 stage's updates read the blocks older than the two "
                          "newest from the FP16 copy; 0: every block in FP32")
     ap.add_argument("--stage1-tol", type=float, default=STAGE1_TOL,
                     help="FP32 stage tolerance before the polish (the library's default is 2e-6; 3e-7 measured "

@@ -127,11 +127,12 @@ typedef struct {
                                    at n = 2e6 (the fused kernel's 16-row
                                    chunks are latency-bound)                     */
     int half_first_update;      /* with half_first_pass (FP32 blocks, b = 8): 1
-                                   (default) the first pass's update reads the
+                                   (default) both passes' updates read the
                                    blocks older than the two newest from the
                                    FP16 copy (their coefficients are of the
-                                   order of the lost orthogonality, so the
-                                   FP16 rounding changes W far below its FP32
+                                   order of the lost orthogonality and of the
+                                   first pass's FP16 Gram error, so the FP16
+                                   rounding changes W far below its FP32
                                    rounding; bbl_block_update_f16old); 0 reads
                                    every block in FP32.  Off after a thick
                                    restart (restart_keep > 0), whose kept

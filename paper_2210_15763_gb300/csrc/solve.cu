@@ -771,7 +771,11 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
                 BBL_TRY(update(n, b, j + 1, dtype, basis.p, C1, Wn, st));
             BBL_TRY(gram(n, b, j + 1, dtype, basis.p, Wn, C2, partials, st));
         }
-        BBL_TRY(update(n, b, j + 1, dtype, basis.p, C2, Wn, st));
+        if (half_upd)
+            BBL_TRY(update_half_old(n, j + 1, 2, shadow.p, basis.as<float>(), C2, reinterpret_cast<float*>(Wn), hwork,
+                                    st));
+        else
+            BBL_TRY(update(n, b, j + 1, dtype, basis.p, C2, Wn, st));
         // A_j = sym(C1 + C2)[j-block]: the second pass's own-block coefficients
         // are the rounding (or, from a cheaper first pass, the approximation)
         // the first left in A_j
@@ -795,8 +799,9 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             out.spmm_bytes += spmm_alg_bytes(A, b, sv, sx);
             // two passes of Gram + update; an FP16 first-pass Gram reads 2 bytes per basis
             // element, and the fused first update + second Gram reads the basis once
-            const double upd1 = (half_upd && !fused2 && j >= 2) ? 0.5 * (double)(j - 1) / (j + 1) + 2.0 / (j + 1) : 1.0;
-            out.reorth_bytes += ((half1 ? 0.5 : 1.0) + (fused2 ? 2.0 : 2.0 + upd1)) * (double)n * m * sx +
+            // an update with the blocks older than the two newest from the FP16 copy
+            const double upd = (half_upd && j >= 2) ? 0.5 * (double)(j - 1) / (j + 1) + 2.0 / (j + 1) : 1.0;
+            out.reorth_bytes += ((half1 ? 0.5 : 1.0) + (fused2 ? 1.0 : 1.0 + upd) + upd) * (double)n * m * sx +
                                 6.0 * (double)n * b * sx;
         }
         out.spmm_calls = tb + 1;

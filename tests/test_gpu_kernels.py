@@ -320,10 +320,10 @@ def test_block_update_f16old_matches_fp64_product(n, nb, nnew):
 
 
 def test_half_first_update_keeps_the_fp32_stage_and_the_result():
-    """The FP32 stage with the first update's older blocks read from the FP16
-    copy (default) and from the FP32 basis: the same block counts to within
-    two, the FP32-stage eigenvalues to the stage's accuracy, and after the
-    polish the same eigenvalues to the FP64 level."""
+    """The FP32 stage with both updates' older blocks read from the FP16 copy
+    (default) and from the FP32 basis: the same block counts to within two,
+    the FP32-stage eigenvalues to the stage's accuracy, and after the polish
+    the same eigenvalues to the FP64 level."""
     torch, bbl = need_gpu()
     H = synth.kron_matrix("kron_n2e4", scale=0.6)
     M = bbl.Matrix(H, storage="fp32")
