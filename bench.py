@@ -329,7 +329,7 @@ def run_ours(args):
     solve_opts["stage1_tol"] = args.stage1_tol
     solve_opts["half_first_pass"] = args.half_first_pass
     solve_opts["fused_update_gram"] = args.fused_update_gram
-    solve_opts["half_first_update"] = args.half_first_update
+    solve_opts["narrow_old_updates"] = args.narrow_old_updates
 
     def step():
         b0 = torch.cuda.Event(enable_timing=True)
@@ -988,7 +988,7 @@ def main():
     ap.add_argument("--fused-update-gram", type=int, default=0,
                     help="1: the first update and the second Gram in one tensor-core kernel; 0 (library default, "
                          "faster at n = 2e6): two FP32 kernels")
-    ap.add_argument("--half-first-update", type=int, default=1,
+    ap.add_argument("--narrow-old-updates", type=int, default=1,
                     help="1 (library default): the FP32 stage's updates read the blocks older than the two "
                          "newest from the FP16 copy; 0: every block in FP32")
     ap.add_argument("--stage1-tol", type=float, default=STAGE1_TOL,

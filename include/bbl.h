@@ -126,7 +126,7 @@ typedef struct {
                                    kernels on the FP32 pipes, which are faster
                                    at n = 2e6 (the fused kernel's 16-row
                                    chunks are latency-bound)                     */
-    int half_first_update;      /* with half_first_pass (FP32 blocks, b = 8): 1
+    int narrow_old_updates;      /* with half_first_pass (FP32 blocks, b = 8): 1
                                    (default) both passes' updates read the
                                    blocks older than the two newest from the
                                    FP16 copy (their coefficients are of the
@@ -330,7 +330,7 @@ bbl_status bbl_block_update_gram(int64_t n, int nblocks, const float* basis, con
 /* W -= Q C for b = 8 and FP32, with the blocks older than the `nnew` newest
  * read from the FP16 copy of the basis: the first pass's update of the
  * full reorthogonalisation (Sec. II.A, Eqs. 7-8) in the FP32 stage
- * (bbl_options.half_first_update, nnew = 2: the blocks j and j-1 whose
+ * (bbl_options.narrow_old_updates, nnew = 2: the blocks j and j-1 whose
  * coefficients are A_j and B_{j-1}^T stay FP32).
  *   basis16  device FP16, nblocks consecutive n x 8 row-major blocks
  *            (round-to-nearest copies of the FP32 blocks)

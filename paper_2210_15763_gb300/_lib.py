@@ -18,7 +18,7 @@ class Options(C.Structure):
                 ("seed", C.c_uint64), ("defl_tol", C.c_double), ("storage", C.c_int), ("polish", C.c_int),
                 ("stage1_tol", C.c_double), ("check_every", C.c_int), ("stream", C.c_void_p),
                 ("ritz_overlap", C.c_int), ("half_first_pass", C.c_int), ("restart_keep", C.c_int),
-                ("max_blocks", C.c_int), ("fused_update_gram", C.c_int), ("half_first_update", C.c_int)]
+                ("max_blocks", C.c_int), ("fused_update_gram", C.c_int), ("narrow_old_updates", C.c_int)]
 
 
 class Stats(C.Structure):

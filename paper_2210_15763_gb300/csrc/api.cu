@@ -219,7 +219,7 @@ void bbl_options_default(bbl_options* o) {
     o->ritz_overlap = 1;
     o->half_first_pass = 1;
     o->fused_update_gram = 0;
-    o->half_first_update = 1;
+    o->narrow_old_updates = 1;
     o->stream = nullptr;
 }
 

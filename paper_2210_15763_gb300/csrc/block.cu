@@ -1272,6 +1272,65 @@ __global__ void __launch_bounds__(256) apply_half_old_kernel(int64_t n, int nblo
     }
 }
 
+// Update of the float-float polish, b = 8: W -= sum_j Q_j C_j with the
+// blocks older than jsplit read from the FP32 copy of the basis (the high
+// parts) with FP32 products and sums, the newer ones from the float-float
+// basis with float-float products.  The older blocks' coefficients are the
+// lost orthogonality and the FP32 first-pass Gram's error, so their FP32
+// products (2^-24 relative) change W far below its float-float rounding;
+// their bytes halve and their arithmetic is one FMA per product.
+__global__ void __launch_bounds__(kThreads) apply_df32_f32old_kernel(int64_t n, int m, int jsplit,
+                                                                     const float* __restrict__ Q32,
+                                                                     const df32* __restrict__ Q,
+                                                                     const double* __restrict__ C, df32* W) {
+    constexpr int B = 8;
+    __shared__ df32 cs[kKT * B];
+    const int tid = threadIdx.x;
+    const int64_t r = (int64_t)blockIdx.x * kThreads + tid;
+    float a32[B];
+    df32 adf[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+        a32[c] = 0.f;
+        adf[c] = df32(0.f);
+    }
+    for (int a0 = 0; a0 < m; a0 += kKT) {
+        const int rows = min(kKT, m - a0);
+        __syncthreads();
+        for (int e = tid; e < rows * B; e += kThreads) cs[e] = df32(C[(int64_t)a0 * B + e]);
+        __syncthreads();
+        if (r < n) {
+            for (int jb = 0; jb < rows; jb += B) {
+                const int j = (a0 + jb) / B;
+                const df32* cr = cs + jb * B;
+                if (j < jsplit) {
+                    const float4 x0 = __ldg(reinterpret_cast<const float4*>(Q32 + ((int64_t)j * n + r) * B));
+                    const float4 x1 = __ldg(reinterpret_cast<const float4*>(Q32 + ((int64_t)j * n + r) * B + 4));
+                    const float q[B] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                    for (int i = 0; i < B; ++i)
+#pragma unroll
+                        for (int c = 0; c < B; ++c) a32[c] = fmaf(q[i], cr[i * B + c].hi, a32[c]);
+                } else {
+                    df32 q[B];
+                    ldvec<df32, B>(Q + ((int64_t)j * n + r) * B, q);
+#pragma unroll
+                    for (int i = 0; i < B; ++i)
+#pragma unroll
+                        for (int c = 0; c < B; ++c) adf[c] = dfm::fma(q[i], cr[i * B + c], adf[c]);
+                }
+            }
+        }
+    }
+    if (r < n) {
+#pragma unroll
+        for (int c = 0; c < B; ++c) {
+            df32* w = W + r * B + c;
+            *w = *w - (adf[c] + df32(a32[c]));
+        }
+    }
+}
+
 template <typename T, bool SUB, typename TA, typename TO>
 bbl_status apply_typed(int64_t n, int b, int m, int kc, const T* Q, const double* C, TO* W, cudaStream_t st) {
     const unsigned grid = (unsigned)ceil_div(n, kThreads);
@@ -1513,6 +1572,15 @@ bbl_status update_half_old(int64_t n, int nblocks, int nnew, const void* Q16, co
     const int64_t warps = ceil_div(n, (int64_t)16);
     apply_half_old_kernel<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, st>>>(
         n, nblocks, jsplit, static_cast<const __half*>(Q16), Q, C, frag, scale, W);
+    BBL_LAUNCH_CHECK();
+    return BBL_OK;
+}
+
+bbl_status update_df32_f32old(int64_t n, int nblocks, int nnew, const float* Q32, const void* Q, const double* C,
+                             void* W, cudaStream_t st) {
+    const int jsplit = nblocks > nnew ? nblocks - nnew : 0;
+    apply_df32_f32old_kernel<<<(unsigned)ceil_div(n, kThreads), kThreads, 0, st>>>(
+        n, nblocks * 8, jsplit, Q32, static_cast<const df32*>(Q), C, static_cast<df32*>(W));
     BBL_LAUNCH_CHECK();
     return BBL_OK;
 }

@@ -264,6 +264,11 @@ bbl_status gram_half(int64_t n, int nblocks, const void* Q16, const float* W, do
 // work is grown as needed
 bbl_status update_half_old(int64_t n, int nblocks, int nnew, const void* Q16, const float* Q, const double* C,
                            float* W, DevBuf& work, cudaStream_t st);
+// float-float W -= Q C (b = 8) with blocks 0 .. nblocks - nnew - 1 read from
+// the FP32 copy Q32 (FP32 products and sums) and the nnew newest from the
+// float-float basis Q
+bbl_status update_df32_f32old(int64_t n, int nblocks, int nnew, const float* Q32, const void* Q, const double* C,
+                             void* W, cudaStream_t st);
 // FP16 copy (round to nearest) of count FP32 values
 bbl_status to_half(int64_t count, const float* in, void* out, cudaStream_t st);
 // out[e] = sum over the nparts parts of partial[p * count + e], in a fixed order

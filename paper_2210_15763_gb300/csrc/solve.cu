@@ -445,10 +445,11 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
     const bool half1 = dtype == BBL_FP32 && b == 8 && o.half_first_pass != 0;
     // FP32 blocks, b = 8: the first update and the second Gram share one read of the basis
     const bool fuse_on = dtype == BBL_FP32 && b == 8 && o.fused_update_gram != 0;
-    // FP32 blocks, b = 8, FP16 copy kept: the first update reads the blocks
-    // older than the two newest from it (not after a thick restart, whose
-    // kept blocks carry large coefficients)
-    const bool half_upd = half1 && o.half_first_update != 0 && keep == 0;
+    // b = 8 with a narrower copy of the basis kept (FP16 for FP32 blocks, FP32
+    // for float-float blocks): both updates read the blocks older than the
+    // two newest from it (not after a thick restart, whose kept blocks carry
+    // large coefficients)
+    const bool half_upd = (half1 || (dtype == kDF32 && b == 8)) && o.narrow_old_updates != 0 && keep == 0;
     {
         size_t freeb = 0, totalb = 0;
         BBL_CUDA(cudaMemGetInfo(&freeb, &totalb));
@@ -570,6 +571,10 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
         return BBL_OK;
     };
     BBL_TRY(shadow_block(0));
+    auto narrow_update = [&](int nbk, const double* Cc, char* Wp) -> bbl_status {
+        if (dtype == kDF32) return update_df32_f32old(n, nbk, 2, shadow.as<float>(), basis.p, Cc, Wp, st);
+        return update_half_old(n, nbk, 2, shadow.p, basis.as<float>(), Cc, reinterpret_cast<float*>(Wp), hwork, st);
+    };
 
     // The Ritz solve of T_j runs on a side stream while the main stream goes
     // on with block j+1 (whose SpMM does not need it); the host checks the
@@ -765,15 +770,13 @@ bbl_status lanczos_stage(const bbl_matrix* A, int nev, int b, const double* pivo
             BBL_TRY(update_gram_tc(n, j + 1, basis.as<float>(), C1, reinterpret_cast<float*>(Wn), C2, partials, st));
         } else {
             if (half_upd)
-                BBL_TRY(update_half_old(n, j + 1, 2, shadow.p, basis.as<float>(), C1, reinterpret_cast<float*>(Wn),
-                                        hwork, st));
+                BBL_TRY(narrow_update(j + 1, C1, Wn));
             else
                 BBL_TRY(update(n, b, j + 1, dtype, basis.p, C1, Wn, st));
             BBL_TRY(gram(n, b, j + 1, dtype, basis.p, Wn, C2, partials, st));
         }
         if (half_upd)
-            BBL_TRY(update_half_old(n, j + 1, 2, shadow.p, basis.as<float>(), C2, reinterpret_cast<float*>(Wn), hwork,
-                                    st));
+            BBL_TRY(narrow_update(j + 1, C2, Wn));
         else
             BBL_TRY(update(n, b, j + 1, dtype, basis.p, C2, Wn, st));
         // A_j = sym(C1 + C2)[j-block]: the second pass's own-block coefficients

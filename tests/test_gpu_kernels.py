@@ -319,7 +319,7 @@ def test_block_update_f16old_matches_fp64_product(n, nb, nnew):
     assert np.abs(W1 - ref).max() <= 1e-5 * (S.max() + np.abs(W).max())
 
 
-def test_half_first_update_keeps_the_fp32_stage_and_the_result():
+def test_narrow_old_updates_keeps_the_fp32_stage_and_the_result():
     """The FP32 stage with both updates' older blocks read from the FP16 copy
     (default) and from the FP32 basis: the same block counts to within two,
     the FP32-stage eigenvalues to the stage's accuracy, and after the polish
@@ -328,13 +328,13 @@ def test_half_first_update_keeps_the_fp32_stage_and_the_result():
     H = synth.kron_matrix("kron_n2e4", scale=0.6)
     M = bbl.Matrix(H, storage="fp32")
     piv = OR.normal_block(13, H.n, 8)
-    r1 = bbl.solve(M, 8, 8, pivot=piv, tol=2e-6, polish=0, max_vectors=800, half_first_update=1)
-    r0 = bbl.solve(M, 8, 8, pivot=piv, tol=2e-6, polish=0, max_vectors=800, half_first_update=0)
+    r1 = bbl.solve(M, 8, 8, pivot=piv, tol=2e-6, polish=0, max_vectors=800, narrow_old_updates=1)
+    r0 = bbl.solve(M, 8, 8, pivot=piv, tol=2e-6, polish=0, max_vectors=800, narrow_old_updates=0)
     assert r1.converged and r0.converged
     assert abs(r1.stats["iters"] - r0.stats["iters"]) <= 2
     np.testing.assert_allclose(r1.evals, r0.evals, rtol=2e-6)
-    p1 = bbl.solve(M, 8, 8, pivot=piv, tol=1e-9, max_vectors=800, half_first_update=1)
-    p0 = bbl.solve(M, 8, 8, pivot=piv, tol=1e-9, max_vectors=800, half_first_update=0)
+    p1 = bbl.solve(M, 8, 8, pivot=piv, tol=1e-9, max_vectors=800, narrow_old_updates=1)
+    p0 = bbl.solve(M, 8, 8, pivot=piv, tol=1e-9, max_vectors=800, narrow_old_updates=0)
     assert p1.converged and p0.converged
     np.testing.assert_allclose(p1.evals, p0.evals, rtol=1e-11)
 
