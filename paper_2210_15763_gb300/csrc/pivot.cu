@@ -294,6 +294,9 @@ extern "C" bbl_status bbl_pivot_bootstrap(const bbl_matrix* A, int64_t trunc_dim
         o.stream = stream;
         o.storage = sub32 ? BBL_FP32 : BBL_FP64;
         o.polish = 0;
+        // a truncated space is small: its blocks take tens of microseconds, so
+        // a Ritz solve beside them would only let the run overshoot its test
+        o.ritz_overlap = 0;
         const int bs = (int)std::min<int64_t>(b, k);
         o.max_vectors = (int)std::min<int64_t>((k / bs) * bs, 2000);
         DevBuf Y;
