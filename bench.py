@@ -484,8 +484,9 @@ def run_ours(args):
                    "method": f"bootstrap trunc_dim={TRUNC} sub_tol={args.sub_tol:g}, FP32 stage "
                              f"({sched['fmt']}, lanes {sched['lanes']}, sigma {sched['sigma']}"
                              f"{'' if args.stage1_tol is None else f', to {args.stage1_tol:g}'}"
-                             f"{', FP16 first-pass Gram' if args.half_first_pass else ''}) + float-float polish, "
-                             f"FP64 residuals",
+                             f"{', FP16 first-pass Gram' if args.half_first_pass else ''}"
+                             f"{', older blocks of both updates from the narrower copy' if args.narrow_old_updates else ''}"
+                             f") + float-float polish, FP64 residuals",
                    "parallelism": "replicas only" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (matrix 4.8 GB)"},
         "converged": ok, "max_resid_rel": resid_rel,
