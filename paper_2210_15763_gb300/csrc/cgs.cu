@@ -21,14 +21,14 @@
 // 4 are formed: a b = a1 b1 + a1 b2 + a2 b1 + a1 b3 + a2 b2 + a3 b1 + e with
 // |e| <= 2^-23 |a b|, about the rounding of an FP32 product.
 //  * Update: M = the chunk's 16 rows, N = 8, K = 16 = the columns of a pair
-//    of basis blocks; the warps split the pairs (two accumulators each) and
-//    their partial sums are added in a fixed order.  The two newest blocks
+//    of basis blocks; the update group's warps split the pairs (two
+//    accumulators each) and their partial sums are added in a fixed order.  The two newest blocks
 //    are applied with FP32 FMAs instead (W's own-block and previous-block
 //    coefficients in Lanczos are of the order of ||H||, the older ones of
 //    the order of the lost orthogonality).
 //  * Gram: M = 16 basis columns (a pair of blocks), N = 8, K = the chunk's
 //    16 rows (k = 2t, 2t+1, 2t+8, 2t+9 read rows t, t+4, t+8, t+12, the same
-//    order for W1); each warp keeps its pairs' 16 x 8 sums in registers over
+//    order for W1); each Gram warp keeps its pairs' 16 x 8 sums in registers over
 //    every chunk its CTA takes (a chunk's products are formed from zero and
 //    added to the running sum in FP32, so the accumulation's rounding is
 //    that of plain FP32 additions), and the CTAs' sums are added in FP64.
@@ -43,8 +43,8 @@ namespace {
 constexpr int kFuRows = 16;                          // rows per chunk
 constexpr int kFuWarps = 16;
 constexpr int kFuThreads = 32 * kFuWarps;
-constexpr int kFuMaxPairsPerWarp = 4;                // register sums per warp
-constexpr int kFuMaxBlocks = 2 * kFuWarps * kFuMaxPairsPerWarp;  // 128 blocks = 1024 columns
+constexpr int kFuMaxBlocks = 128;                    // 1024 basis columns
+constexpr int kFuGramPairsPerWarp = kFuMaxBlocks / 2 / (kFuWarps / 2);  // register sums per Gram warp
 constexpr int kFuMaxStages = 5;
 constexpr size_t kFuSmemLimit = 220 * 1024;
 
@@ -263,9 +263,9 @@ __global__ void __launch_bounds__(kFuThreads, 1) cgs_update_gram_kernel(int64_t 
         // ---------------- Gram group
         const int gw = warp - kFuGroupWarps;
         const int npairs = (nblocks + 1) >> 1;
-        float acc[2 * kFuMaxPairsPerWarp][4];
+        float acc[kFuGramPairsPerWarp][4];
 #pragma unroll
-        for (int k = 0; k < 2 * kFuMaxPairsPerWarp; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.f;
+        for (int k = 0; k < kFuGramPairsPerWarp; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.f;
         int i = 0;
         for (int64_t c = blockIdx.x; c < nchunks; c += G, ++i) {
             const int s = i % stages;
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kFuThreads, 1) cgs_update_gram_kernel(int64_t 
             bf16x3_split(W1c[t * 8 + g], W1c[(t + 4) * 8 + g], bw[0][0], bw[1][0], bw[2][0]);
             bf16x3_split(W1c[(t + 8) * 8 + g], W1c[(t + 12) * 8 + g], bw[0][1], bw[1][1], bw[2][1]);
 #pragma unroll
-            for (int k = 0; k < 2 * kFuMaxPairsPerWarp; ++k) {
+            for (int k = 0; k < kFuGramPairsPerWarp; ++k) {
                 const int p = gw + kFuGroupWarps * k;
                 if (p < npairs) {
                     // A = [Q_2p Q_2p+1]^T: row = column of the pair (g: block 2p, g + 8:
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(kFuThreads, 1) cgs_update_gram_kernel(int64_t 
         // this CTA's sums -> its FP64 slot (row-major m x 8)
         double* part = partial + (int64_t)blockIdx.x * nblocks * 64;
 #pragma unroll
-        for (int k = 0; k < 2 * kFuMaxPairsPerWarp; ++k) {
+        for (int k = 0; k < kFuGramPairsPerWarp; ++k) {
             const int p = gw + kFuGroupWarps * k;
             if (p < npairs) {
                 part[((2 * p) * 8 + g) * 8 + 2 * t] = (double)acc[k][0];
