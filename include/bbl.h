@@ -340,7 +340,8 @@ bbl_status bbl_block_update_gram(int64_t n, int nblocks, const float* basis, con
  *   nnew     0 <= nnew (all blocks FP16 when 0, all FP32 when >= nblocks)
  * The older blocks' product runs on the tensor cores (mma.sync m16n8k16,
  * FP16 in, FP32 accumulate) with their rows of C multiplied by one power of
- * two s (largest entry into [2^13, 2^14)), rounded to FP16, and the sum
+ * two s (largest entry into [2^13, 2^14); s at most 2^114), rounded to
+ * FP16, and the sum
  * multiplied by 1/s: a rounding of those coefficients, which the second
  * Gram-Schmidt pass removes.  The newest blocks are FP32 FMA products with
  * C rounded to FP32, added to the same FP32 sum, which is then subtracted

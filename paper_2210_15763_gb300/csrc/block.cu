@@ -1201,7 +1201,10 @@ __global__ void __launch_bounds__(256) half_old_prep_kernel(int jsplit, const do
     mx = smax[0];
     int ex = 0;
     if (mx > 0.0) (void)frexp(mx, &ex);  // mx = f 2^ex, f in [0.5, 1)
-    const double sc = (mx > 0.0) ? ldexp(1.0, 14 - ex) : 1.0;  // max * sc in [2^13, 2^14)
+    // max * sc in [2^13, 2^14); coefficients below 2^-100 (negligible) keep
+    // sc = 2^114, so that sc and 1/sc stay finite and normal in FP32
+    ex = ex < -100 ? -100 : ex;
+    const double sc = (mx > 0.0) ? ldexp(1.0, 14 - ex) : 1.0;
     if (threadIdx.x == 0) scale[0] = (float)(1.0 / sc);
     const int npo = (jsplit + 1) >> 1;
     for (int e = threadIdx.x; e < npo * 32; e += 256) {

@@ -278,12 +278,13 @@ def test_block_update_gram_on_an_orthonormal_basis_removes_the_projection():
 
 def _f16old_coefficients(C, js):
     """The coefficients the FP16-copy update applies: rows of the js older
-    blocks times s = 2^(14 - e) (max |C_old| = f 2^e, f in [0.5, 1)), rounded
-    to FP16 and divided by s; the newer rows rounded to FP32."""
+    blocks times s = 2^(14 - e) (max |C_old| = f 2^e, f in [0.5, 1), e at
+    least -100), rounded to FP16 and divided by s; the newer rows rounded to
+    FP32."""
     Ce = C.astype(np.float32).astype(np.float64)
     if js > 0:
         mx = np.abs(C[:8 * js]).max()
-        s = 2.0 ** (14 - np.frexp(mx)[1]) if mx > 0 else 1.0
+        s = 2.0 ** (14 - max(int(np.frexp(mx)[1]), -100)) if mx > 0 else 1.0
         Ce[:8 * js] = (C[:8 * js] * s).astype(np.float32).astype(np.float16).astype(np.float64) / s
     return Ce
 
